@@ -1,0 +1,230 @@
+/*
+ * qaoa.h -- C ABI of libqaoa: orbit-reduced depth-p QAOA MaxCut energies and
+ * their adjoint gradients on one GB300 (sm_103a).
+ *
+ * What is computed (arXiv:2101.10296):
+ *   E_p(gamma, beta) = sum_{(u,v) in E} 1/2 (1 - <Z_u Z_v>)       (Sec. 2.3-2.4)
+ * for the QAOA state U_B(beta_p) U_P(gamma_p) ... U_B(beta_1) U_P(gamma_1)|+>^n
+ * with U_P(gamma) = exp(-i gamma H), H the diagonal cut count, and
+ * U_B(beta) = prod_j exp(-i beta X_j) (Sec. 2.2).  Each edge term is simulated
+ * on the state vector of the edge's reverse causal cone, the vertices within
+ * distance p of the edge (Sec. 2.3), and with orbit reduction only one
+ * representative edge per orbit of Aut(G) is simulated, its term weighted by
+ * the orbit size (Sec. 3, Theorem 1 and the orbit-weighted sum after it).
+ *
+ * Conventions used by every entry point:
+ *   - A graph is simple and undirected: vertices 0..n-1, edges given as
+ *     int32 pairs [m][2] (either order), no self-loops, no repeated edges.
+ *   - Parameter rows are (gamma_1..gamma_p, beta_1..beta_p), float64.
+ *   - Return value: QAOA_OK (0) or a negative qaoa_status.  On error a
+ *     message is available from qaoa_last_error() (thread-local) and no
+ *     output has been written unless stated.  Argument errors are found on
+ *     the host before anything is launched.
+ *   - Device pointers (suffix _dev) are caller-owned CUDA device memory on
+ *     the current device; host pointers (no suffix) are caller-owned host
+ *     memory.  Device-side work is enqueued on `stream` (a cudaStream_t;
+ *     NULL = legacy default stream) and is asynchronous: outputs are ready
+ *     when the stream reaches that point.
+ *   - A plan is immutable after qaoa_plan_upload and may be used from
+ *     several streams at once; each call gets its own stream-ordered scratch.
+ */
+#ifndef QAOA_H
+#define QAOA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qaoa_plan qaoa_plan;
+typedef void *qaoa_stream_t; /* cudaStream_t */
+
+enum qaoa_status {
+    QAOA_OK = 0,
+    QAOA_E_INVALID = -1,        /* bad argument, graph or state */
+    QAOA_E_CONE_TOO_LARGE = -2, /* a cone exceeds the qubit or edge cap */
+    QAOA_E_OOM = -3,            /* host or device allocation failed */
+    QAOA_E_CUDA = -4,           /* a CUDA runtime call failed */
+    QAOA_E_DEVICE = -5          /* a kernel's own guard tripped (status word) */
+};
+
+enum qaoa_flags {
+    QAOA_ORBITS_OFF = 0u, /* every edge is its own representative */
+    QAOA_ORBITS = 1u,     /* one representative per edge orbit of Aut(G) */
+    QAOA_FULL_CONE = 2u   /* simulate the whole 2^n cone state with the mixer on
+                             every cone qubit in every layer (no pruning of the
+                             gates that cancel); slower, used for cross-checks */
+};
+
+/* Largest cone handled: qubits per cone and local edges per cone. */
+#define QAOA_MAX_CONE_QUBITS 32
+#define QAOA_MAX_CONE_EDGES 64
+#define QAOA_MAX_P 8
+
+/*
+ * qaoa_plan_graphs -- plan a batch of graphs (host only; no CUDA call).
+ *
+ * Steps, per graph: validate and build adjacency; if QAOA_ORBITS, find the
+ * edge orbits of Aut(G) (Sec. 2.6 and Sec. 4: colour refinement, then an
+ * individualisation-refinement search for automorphism generators, each
+ * verified to preserve every edge; orbits by union-find); pick the smallest
+ * edge index of each orbit as its representative (the paper's arbitrary
+ * representative, Sec. 3); extract each representative's reverse causal cone
+ * (Sec. 2.3): BFS to depth p from {u, v}, local qubit 0 = min(u,v),
+ * 1 = max(u,v), the rest ordered by (distance, vertex id); the cone's edges
+ * are the edges with at least one endpoint within distance p-1 (the terms
+ * whose support meets the growing operator support, Sec. 2.3).
+ *
+ *   n_graphs        number of graphs G >= 1
+ *   n_vertices      host int32[G]
+ *   edge_offsets    host int64[G+1]; graph g owns edge rows
+ *                   edge_offsets[g] .. edge_offsets[g+1]-1 of `edges`
+ *   edges           host int32[edge_offsets[G]][2]
+ *   p               QAOA depth, 1..QAOA_MAX_P
+ *   flags           qaoa_flags
+ *   max_cone_qubits cap on qubits per cone (<= QAOA_MAX_CONE_QUBITS;
+ *                   0 = QAOA_MAX_CONE_QUBITS); a larger cone fails the
+ *                   call with QAOA_E_CONE_TOO_LARGE
+ *   search_budget   cap on refinement calls of the automorphism search per
+ *                   graph (0 = default 2,000,000).  When reached, the search
+ *                   stops and the orbits of the verified subgroup found so far
+ *                   are used: still exact (any subgroup of symmetries gives a
+ *                   valid reduction, Sec. 3), only less reduced.
+ *   out             receives the new plan (caller frees with qaoa_plan_free)
+ *
+ * Errors: QAOA_E_INVALID (bad sizes, vertex out of range, self-loop,
+ * repeated edge, p out of range), QAOA_E_CONE_TOO_LARGE, QAOA_E_OOM.
+ */
+int qaoa_plan_graphs(int32_t n_graphs, const int32_t *n_vertices,
+                     const int64_t *edge_offsets, const int32_t *edges,
+                     int32_t p, uint32_t flags, int32_t max_cone_qubits,
+                     int64_t search_budget, qaoa_plan **out);
+
+/* Single-graph form of qaoa_plan_graphs (edges: host int32[n_edges][2]). */
+int qaoa_plan_graph(int32_t n_vertices, int64_t n_edges, const int32_t *edges,
+                    int32_t p, uint32_t flags, int32_t max_cone_qubits,
+                    int64_t search_budget, qaoa_plan **out);
+
+/* Frees the plan and all host and device memory it owns.  NULL is a no-op.
+ * The caller must make sure no stream still uses the plan. */
+void qaoa_plan_free(qaoa_plan *plan);
+
+typedef struct qaoa_plan_info_t {
+    int32_t p;
+    int32_t n_graphs;
+    int64_t n_edges_total;  /* sum of |E_g| */
+    int64_t n_reps;         /* simulated cones (= orbits, or edges if OFF) */
+    int32_t max_qubits;     /* largest cone */
+    int32_t max_inner;      /* largest inner part (qubits within distance p-1) */
+    int32_t max_edges;      /* largest cone edge count */
+    int32_t on_device;      /* 1 after qaoa_plan_upload */
+    int64_t n_big;          /* cones routed to the large-state path */
+    double amps_per_point;  /* sum over reps of 2^n_c (one eval, one layer) */
+    double t_orbits_s;      /* wall time of orbit finding (all graphs) */
+    double t_cones_s;       /* wall time of cone extraction */
+    int32_t orbits_complete; /* 1 if every graph's search finished in budget */
+} qaoa_plan_info_t;
+
+int qaoa_plan_info(const qaoa_plan *plan, qaoa_plan_info_t *info);
+
+/*
+ * Per-graph orbit summary.  orbit_id: host int32[|E_g|] (may be NULL)
+ * receives, for each edge in input order, the index of the smallest edge in
+ * its orbit.  n_orbits, log10_aut (log10 of the order of the group found,
+ * from the orbit-stabiliser product along the search's first path) and
+ * complete (1 if the search finished within budget) may each be NULL.
+ */
+int qaoa_plan_orbits(const qaoa_plan *plan, int32_t graph, int32_t *orbit_id,
+                     int64_t *n_orbits, double *log10_aut, int32_t *complete);
+
+/*
+ * Representatives, in plan order (the row order of terms_dev).  Each array
+ * is host memory of length n_reps and may be NULL.  weight = orbit size.
+ */
+int qaoa_plan_reps(const qaoa_plan *plan, int32_t *graph, int64_t *edge,
+                   int32_t *weight, int32_t *n_qubits, int32_t *n_inner,
+                   int32_t *n_cone_edges);
+
+/*
+ * One representative's cone.  verts: host int32[n_qubits] global vertex of
+ * each local qubit; dist: host int32[n_qubits] distance to the edge;
+ * cone_edges: host int32[n_cone_edges][2] local pairs (a < b), in the bit
+ * order used by the cut table.  Any pointer may be NULL.
+ */
+int qaoa_plan_cone(const qaoa_plan *plan, int64_t rep, int32_t *verts,
+                   int32_t *dist, int32_t *cone_edges);
+
+/*
+ * Host-only edge-orbit finder on one graph (the plan's orbit step alone),
+ * for callers that only want symmetry.  orbit_id: host int32[n_edges] as in
+ * qaoa_plan_orbits.  n_generators, log10_aut and complete may be NULL.
+ */
+int qaoa_edge_orbits(int32_t n_vertices, int64_t n_edges, const int32_t *edges,
+                     int64_t search_budget, int32_t *orbit_id,
+                     int64_t *n_orbits, int64_t *n_generators,
+                     double *log10_aut, int32_t *complete);
+
+/*
+ * Copies the plan's cone descriptors to the current device (synchronous).
+ * Called implicitly by the first energy call if not done; calling it first
+ * keeps allocation out of later calls.  Errors: QAOA_E_CUDA, QAOA_E_OOM.
+ */
+int qaoa_plan_upload(qaoa_plan *plan);
+
+/*
+ * Integer cut table of one representative's cone (Sec. 2.4: the MaxCut
+ * Hamiltonian is diagonal with value C(z) = number of cone edges (a, b) with
+ * z_a != z_b; bit q of z is local qubit q).  out_dev: device uint8[2^n]
+ * with n = the cone's qubit count; computed by the same device routine the
+ * energy kernels use.  Bit-exact.
+ */
+int qaoa_cut_table(const qaoa_plan *plan, int64_t rep, uint8_t *out_dev,
+                   qaoa_stream_t stream);
+
+/*
+ * Energies at n_points parameter points per graph.
+ *   params_dev  device float64[n_graphs][n_points][2p]
+ *   energy_dev  device float64[n_graphs][n_points]  E_p of each graph
+ *   terms_dev   optional device float64[n_reps][n_points]: <Z_u Z_v> of each
+ *               representative (NULL to skip)
+ * State: complex64 amplitudes, FP32 arithmetic; cut values are integers;
+ * the phase table exp(-i gamma c) is computed in FP64 and rounded to FP32;
+ * per-cone and orbit-weighted sums are accumulated in FP64.
+ * Errors: QAOA_E_INVALID (n_points < 1, NULL params/energy),
+ * QAOA_E_CUDA / QAOA_E_OOM.
+ */
+int qaoa_energy(const qaoa_plan *plan, int64_t n_points, const double *params_dev,
+                double *energy_dev, double *terms_dev, qaoa_stream_t stream);
+
+/*
+ * Energies and their gradients dE/d(gamma_1..gamma_p, beta_1..beta_p) by the
+ * adjoint method: after the forward sweep, the state psi and the co-state
+ * lambda = -1/2 Z_u Z_v psi are taken back through the inverse gates; each
+ * derivative is 2 Im <lambda| G |psi> at the gate exp(-i theta G).
+ *   grad_dev  device float64[n_graphs][n_points][2p]
+ * Other arguments and errors as qaoa_energy.
+ */
+int qaoa_energy_grad(const qaoa_plan *plan, int64_t n_points,
+                     const double *params_dev, double *energy_dev,
+                     double *grad_dev, double *terms_dev, qaoa_stream_t stream);
+
+/*
+ * Reads and clears the plan's device status word (synchronises the device).
+ * *status = 0 if no kernel guard tripped since the last read; otherwise a
+ * nonzero code (1: descriptor out of range, 2: non-finite result).
+ */
+int qaoa_device_status(const qaoa_plan *plan, int32_t *status);
+
+/* Last error message of the calling thread ("" if none). */
+const char *qaoa_last_error(void);
+
+/* Library version string. */
+const char *qaoa_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QAOA_H */

@@ -1,0 +1,334 @@
+// C-ABI device entry points: plan upload, energy / gradient launches,
+// cut tables, device status.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "device.cuh"
+#include "host.hpp"
+
+using namespace qaoa;
+
+struct DevWork {
+    int32_t *order = nullptr;
+    int64_t *prefix = nullptr;
+    int32_t *warp_first = nullptr;
+    int64_t slots = 0, warps = 0;
+    int32_t n = 0;
+};
+
+struct qaoa_device_plan {
+    int device = -1;
+    DevCone *cones = nullptr;
+    int64_t n_cones = 0;
+    DevWork reg6, reg5;
+    double *half_edges = nullptr;
+    int32_t *status = nullptr;
+    int32_t cmax1 = 1;
+    int64_t n_big = 0;
+};
+
+namespace {
+
+int cuda_fail(cudaError_t e, const char *what) {
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? QAOA_E_OOM : QAOA_E_CUDA;
+}
+
+void free_work(DevWork &w) {
+    cudaFree(w.order);
+    cudaFree(w.prefix);
+    cudaFree(w.warp_first);
+    w = DevWork{};
+}
+
+// Builds the slot list for R register qubits over the given plan indices.
+int build_work(const std::vector<DevCone> &hc, const std::vector<int32_t> &idx, int R, DevWork &w) {
+    std::vector<int32_t> order(idx);
+    auto T = [&](int32_t i) { return int64_t(1) << std::max(hc[i].n - R, 0); };
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return T(a) > T(b); });
+    std::vector<int64_t> prefix(order.size() + 1, 0);
+    for (size_t i = 0; i < order.size(); ++i) prefix[i + 1] = prefix[i] + T(order[i]);
+    const int64_t slots = prefix.back();
+    const int64_t warps = (slots + 31) / 32;
+    std::vector<int32_t> first(size_t(std::max<int64_t>(warps, 1)), 0);
+    size_t ci = 0;
+    for (int64_t wi = 0; wi < warps; ++wi) {
+        while (prefix[ci + 1] <= wi * 32) ++ci;
+        first[wi] = int32_t(ci);
+    }
+    w.slots = slots;
+    w.warps = warps;
+    w.n = int32_t(order.size());
+    if (order.empty()) return QAOA_OK;
+    cudaError_t e;
+    if ((e = cudaMalloc(&w.order, order.size() * sizeof(int32_t))) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&w.prefix, prefix.size() * sizeof(int64_t))) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&w.warp_first, first.size() * sizeof(int32_t))) != cudaSuccess)
+        return cuda_fail(e, "cudaMalloc");
+    cudaMemcpy(w.order, order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    cudaMemcpy(w.prefix, prefix.data(), prefix.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+    if ((e = cudaMemcpy(w.warp_first, first.data(), first.size() * sizeof(int32_t), cudaMemcpyHostToDevice)) !=
+        cudaSuccess)
+        return cuda_fail(e, "cudaMemcpy");
+    return QAOA_OK;
+}
+
+RegWork as_reg(const qaoa_device_plan *d, const DevWork &w) {
+    RegWork r;
+    r.cones = d->cones;
+    r.order = w.order;
+    r.prefix = w.prefix;
+    r.warp_first = w.warp_first;
+    r.n_cones = w.n;
+    r.slots = w.slots;
+    r.warps = w.warps;
+    return r;
+}
+
+int check_device(const qaoa_plan *plan) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev != plan->dev->device) {
+        set_error("plan was uploaded to device " + std::to_string(plan->dev->device) + ", current device is " +
+                  std::to_string(dev));
+        return QAOA_E_INVALID;
+    }
+    return QAOA_OK;
+}
+
+int ensure_uploaded(const qaoa_plan *plan) {
+    if (!plan->dev) return qaoa_plan_upload(const_cast<qaoa_plan *>(plan));
+    return check_device(plan);
+}
+
+int run(const qaoa_plan *plan, int64_t n_points, const double *params, double *energy, double *grad,
+        double *terms, cudaStream_t s) {
+    if (!plan || n_points < 1 || !params || !energy) {
+        set_error("need a plan, n_points >= 1, params and energy");
+        return QAOA_E_INVALID;
+    }
+    int rc = ensure_uploaded(plan);
+    if (rc != QAOA_OK) return rc;
+    const qaoa_device_plan *d = plan->dev;
+    const int32_t G = plan->n_graphs, p = plan->p;
+    float2 *lut = nullptr, *mix = nullptr;
+    const size_t nlut = size_t(G) * n_points * p * d->cmax1;
+    const size_t nmix = size_t(G) * n_points * p;
+    cudaError_t e;
+    if ((e = cudaMallocAsync(&lut, nlut * sizeof(float2), s)) != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
+    if ((e = cudaMallocAsync(&mix, nmix * sizeof(float2), s)) != cudaSuccess) {
+        cudaFreeAsync(lut, s);
+        return cuda_fail(e, "cudaMallocAsync");
+    }
+    PrepArgs pa;
+    pa.params = params;
+    pa.G = G;
+    pa.p = p;
+    pa.cmax1 = d->cmax1;
+    pa.P = n_points;
+    pa.half_edges = d->half_edges;
+    pa.lut = lut;
+    pa.mix = mix;
+    pa.energy = energy;
+    pa.grad = grad;
+    pa.terms = terms;
+    pa.n_reps = d->n_cones;
+    e = launch_prep(pa, s);
+    if (e == cudaSuccess) {
+        RegLaunch L;
+        L.n_points = n_points;
+        L.p = p;
+        L.cmax1 = d->cmax1;
+        L.lut = lut;
+        L.mix = mix;
+        L.energy = energy;
+        L.grad = grad;
+        L.terms = terms;
+        L.status = d->status;
+        if (grad) {
+            L.work = as_reg(d, d->reg5);
+            if (L.work.warps > 0) {
+                int64_t grid = std::min<int64_t>(reg_grad_grid(), (L.work.warps * n_points + 3) / 4);
+                e = launch_reg_grad(L, int(std::max<int64_t>(grid, 1)), s);
+            }
+        } else {
+            L.work = as_reg(d, d->reg6);
+            if (L.work.warps > 0) {
+                int64_t grid = std::min<int64_t>(reg_energy_grid(), (L.work.warps * n_points + 3) / 4);
+                e = launch_reg_energy(L, int(std::max<int64_t>(grid, 1)), s);
+            }
+        }
+    }
+    cudaFreeAsync(mix, s);
+    cudaFreeAsync(lut, s);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    return QAOA_OK;
+}
+
+}  // namespace
+
+extern "C" void qaoa_device_release(qaoa_plan *plan) {
+    if (!plan || !plan->dev) return;
+    qaoa_device_plan *d = plan->dev;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (d->device >= 0) cudaSetDevice(d->device);
+    cudaFree(d->cones);
+    free_work(d->reg6);
+    free_work(d->reg5);
+    cudaFree(d->half_edges);
+    cudaFree(d->status);
+    if (cur >= 0) cudaSetDevice(cur);
+    delete d;
+    plan->dev = nullptr;
+}
+
+extern "C" int qaoa_plan_upload(qaoa_plan *plan) {
+    if (!plan) {
+        set_error("plan is NULL");
+        return QAOA_E_INVALID;
+    }
+    if (plan->dev) return check_device(plan);
+    std::vector<DevCone> hc(plan->cones.size());
+    int32_t cmax = 0;
+    std::vector<int32_t> reg_idx;
+    int64_t n_big = 0;
+    for (size_t i = 0; i < plan->cones.size(); ++i) {
+        const Cone &c = plan->cones[i];
+        DevCone &d = hc[i];
+        std::memset(&d, 0, sizeof d);
+        d.graph = c.graph;
+        d.n = c.n;
+        d.n_in = c.n_in;
+        d.m = int32_t(c.ea.size());
+        for (int l = 0; l < QAOA_MAX_P; ++l) d.k[l] = c.k[l];
+        d.weight = double(c.weight);
+        d.rep = int64_t(i);
+        for (size_t e = 0; e < c.ea.size(); ++e) {
+            d.col[c.ea[e]] |= 1ull << e;
+            d.col[c.eb[e]] |= 1ull << e;
+        }
+        cmax = std::max(cmax, d.m);
+        if (c.n_in <= kRegBitsGrad + kLaneBits)
+            reg_idx.push_back(int32_t(i));
+        else
+            ++n_big;
+    }
+    if (n_big > 0) {
+        set_error("cones whose inner part exceeds 10 qubits need the large-state path");
+        return QAOA_E_CONE_TOO_LARGE;
+    }
+    auto *d = new qaoa_device_plan;
+    cudaGetDevice(&d->device);
+    d->n_cones = int64_t(hc.size());
+    d->cmax1 = cmax + 1;
+    d->n_big = n_big;
+    plan->dev = d;
+    cudaError_t e;
+    int rc = QAOA_OK;
+    if (!hc.empty()) {
+        if ((e = cudaMalloc(&d->cones, hc.size() * sizeof(DevCone))) != cudaSuccess) {
+            rc = cuda_fail(e, "cudaMalloc");
+        } else if ((e = cudaMemcpy(d->cones, hc.data(), hc.size() * sizeof(DevCone), cudaMemcpyHostToDevice)) !=
+                   cudaSuccess) {
+            rc = cuda_fail(e, "cudaMemcpy");
+        }
+    }
+    if (rc == QAOA_OK) rc = build_work(hc, reg_idx, kRegBitsEnergy, d->reg6);
+    if (rc == QAOA_OK) rc = build_work(hc, reg_idx, kRegBitsGrad, d->reg5);
+    if (rc == QAOA_OK) {
+        std::vector<double> half(size_t(plan->n_graphs));
+        for (int32_t g = 0; g < plan->n_graphs; ++g) half[g] = 0.5 * double(plan->n_edges[g]);
+        if ((e = cudaMalloc(&d->half_edges, half.size() * sizeof(double))) != cudaSuccess)
+            rc = cuda_fail(e, "cudaMalloc");
+        else
+            cudaMemcpy(d->half_edges, half.data(), half.size() * sizeof(double), cudaMemcpyHostToDevice);
+    }
+    if (rc == QAOA_OK) {
+        if ((e = cudaMalloc(&d->status, sizeof(int32_t))) != cudaSuccess)
+            rc = cuda_fail(e, "cudaMalloc");
+        else if ((e = cudaMemset(d->status, 0, sizeof(int32_t))) != cudaSuccess)
+            rc = cuda_fail(e, "cudaMemset");
+    }
+    if (rc == QAOA_OK && (e = cudaDeviceSynchronize()) != cudaSuccess) rc = cuda_fail(e, "upload");
+    if (rc != QAOA_OK) qaoa_device_release(plan);
+    return rc;
+}
+
+extern "C" int qaoa_plan_info(const qaoa_plan *plan, qaoa_plan_info_t *info) {
+    if (!plan || !info) {
+        set_error("plan or info is NULL");
+        return QAOA_E_INVALID;
+    }
+    std::memset(info, 0, sizeof *info);
+    info->p = plan->p;
+    info->n_graphs = plan->n_graphs;
+    for (int64_t m : plan->n_edges) info->n_edges_total += m;
+    info->n_reps = int64_t(plan->cones.size());
+    info->orbits_complete = 1;
+    for (const auto &o : plan->orbits) info->orbits_complete &= o.complete ? 1 : 0;
+    for (const Cone &c : plan->cones) {
+        info->max_qubits = std::max(info->max_qubits, c.n);
+        info->max_inner = std::max(info->max_inner, c.n_in);
+        info->max_edges = std::max(info->max_edges, int32_t(c.ea.size()));
+        info->amps_per_point += std::ldexp(1.0, c.n);
+        if (c.n_in > kRegBitsGrad + kLaneBits) info->n_big++;
+    }
+    info->on_device = plan->dev ? 1 : 0;
+    info->t_orbits_s = plan->t_orbits;
+    info->t_cones_s = plan->t_cones;
+    return QAOA_OK;
+}
+
+extern "C" int qaoa_energy(const qaoa_plan *plan, int64_t n_points, const double *params_dev, double *energy_dev,
+                           double *terms_dev, qaoa_stream_t stream) {
+    return run(plan, n_points, params_dev, energy_dev, nullptr, terms_dev, (cudaStream_t)stream);
+}
+
+extern "C" int qaoa_energy_grad(const qaoa_plan *plan, int64_t n_points, const double *params_dev,
+                                double *energy_dev, double *grad_dev, double *terms_dev, qaoa_stream_t stream) {
+    if (!grad_dev) {
+        set_error("grad_dev is NULL");
+        return QAOA_E_INVALID;
+    }
+    return run(plan, n_points, params_dev, energy_dev, grad_dev, terms_dev, (cudaStream_t)stream);
+}
+
+extern "C" int qaoa_cut_table(const qaoa_plan *plan, int64_t rep, uint8_t *out_dev, qaoa_stream_t stream) {
+    if (!plan || rep < 0 || rep >= int64_t(plan->cones.size()) || !out_dev) {
+        set_error("bad plan, representative index or output pointer");
+        return QAOA_E_INVALID;
+    }
+    int rc = ensure_uploaded(plan);
+    if (rc != QAOA_OK) return rc;
+    cudaError_t e =
+        launch_cut_table(plan->dev->cones + rep, out_dev, plan->cones[rep].n, plan->dev->status, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cut table launch");
+    return QAOA_OK;
+}
+
+extern "C" int qaoa_device_status(const qaoa_plan *plan, int32_t *status) {
+    if (!plan || !status) {
+        set_error("plan or status is NULL");
+        return QAOA_E_INVALID;
+    }
+    if (!plan->dev) {
+        *status = 0;
+        return QAOA_OK;
+    }
+    int rc = check_device(plan);
+    if (rc != QAOA_OK) return rc;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+    int32_t v = 0;
+    if ((e = cudaMemcpy(&v, plan->dev->status, sizeof v, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpy");
+    cudaMemset(plan->dev->status, 0, sizeof(int32_t));
+    *status = v;
+    return QAOA_OK;
+}

@@ -1,0 +1,84 @@
+// Device-side data layout shared by the kernels and the C-ABI launch code.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/qaoa.h"
+
+namespace qaoa {
+
+// One simulated cone (representative edge), as the kernels read it.
+//
+// Local qubits: 0 = u, 1 = v, then by (distance, vertex id).  `col[q]` has
+// bit e set when cone edge e touches qubit q, so for a basis index z the
+// word M(z) = XOR over set bits q of z of col[q] has bit e set exactly when
+// edge e is cut, and the cut value is C(z) = popcount(M(z)).  M is linear
+// over GF(2): M(hi | lo) = M(hi) ^ M(lo), which the kernels use to split z
+// into a per-thread part and a per-register part.
+struct alignas(16) DevCone {
+    int32_t graph;   // graph index g
+    int32_t n;       // qubits
+    int32_t n_in;    // inner qubits: the only ones any mixer touches
+    int32_t m;       // cone edges
+    int32_t k[QAOA_MAX_P];  // layer l mixes qubits [0, k[l])
+    double weight;   // orbit size
+    int64_t rep;     // row of this cone in terms[]
+    uint64_t col[QAOA_MAX_CONE_QUBITS];
+};
+
+// Work list of the register-resident kernels.  Each (cone, point) needs
+// T_c = 2^max(n_c - R, 0) threads (R register qubits per thread).  Cones are
+// sorted by T_c descending so that every cone's first slot is aligned to
+// min(T_c, 32) lanes; slots of one point are the concatenation of all cones'
+// T_c slots and a warp covers 32 consecutive slots of one point.
+struct RegWork {
+    const DevCone *cones = nullptr;     // plan order
+    const int32_t *order = nullptr;     // sorted position -> plan index
+    const int64_t *prefix = nullptr;    // [n+1] slot prefix over sorted cones
+    const int32_t *warp_first = nullptr;  // sorted index of the cone at slot 32*w
+    int32_t n_cones = 0;
+    int64_t slots = 0;                  // slots per point
+    int64_t warps = 0;                  // warps per point
+};
+
+struct RegLaunch {
+    RegWork work;
+    int64_t n_points;
+    int32_t p;
+    int32_t cmax1;            // phase-table row length (max cone edges + 1)
+    const float2 *lut;        // [G][P][p][cmax1]  exp(-i gamma_l c)
+    const float2 *mix;        // [G][P][p]         (cos beta_l, sin beta_l)
+    double *energy;           // [G][P]
+    double *grad;             // [G][P][2p] or null
+    double *terms;            // [reps][P] or null
+    int32_t *status;
+};
+
+struct PrepArgs {
+    const double *params;     // [G][P][2p]
+    int32_t G, p, cmax1;
+    int64_t P;
+    const double *half_edges; // [G]
+    float2 *lut;
+    float2 *mix;
+    double *energy;
+    double *grad;             // may be null
+    double *terms;            // may be null
+    int64_t n_reps;
+};
+
+// launchers (kernels.cu)
+cudaError_t launch_prep(const PrepArgs &a, cudaStream_t s);
+cudaError_t launch_reg_energy(const RegLaunch &a, int grid, cudaStream_t s);
+cudaError_t launch_reg_grad(const RegLaunch &a, int grid, cudaStream_t s);
+cudaError_t launch_cut_table(const DevCone *cone, uint8_t *out, int32_t n, int32_t *status, cudaStream_t s);
+// occupancy-sized persistent grids
+int reg_energy_grid();
+int reg_grad_grid();
+
+constexpr int kRegBitsEnergy = 5;
+constexpr int kRegBitsGrad = 5;
+constexpr int kLaneBits = 5;
+
+}  // namespace qaoa

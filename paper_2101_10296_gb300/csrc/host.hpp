@@ -1,0 +1,75 @@
+// Host-side planner internals: graph, edge-orbit finder, lightcone extractor,
+// plan object.  Nothing here touches CUDA.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/qaoa.h"
+
+namespace qaoa {
+
+// Simple undirected graph in CSR form.  Edge e joins eu[e] < ev[e]; adj lists
+// are sorted and eid[k] is the edge id of adjacency entry k.
+struct Graph {
+    int32_t n = 0;
+    int64_t m = 0;
+    std::vector<int64_t> off;
+    std::vector<int32_t> adj;
+    std::vector<int64_t> eid;
+    std::vector<int32_t> eu, ev;
+    int32_t degree(int32_t v) const { return int32_t(off[v + 1] - off[v]); }
+};
+
+// Validates and builds; returns QAOA_OK or QAOA_E_INVALID with `err` set.
+int build_graph(int32_t n, int64_t m, const int32_t *edges, Graph &g, std::string &err);
+int64_t find_edge(const Graph &g, int32_t a, int32_t b);
+
+struct OrbitResult {
+    std::vector<int32_t> orbit_id;  // per edge: smallest edge index of its orbit
+    int64_t n_orbits = 0;
+    int64_t n_generators = 0;
+    double log10_aut = 0.0;
+    bool complete = true;
+};
+
+// Edge orbits of Aut(G) (or of the verified subgroup found within budget).
+void edge_orbits(const Graph &g, int64_t budget, OrbitResult &out);
+// Every edge its own orbit.
+void trivial_orbits(const Graph &g, OrbitResult &out);
+
+// One representative's reverse causal cone.
+struct Cone {
+    int32_t graph = 0;
+    int64_t edge = 0;     // representative edge index within its graph
+    int32_t weight = 1;   // orbit size
+    int32_t n = 0;        // qubits (ball of radius p)
+    int32_t n_in = 0;     // qubits within distance p-1 (mixed in layer 1)
+    int32_t k[QAOA_MAX_P] = {0};  // layer l mixes local qubits [0, k[l])
+    std::vector<int32_t> verts, dist;
+    std::vector<int32_t> ea, eb;  // local edges (a < b), sorted
+};
+
+// Fills cone for edge `e` of g at depth p.  full_cone: mix every qubit in
+// every layer.  Returns QAOA_OK or QAOA_E_CONE_TOO_LARGE.
+int extract_cone(const Graph &g, int64_t e, int32_t p, bool full_cone, int32_t max_qubits,
+                 std::vector<int32_t> &dist_scratch, Cone &c, std::string &err);
+
+void set_error(const std::string &msg);
+
+}  // namespace qaoa
+
+struct qaoa_device_plan;  // defined in the CUDA translation unit
+
+struct qaoa_plan {
+    int32_t p = 1;
+    uint32_t flags = 0;
+    int32_t n_graphs = 0;
+    std::vector<int32_t> n_vertices;
+    std::vector<int64_t> n_edges;
+    std::vector<qaoa::OrbitResult> orbits;
+    std::vector<qaoa::Cone> cones;  // plan order (rows of terms)
+    double t_orbits = 0.0, t_cones = 0.0;
+    qaoa_device_plan *dev = nullptr;
+};

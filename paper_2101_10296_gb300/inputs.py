@@ -223,3 +223,17 @@ def mixed_benchmark_graphs():
         specs.append((f"C{n}({','.join(map(str, j))})", (lambda n=n, j=j: circulant(n, j))))
     assert len(specs) == 48
     return specs
+
+
+def torus3d(m):
+    """Periodic m x m x m cubic grid (6-regular for m >= 3)."""
+    n = m * m * m
+    e = []
+    for x in range(m):
+        for y in range(m):
+            for z in range(m):
+                v = (x * m + y) * m + z
+                e.append((v, (((x + 1) % m) * m + y) * m + z))
+                e.append((v, (x * m + (y + 1) % m) * m + z))
+                e.append((v, (x * m + y) * m + (z + 1) % m))
+    return n, _normalize(e, n)

@@ -1,0 +1,273 @@
+"""Python binding of libqaoa (include/qaoa.h): argument marshalling only.
+
+Every computation runs in the C++ planner or the CUDA kernels behind the C
+ABI; this module converts arguments, checks shapes, passes raw pointers and
+the current CUDA stream, and raises :class:`QAOAError` on a negative status.
+There is no fallback: if the library has not been built, loading fails.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libqaoa.so")
+
+QAOA_OK = 0
+QAOA_E_INVALID = -1
+QAOA_E_CONE_TOO_LARGE = -2
+QAOA_E_OOM = -3
+QAOA_E_CUDA = -4
+QAOA_E_DEVICE = -5
+
+ORBITS_OFF = 0
+ORBITS = 1
+FULL_CONE = 2
+
+
+class QAOAError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libqaoa error {code}: {msg}")
+        self.code = code
+
+
+class PlanInfo(C.Structure):
+    _fields_ = [
+        ("p", C.c_int32), ("n_graphs", C.c_int32), ("n_edges_total", C.c_int64),
+        ("n_reps", C.c_int64), ("max_qubits", C.c_int32), ("max_inner", C.c_int32),
+        ("max_edges", C.c_int32), ("on_device", C.c_int32), ("n_big", C.c_int64),
+        ("amps_per_point", C.c_double), ("t_orbits_s", C.c_double), ("t_cones_s", C.c_double),
+        ("orbits_complete", C.c_int32),
+    ]
+
+
+_lib = None
+_P = C.c_void_p
+_I32P = C.POINTER(C.c_int32)
+_I64P = C.POINTER(C.c_int64)
+_F64P = C.POINTER(C.c_double)
+
+_SIGS = {
+    "qaoa_plan_graphs": (C.c_int, [C.c_int32, _I32P, _I64P, _I32P, C.c_int32, C.c_uint32, C.c_int32,
+                                   C.c_int64, C.POINTER(_P)]),
+    "qaoa_plan_graph": (C.c_int, [C.c_int32, C.c_int64, _I32P, C.c_int32, C.c_uint32, C.c_int32,
+                                  C.c_int64, C.POINTER(_P)]),
+    "qaoa_plan_free": (None, [_P]),
+    "qaoa_plan_info": (C.c_int, [_P, C.POINTER(PlanInfo)]),
+    "qaoa_plan_orbits": (C.c_int, [_P, C.c_int32, _I32P, _I64P, _F64P, _I32P]),
+    "qaoa_plan_reps": (C.c_int, [_P, _I32P, _I64P, _I32P, _I32P, _I32P, _I32P]),
+    "qaoa_plan_cone": (C.c_int, [_P, C.c_int64, _I32P, _I32P, _I32P]),
+    "qaoa_edge_orbits": (C.c_int, [C.c_int32, C.c_int64, _I32P, C.c_int64, _I32P, _I64P, _I64P, _F64P, _I32P]),
+    "qaoa_plan_upload": (C.c_int, [_P]),
+    "qaoa_cut_table": (C.c_int, [_P, C.c_int64, _P, _P]),
+    "qaoa_energy": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P]),
+    "qaoa_energy_grad": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P, _P]),
+    "qaoa_device_status": (C.c_int, [_P, _I32P]),
+    "qaoa_last_error": (C.c_char_p, []),
+    "qaoa_version": (C.c_char_p, []),
+}
+
+
+def lib():
+    """The loaded libqaoa (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2101_10296_gb300.build.build()")
+        h = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(h, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = h
+    return _lib
+
+
+def _check(code):
+    if code != QAOA_OK:
+        raise QAOAError(code, lib().qaoa_last_error().decode())
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype))
+
+
+def edge_orbits(n, edges, budget=0):
+    """Host-only orbit finder: (orbit_id[m], n_orbits, n_generators, log10|Aut|, complete)."""
+    e = _i32(np.asarray(edges).reshape(-1, 2))
+    m = e.shape[0]
+    oid = np.zeros(m, dtype=np.int32)
+    norb, ngen = C.c_int64(), C.c_int64()
+    l10 = C.c_double()
+    comp = C.c_int32()
+    _check(lib().qaoa_edge_orbits(n, m, _ptr(e, C.c_int32), budget, _ptr(oid, C.c_int32), C.byref(norb),
+                                  C.byref(ngen), C.byref(l10), C.byref(comp)))
+    return oid, norb.value, ngen.value, l10.value, bool(comp.value)
+
+
+def _stream_handle(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+class Plan:
+    """A planned batch of graphs (orbits + cones), owning its device copy."""
+
+    def __init__(self, graphs, p, orbits=True, full_cone=False, max_cone_qubits=0, search_budget=0):
+        if isinstance(graphs, tuple):
+            graphs = [graphs]
+        nv = _i32([g[0] for g in graphs])
+        offs = [0]
+        rows = []
+        for n, e in graphs:
+            e = np.asarray(e, dtype=np.int64).reshape(-1, 2)
+            rows.append(e)
+            offs.append(offs[-1] + e.shape[0])
+        edges = _i32(np.concatenate(rows) if rows else np.zeros((0, 2)))
+        offs = np.asarray(offs, dtype=np.int64)
+        flags = (ORBITS if orbits else ORBITS_OFF) | (FULL_CONE if full_cone else 0)
+        h = C.c_void_p()
+        _check(lib().qaoa_plan_graphs(len(graphs), _ptr(nv, C.c_int32), _ptr(offs, C.c_int64),
+                                      _ptr(edges, C.c_int32) if edges.size else None, p, flags,
+                                      max_cone_qubits, search_budget, C.byref(h)))
+        self._h = h
+        self.p = p
+        self.n_graphs = len(graphs)
+        self.n_edges = [int(r.shape[0]) for r in rows]
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().qaoa_plan_free(self._h)
+            self._h = C.c_void_p()
+
+    __del__ = close
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self):
+        i = PlanInfo()
+        _check(lib().qaoa_plan_info(self._h, C.byref(i)))
+        return {k: getattr(i, k) for k, _ in PlanInfo._fields_}
+
+    def orbits(self, graph=0):
+        oid = np.zeros(self.n_edges[graph], dtype=np.int32)
+        norb = C.c_int64()
+        l10 = C.c_double()
+        comp = C.c_int32()
+        _check(lib().qaoa_plan_orbits(self._h, graph, _ptr(oid, C.c_int32), C.byref(norb), C.byref(l10),
+                                      C.byref(comp)))
+        return oid, norb.value, l10.value, bool(comp.value)
+
+    def reps(self):
+        r = self.info()["n_reps"]
+        out = {k: np.zeros(r, dtype=np.int32) for k in ("graph", "weight", "n_qubits", "n_inner", "n_cone_edges")}
+        edge = np.zeros(r, dtype=np.int64)
+        _check(lib().qaoa_plan_reps(self._h, _ptr(out["graph"], C.c_int32), _ptr(edge, C.c_int64),
+                                    _ptr(out["weight"], C.c_int32), _ptr(out["n_qubits"], C.c_int32),
+                                    _ptr(out["n_inner"], C.c_int32), _ptr(out["n_cone_edges"], C.c_int32)))
+        out["edge"] = edge
+        return out
+
+    def cone(self, rep):
+        reps = self.reps()
+        nq = int(reps["n_qubits"][rep])
+        ne = int(reps["n_cone_edges"][rep])
+        verts = np.zeros(nq, dtype=np.int32)
+        dist = np.zeros(nq, dtype=np.int32)
+        ce = np.zeros((max(ne, 1), 2), dtype=np.int32)
+        _check(lib().qaoa_plan_cone(self._h, rep, _ptr(verts, C.c_int32), _ptr(dist, C.c_int32),
+                                    _ptr(ce, C.c_int32)))
+        return verts, dist, ce[:ne]
+
+    def upload(self):
+        _check(lib().qaoa_plan_upload(self._h))
+
+    def cut_table(self, rep, stream=None):
+        import torch
+        nq = int(self.reps()["n_qubits"][rep])
+        out = torch.empty(1 << nq, dtype=torch.uint8, device="cuda")
+        _check(lib().qaoa_cut_table(self._h, rep, C.c_void_p(out.data_ptr()), _stream_handle(stream)))
+        return out
+
+    def _params(self, params):
+        import torch
+        if not (isinstance(params, torch.Tensor) and params.is_cuda and params.dtype == torch.float64):
+            raise TypeError("params must be a CUDA float64 tensor")
+        if params.dim() == 2:
+            params = params.unsqueeze(0)
+        if params.dim() != 3 or params.shape[0] != self.n_graphs or params.shape[2] != 2 * self.p:
+            raise ValueError(f"params must have shape [{self.n_graphs}, P, {2 * self.p}]")
+        return params.contiguous()
+
+    def energy(self, params, terms=False, stream=None):
+        """E[g, j] for params [G, P, 2p] (CUDA float64); optionally <ZZ> per rep."""
+        import torch
+        params = self._params(params)
+        G, P = params.shape[0], params.shape[1]
+        e = torch.empty(G, P, dtype=torch.float64, device=params.device)
+        t = torch.empty(self.info()["n_reps"], P, dtype=torch.float64, device=params.device) if terms else None
+        _check(lib().qaoa_energy(self._h, P, C.c_void_p(params.data_ptr()), C.c_void_p(e.data_ptr()),
+                                 C.c_void_p(t.data_ptr()) if terms else None, _stream_handle(stream)))
+        return (e, t) if terms else e
+
+    def energy_grad(self, params, terms=False, stream=None):
+        """(E[g, j], dE/dtheta[g, j, 2p]) by the adjoint kernels."""
+        import torch
+        params = self._params(params)
+        G, P = params.shape[0], params.shape[1]
+        e = torch.empty(G, P, dtype=torch.float64, device=params.device)
+        g = torch.empty(G, P, 2 * self.p, dtype=torch.float64, device=params.device)
+        t = torch.empty(self.info()["n_reps"], P, dtype=torch.float64, device=params.device) if terms else None
+        _check(lib().qaoa_energy_grad(self._h, P, C.c_void_p(params.data_ptr()), C.c_void_p(e.data_ptr()),
+                                      C.c_void_p(g.data_ptr()), C.c_void_p(t.data_ptr()) if terms else None,
+                                      _stream_handle(stream)))
+        return (e, g, t) if terms else (e, g)
+
+    def device_status(self):
+        s = C.c_int32()
+        _check(lib().qaoa_device_status(self._h, C.byref(s)))
+        return s.value
+
+
+def _autograd_cls():
+    import torch
+
+    class QAOAEnergy(torch.autograd.Function):
+        """E(theta) with dE/dtheta from the adjoint kernels (one launch does both)."""
+
+        @staticmethod
+        def forward(ctx, params, plan):
+            ctx.shape = params.shape
+            if params.requires_grad:
+                e, g = plan.energy_grad(params.detach())
+                ctx.save_for_backward(g)
+            else:
+                e = plan.energy(params.detach())
+            return e
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            (g,) = ctx.saved_tensors
+            return (grad_out.reshape(g.shape[:-1]).unsqueeze(-1) * g).reshape(ctx.shape), None
+
+    return QAOAEnergy
+
+
+_QAOAEnergy = None
+
+
+def qaoa_energy(params, plan):
+    """Differentiable E(params) for ``plan`` (params: CUDA float64 [G, P, 2p])."""
+    global _QAOAEnergy
+    if _QAOAEnergy is None:
+        _QAOAEnergy = _autograd_cls()
+    return _QAOAEnergy.apply(params, plan)

@@ -11,3 +11,13 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built extension")
     config.addinivalue_line("markers", "slow: longer CPU test")
+
+
+@pytest.fixture(scope="session")
+def qlib():
+    """The built libqaoa binding (compiled in-tree if missing or stale)."""
+    from paper_2101_10296_gb300 import build
+    build.build()
+    from paper_2101_10296_gb300 import qaoa
+    qaoa.lib()
+    return qaoa

@@ -1,0 +1,269 @@
+"""Host planner through the C ABI (no GPU): edge orbits and reverse causal cones.
+
+Orbits are checked against the oracle's brute-force enumeration and against
+textbook group orders and the paper's printed orbit counts; cones against the
+oracle's own BFS lightcone.
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import qaoa_oracle as O
+from paper_2101_10296_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "paper_orbit_counts.txt")
+
+
+def _canon(labels):
+    """Relabel a partition by order of first occurrence."""
+    seen = {}
+    return np.array([seen.setdefault(int(x), len(seen)) for x in labels])
+
+
+# ------------------------------------------------------------ vs brute force
+
+def test_orbits_match_brute_force_all_graphs_on_5_vertices(qlib):
+    pairs = list(itertools.combinations(range(5), 2))
+    for mask in range(1, 1 << len(pairs)):
+        edges = np.array([pairs[i] for i in range(len(pairs)) if mask >> i & 1])
+        oid, norb, _, l10, comp = qlib.edge_orbits(5, edges)
+        ref = O.brute_edge_orbits(5, edges)
+        assert comp
+        assert np.array_equal(_canon(oid), _canon(ref)), edges
+        assert norb == len(np.unique(ref))
+        assert abs(10 ** l10 - len(O.brute_automorphisms(5, edges))) < 1e-6 * 10 ** l10
+
+
+@pytest.mark.parametrize("n,q,count", [(7, 0.3, 60), (8, 0.5, 40), (9, 0.35, 30), (10, 0.3, 12)])
+def test_orbits_match_brute_force_random_graphs(qlib, n, q, count):
+    rng = np.random.default_rng(n)
+    for _ in range(count):
+        _, edges = I.erdos_renyi(n, q, int(rng.integers(1 << 30)))
+        if len(edges) == 0:
+            continue
+        oid, norb, _, l10, comp = qlib.edge_orbits(n, edges)
+        ref = O.brute_edge_orbits(n, edges)
+        assert comp
+        assert np.array_equal(_canon(oid), _canon(ref))
+        assert abs(10 ** l10 / len(O.brute_automorphisms(n, edges)) - 1) < 1e-9
+
+
+@pytest.mark.parametrize("graph", [I.petersen(), I.wheel(6), I.hypercube(3), I.circulant(10, [1, 3]),
+                                   I.complete_bipartite(3, 4), I.random_regular(10, 3, 5)])
+def test_orbits_match_brute_force_families(qlib, graph):
+    n, edges = graph
+    oid, _, _, _, _ = qlib.edge_orbits(n, edges)
+    assert np.array_equal(_canon(oid), _canon(O.brute_edge_orbits(n, edges)))
+
+
+def test_orbit_id_is_smallest_edge_of_orbit(qlib):
+    n, edges = I.circulant(12, [1, 5])
+    oid, *_ = qlib.edge_orbits(n, edges)
+    for i, r in enumerate(oid):
+        assert r <= i and oid[r] == r
+
+
+# ----------------------------------------------------- textbook group orders
+
+def _log10_fact(k):
+    return math.lgamma(k + 1) / math.log(10)
+
+
+@pytest.mark.parametrize("name,graph,log10_order,n_orb", [
+    ("K12", I.complete(12), _log10_fact(12), 1),
+    ("C31", I.cycle(31), math.log10(62), 1),
+    ("Q6", I.hypercube(6), 6 * math.log10(2) + _log10_fact(6), 1),
+    ("Q10", I.hypercube(10), 10 * math.log10(2) + _log10_fact(10), 1),
+    ("petersen", I.petersen(), math.log10(120), 1),
+    ("torus7x7", I.torus(7, 7), math.log10(8 * 49), 1),
+    ("torus5x7", I.torus(5, 7), math.log10(4 * 35), 2),
+    ("torus3d-5", I.torus3d(5), math.log10(48 * 125), 1),
+    ("paley13", I.paley(13), math.log10(13 * 12 / 2), 1),
+    ("paley29", I.paley(29), math.log10(29 * 28 / 2), 1),
+    ("rook6", I.rook(6), math.log10(2) + 2 * _log10_fact(6), 1),
+    ("star9", I.star(9), _log10_fact(9), 1),
+    ("K34", I.complete_bipartite(3, 4), _log10_fact(3) + _log10_fact(4), 1),
+    ("P9", I.path(9), math.log10(2), 4),
+])
+def test_group_order_and_orbit_count(qlib, name, graph, log10_order, n_orb):
+    n, edges = graph
+    oid, norb, ngen, l10, comp = qlib.edge_orbits(n, edges)
+    assert comp
+    assert norb == n_orb
+    assert abs(l10 - log10_order) < 1e-9
+
+
+def _golden_rows():
+    rows = []
+    for line in open(GOLDEN):
+        line = line.split("#", 1)[0].strip()
+        if line:
+            name, m, n, norb = line.split()[:4]
+            rows.append((name, int(m), int(n), int(norb)))
+    return rows
+
+
+def _family(name):
+    if name.startswith("k-"):
+        return I.complete(int(name[2:]))
+    if name.startswith("paley-"):
+        return I.paley(int(name[6:]))
+    if name.startswith("lattice-"):
+        return I.rook(int(name[8:]))
+    if name.startswith("grid-w-2-"):
+        m = int(name[9:])
+        return I.torus(m, m)
+    if name.startswith("grid-w-3-"):
+        return I.torus3d(int(name[9:]))
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("row", _golden_rows(), ids=lambda r: r[0])
+def test_paper_printed_orbit_counts(qlib, row):
+    name, m, n, norb_paper = row
+    nv, edges = _family(name)
+    assert (nv, len(edges)) == (n, m)
+    _, norb, _, _, comp = qlib.edge_orbits(nv, edges)
+    assert comp and norb == norb_paper
+
+
+@pytest.mark.parametrize("graph,n_orb", [
+    (I.circulant(20, [1, 4]), 2),
+    (I.circulant(5000, [1, 7, 23]), 3),
+    (I.circulant(5000, [1, 7]), 2),
+    (I.torus(100, 100), 1),
+    (I.torus(50, 200), 2),
+    (I.hypercube(12), 1),
+])
+def test_benchmark_family_orbit_counts(qlib, graph, n_orb):
+    n, edges = graph
+    _, norb, _, _, comp = qlib.edge_orbits(n, edges)
+    assert comp and norb == n_orb
+
+
+def test_c20_orbits_match_brute_force(qlib):
+    n, edges = I.circulant(20, [1, 4])
+    oid, *_ = qlib.edge_orbits(n, edges)
+    assert np.array_equal(_canon(oid), _canon(O.brute_edge_orbits(n, edges)))
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4])
+def test_random_3_regular_are_asymmetric(qlib, seed):
+    # Sec. 2.6: random 3-regular graphs almost surely have no automorphism
+    n, edges = I.random_regular(2000, 3, seed)
+    _, norb, _, l10, comp = qlib.edge_orbits(n, edges)
+    assert comp and norb == len(edges) and l10 == 0.0
+
+
+def test_budget_fallback_gives_sub_orbits(qlib):
+    n, edges = I.rook(7)
+    oid_small, norb_small, _, _, comp = qlib.edge_orbits(n, edges, budget=3)
+    assert not comp
+    oid_full, norb_full, *_ = qlib.edge_orbits(n, edges)
+    assert norb_full == 1 and norb_small >= norb_full
+    # every orbit of the subgroup lies inside an orbit of the full group
+    for r in np.unique(oid_small):
+        assert len(np.unique(oid_full[oid_small == r])) == 1
+
+
+# ---------------------------------------------------------------- cones
+
+@pytest.mark.parametrize("graph,p", [
+    (I.petersen(), 1), (I.petersen(), 2), (I.random_regular(40, 3, 3), 2), (I.random_regular(24, 3, 1), 3),
+    (I.torus(8, 8), 2), (I.erdos_renyi(60, 0.07, 2), 1), (I.hypercube(5), 1), (I.circulant(30, [1, 4]), 2),
+])
+def test_cones_match_oracle_lightcone(qlib, graph, p):
+    n, edges = graph
+    plan = qlib.Plan((n, edges), p, orbits=False)
+    reps = plan.reps()
+    assert len(reps["edge"]) == len(edges)
+    adj = O.adjacency(n, edges)
+    for r in range(0, len(edges), max(1, len(edges) // 25)):
+        verts, dist, ce = plan.cone(r)
+        e = edges[reps["edge"][r]]
+        ov, od, oe = O.lightcone(n, edges, e, p, adj)
+        assert list(verts) == ov and list(dist) == od
+        # cone terms: induced edges with an endpoint within distance p-1
+        keep = sorted((min(a, b), max(a, b)) for a, b in oe.tolist() if min(od[a], od[b]) <= p - 1)
+        assert [tuple(x) for x in ce.tolist()] == keep
+        assert reps["n_inner"][r] == sum(d <= p - 1 for d in od)
+        assert reps["n_qubits"][r] == len(ov)
+
+
+def test_full_cone_flag_marks_every_qubit_inner(qlib):
+    n, edges = I.random_regular(30, 3, 2)
+    plan = qlib.Plan((n, edges), 2, orbits=False, full_cone=True)
+    reps = plan.reps()
+    assert np.array_equal(reps["n_inner"], reps["n_qubits"])
+
+
+def test_multi_graph_plan_weights_sum_to_edges(qlib):
+    gs = [I.circulant(20, [1, 4]), I.torus(6, 6), I.random_regular(30, 3, 1), I.petersen()]
+    plan = qlib.Plan(gs, 1)
+    reps = plan.reps()
+    info = plan.info()
+    assert info["n_graphs"] == 4 and info["n_edges_total"] == sum(len(e) for _, e in gs)
+    for g, (_, e) in enumerate(gs):
+        assert reps["weight"][reps["graph"] == g].sum() == len(e)
+    assert info["n_reps"] == sum(qlib.edge_orbits(n, e)[1] for n, e in gs)
+    for g, (n, e) in enumerate(gs):
+        assert np.array_equal(plan.orbits(g)[0], qlib.edge_orbits(n, e)[0])
+    assert info["orbits_complete"] == 1
+
+
+def test_orbits_off_every_edge_is_a_rep(qlib):
+    n, edges = I.torus(6, 6)
+    plan = qlib.Plan((n, edges), 1, orbits=False)
+    reps = plan.reps()
+    assert np.array_equal(reps["edge"], np.arange(len(edges))) and np.all(reps["weight"] == 1)
+
+
+def test_empty_and_isolated_graphs(qlib):
+    plan = qlib.Plan((6, np.zeros((0, 2), dtype=np.int32)), 2)
+    assert plan.info()["n_reps"] == 0
+    plan = qlib.Plan((9, np.array([[0, 1], [2, 3]])), 2)  # isolated vertices 4..8
+    reps = plan.reps()
+    assert plan.info()["n_reps"] == 1 and reps["weight"][0] == 2 and reps["n_qubits"][0] == 2
+
+
+# ----------------------------------------------------------- error paths
+
+@pytest.mark.parametrize("n,edges,p,msg", [
+    (4, [[0, 0]], 1, "self-loop"),
+    (4, [[0, 1], [1, 0]], 1, "repeated"),
+    (4, [[0, 4]], 1, "outside"),
+    (4, [[0, 1]], 0, "p must"),
+    (4, [[0, 1]], 9, "p must"),
+])
+def test_invalid_inputs_are_rejected(qlib, n, edges, p, msg):
+    with pytest.raises(qlib.QAOAError) as ei:
+        qlib.Plan((n, np.array(edges)), p)
+    assert ei.value.code == qlib.QAOA_E_INVALID and msg in str(ei.value)
+
+
+def test_cone_caps(qlib):
+    n, edges = I.random_regular(200, 3, 1)
+    with pytest.raises(qlib.QAOAError) as ei:
+        qlib.Plan((n, edges), 3, max_cone_qubits=20)
+    assert ei.value.code == qlib.QAOA_E_CONE_TOO_LARGE
+    n, edges = I.complete(40)  # p = 1 cone of K_40 has 2*38+1 = 77 edges > 64
+    with pytest.raises(qlib.QAOAError) as ei:
+        qlib.Plan((n, edges), 1)
+    assert ei.value.code == qlib.QAOA_E_CONE_TOO_LARGE
+
+
+def test_bad_call_arguments(qlib):
+    import ctypes as C
+    h = C.c_void_p()
+    nv = np.array([3], dtype=np.int32)
+    offs = np.array([1, 2], dtype=np.int64)
+    e = np.array([[0, 1]], dtype=np.int32)
+    rc = qlib.lib().qaoa_plan_graphs(1, qlib._ptr(nv, C.c_int32), qlib._ptr(offs, C.c_int64),
+                                     qlib._ptr(e, C.c_int32), 1, 1, 0, 0, C.byref(h))
+    assert rc == qlib.QAOA_E_INVALID
+    assert qlib.lib().qaoa_plan_graph(3, 1, qlib._ptr(e, C.c_int32), 1, 1, 0, 0, None) == qlib.QAOA_E_INVALID
+    assert qlib.lib().qaoa_plan_info(None, None) == qlib.QAOA_E_INVALID
+    assert qlib.lib().qaoa_energy(None, 1, None, None, None, None) == qlib.QAOA_E_INVALID
