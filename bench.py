@@ -1,0 +1,469 @@
+#!/usr/bin/env python3
+"""Benchmark: QAOA MaxCut energy + adjoint gradient evaluations per second.
+
+Workload (one step): 4 random 3-regular graphs with n = 2000 (3000 edges,
+seeds 1-4), depth p = 2, 64 parameter points per graph drawn with the
+project's recipe, orbit reduction on, energies and gradients of all
+4 x 64 = 256 (graph, point) evaluations in one launch of the adjoint cone
+kernel.  The inputs are synthetic, shaped like the asymmetric random graphs of
+the paper's benchmark (Sec. 5).
+
+Timing: W untimed warm-up steps, then K steps each bracketed by CUDA events on
+the launching stream, with a 512 MB L2 flush written between steps outside the
+events; barrier + synchronize on both sides; max over ranks.  With N > 1 every
+rank runs its own replica (the path shards into independent problems; there
+is no data-path collective), so the whole-job value is N x per-rank evals.
+
+``--impl reference`` times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "QAOA energy+grad evals/s on 1 GB300, orbit-reduced batched vs plain all-edge"
+UNIT = "evals/s"
+WORKLOAD = "rr3-n2000x4-p2-P64: 4 random 3-regular graphs n=2000 (seeds 1-4), p=2, 64 points each, energy+grad"
+SEEDS = (1, 2, 3, 4)
+N_VERT, DEG, P_DEPTH, N_POINTS = 2000, 3, 2, 64
+
+# DRAM bytes per launch of the adjoint cone kernel from one ncu capture of this
+# workload, with the hash of the kernel source they were taken on (a changed
+# kernel reports null until it is profiled again).
+TRAFFIC = {"kernels_sha1": None, "bytes_per_launch": None}
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def workload():
+    from paper_2101_10296_gb300 import inputs as I
+    graphs = [I.random_regular(N_VERT, DEG, s) for s in SEEDS]
+    theta = np.stack([I.draw_params(P_DEPTH, N_POINTS, s) for s in SEEDS])
+    return graphs, theta
+
+
+# ------------------------------------------------------------------ roofline
+
+def algorithmic_flops(reps, p, grad):
+    """FP32 FLOPs of the pruned state-vector circuit per point, summed over reps.
+
+    Per cone with A = 2^n amplitudes and k_l qubits mixed in layer l
+    (FMA = 2 FLOPs): forward = A (6 (p-1) + 6 sum_l k_l + 4) -- phase
+    complex multiply 6 per amplitude from layer 2 on (layer 1 is a table
+    read), RX butterfly 6 per amplitude per mixed qubit, |psi|^2 and the
+    signed accumulation 4; adjoint adds A (2 + 16 sum_l k_l + 5 p + 12 (p-1))
+    -- co-state 2, per mixed qubit the Im<lam|X|psi> term 4 and undoing RX
+    on both states 12, per layer the Im<lam|C|psi> term 5, undoing the phase
+    on both states 12.
+    """
+    A = np.ldexp(1.0, reps["n_qubits"].astype(np.int64))
+    ksum = reps["mix_qubits"][:, :p].sum(axis=1).astype(np.float64)
+    fwd = A * (6 * (p - 1) + 6 * ksum + 4)
+    if grad:
+        fwd = fwd + A * (2 + 16 * ksum + 5 * p + 12 * (p - 1))
+    return float(fwd.sum())
+
+
+def fp32_peak_tflops():
+    """152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x the maximum SM clock."""
+    mhz = 2070.0
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            mhz = float(json.load(open(path)).get("sm_max_mhz", mhz))
+        except Exception:
+            pass
+    return 152 * 128 * 2 * mhz * 1e6 / 1e12, mhz
+
+
+def kernels_sha1():
+    h = hashlib.sha1()
+    for f in ("kernels.cu", "device.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2101_10296_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+# -------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------- CPU oracle
+
+_W = {}
+
+
+def _init_oracle_worker():
+    """Pool initializer: each worker rebuilds the seeded graphs once."""
+    from oracle import qaoa_oracle as O
+    graphs, theta = workload()
+    _W["graphs"] = graphs
+    _W["theta"] = theta
+    _W["adj"] = [O.adjacency(n, e) for n, e in graphs]
+
+
+def _oracle_term_job(job):
+    from oracle import qaoa_oracle as O
+    g, ei, j = job
+    n, edges = _W["graphs"][g]
+    verts, _, ledges = O.lightcone(n, edges, edges[ei], P_DEPTH, _W["adj"][g])
+    return O.term_grad_adjoint(len(verts), ledges, _W["theta"][g, j], P_DEPTH)
+
+
+def make_oracle_pool(cores):
+    """One single-threaded oracle process per host core (spawned, so it is safe
+    to create after CUDA is initialised)."""
+    import multiprocessing as mp
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+    return mp.get_context("spawn").Pool(cores, initializer=_init_oracle_worker)
+
+
+def oracle_sample(target_s=15.0, pool=None, seed=0):
+    """Times the FP64 oracle (per-edge cone energy + adjoint gradient) on a
+    random sample of (graph, edge) terms at point 0, sized to about target_s
+    of wall time; returns (evals/s extrapolated to whole (graph, point) evals,
+    processes, seconds, terms)."""
+    rng = np.random.default_rng(seed)
+    cores = os.cpu_count() or 1
+    own = pool is None
+    if own:
+        pool = make_oracle_pool(cores)
+    try:
+        probe = [(0, k, 0) for k in range(cores)]
+        pool.map(_oracle_term_job, probe, chunksize=1)  # warms the workers
+        t0 = time.perf_counter()
+        pool.map(_oracle_term_job, probe, chunksize=1)
+        t_one = (time.perf_counter() - t0)  # ~ one term per process
+        n_terms = int(max(cores, min(50000, 0.8 * target_s / max(t_one, 1e-4) * cores)))
+        jobs = [(int(rng.integers(len(SEEDS))), int(rng.integers(N_VERT * DEG // 2)), 0) for _ in range(n_terms)]
+        t0 = time.perf_counter()
+        pool.map(_oracle_term_job, jobs, chunksize=max(1, n_terms // (8 * cores)))
+        dt = time.perf_counter() - t0
+    finally:
+        if own:
+            pool.close()
+            pool.join()
+    terms_per_eval = N_VERT * DEG // 2  # random 3-regular: trivial Aut, one cone per edge
+    return n_terms / dt / terms_per_eval, cores, dt, n_terms
+
+
+def max_over_ranks(x, dist, device):
+    """Max of a float over all ranks (identity without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world, evals_per_rank, ms_per_step):
+    """Evals/s of the whole job: every rank processes its own evals in parallel."""
+    return world * evals_per_rank / (ms_per_step / 1e3)
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2101_10296_gb300 import qaoa
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    device = torch.device("cuda", local_rank)
+    torch.cuda.set_device(device)
+    graphs, theta = workload()
+    G, P, p = len(graphs), N_POINTS, P_DEPTH
+    evals = G * P
+
+    pool = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        pool = make_oracle_pool(os.cpu_count() or 1)  # spawned before the first GPU call
+
+    t0 = time.perf_counter()
+    plan = qaoa.Plan(graphs, p, orbits=True)
+    t_plan = time.perf_counter() - t0
+    plan.upload()
+    info = plan.info()
+    reps = plan.reps()
+    params = torch.tensor(theta, device=device)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=device)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        return plan.energy_grad(params)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    plan.set_timing(True)
+    plan.kernel_time()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            starts[k].record(stream)
+            step()
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    clocks = clk.summary()
+    if dist:
+        dist.barrier()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    kern_ms, kern_launches, all_launches = plan.kernel_time()
+    plan.set_timing(False)
+    ms_per_step = max_over_ranks(sum(step_ms) / len(step_ms), dist, device)
+    value = whole_job_value(world, evals, ms_per_step)
+
+    # e2e: public API with host buffers, copies inside the timed region
+    host_params = torch.tensor(theta).pin_memory()
+    host_e = torch.empty(G, P, dtype=torch.float64).pin_memory()
+    host_g = torch.empty(G, P, 2 * p, dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    for k in range(args.warmup + args.steps):
+        flush.fill_(k & 0xFF)
+        s_ev, e_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s_ev.record(stream)
+        dev_p = host_params.to(device, non_blocking=True)
+        e_dev, g_dev = plan.energy_grad(dev_p)
+        host_e.copy_(e_dev, non_blocking=True)
+        host_g.copy_(g_dev, non_blocking=True)
+        e_ev.record(stream)
+        e_ev.synchronize()
+        if k >= args.warmup:
+            e2e_ms.append(s_ev.elapsed_time(e_ev))
+    e2e_step = max_over_ranks(sum(e2e_ms) / len(e2e_ms), dist, device)
+
+    # energy-only and plain all-edge comparisons (same kernels, not the headline)
+    def timed(fn, reps_=5):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        out = []
+        for k in range(reps_):
+            flush.fill_(k & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            out.append(a.elapsed_time(b))
+        return sum(out) / len(out)
+
+    energy_ms = timed(lambda: plan.energy(params))
+    plain = qaoa.Plan(graphs, p, orbits=False)
+    plain.upload()
+    plain_ms = timed(lambda: plain.energy_grad(params))
+
+    # roofline of the dominant kernel (the adjoint cone kernel)
+    flops = algorithmic_flops(reps, p, grad=True) * P
+    kern_avg_ms = kern_ms / max(kern_launches, 1)
+    achieved = flops / (kern_avg_ms / 1e3) / 1e12
+    peak, mhz = fp32_peak_tflops()
+    traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["kernels_sha1"] == kernels_sha1() else None
+    amp_updates = float((np.ldexp(1.0, reps["n_qubits"].astype(np.int64)) * p).sum()) * P
+
+    status = plan.device_status()
+    if rank != 0:
+        return None
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_per_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {
+            "workload": WORKLOAD,
+            "graphs": G, "n": N_VERT, "degree": DEG, "p": p, "points_per_graph": P,
+            "orbit_reduction": True, "n_reps": int(info["n_reps"]), "max_cone_qubits": int(info["max_qubits"]),
+            "max_inner_qubits": int(info["max_inner"]),
+            "l2": "512 MB buffer written between timed steps (outside the events)",
+            "parallelism": f"replicas x{world}",
+        },
+        "roofline": {
+            "bound": "alu",
+            "kernel": "reg_cone_kernel<5,true> (adjoint)",
+            "achieved": achieved,
+            "peak": peak,
+            "unit": "TFLOP/s",
+            "frac": achieved / peak,
+            "traffic": traffic,
+            "algorithmic_flops_per_launch": flops,
+            "kernel_ms_per_launch": kern_avg_ms,
+            "peak_basis": f"FP32: 152 SMs x 128 lanes x 2 FLOP x {mhz:.0f} MHz (max SM clock)",
+        },
+        "e2e": {"value": whole_job_value(world, evals, e2e_step), "unit": UNIT,
+                "h2d_bytes_per_step": int(theta.nbytes), "d2h_bytes_per_step": int(G * P * (1 + 2 * p) * 8)},
+        "gpu_launches": int(all_launches),
+        "clocks": clocks,
+        "energy_only_evals_per_s": world * evals / (energy_ms / 1e3),
+        "plain_all_edge_evals_per_s": world * evals / (plain_ms / 1e3),
+        "amp_updates_per_s": world * amp_updates / (ms_per_step / 1e3),
+        "plan_s": t_plan,
+        "t_orbits_s": info["t_orbits_s"],
+        "wall_s_timed_region": wall,
+        "device_status": status,
+    }
+    if pool is not None:
+        try:
+            v, cores, dt, nt = oracle_sample(target_s=args.cpu_seconds, pool=pool)
+            out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                   "sample": f"{nt} random (graph, edge) cone terms at point 0, FP64 energy + "
+                                             f"adjoint gradient, {dt:.1f} s on {cores} processes, "
+                                             f"scaled to whole evals of 3000 terms"}
+        finally:
+            pool.close()
+            pool.join()
+    return out
+
+
+def run_reference(args, rank, world):
+    """The FP64 CPU oracle on the host cores, as the reference arm."""
+    if rank != 0:
+        return None
+    cores = os.cpu_count() or 1
+    pool = make_oracle_pool(cores)
+    try:
+        budget = max(5.0, min(30.0, 150.0 / max(args.steps + args.warmup, 1)))
+        vals = []
+        samples = []
+        for k in range(args.warmup + args.steps):
+            v, c, dt, nt = oracle_sample(target_s=budget, pool=pool, seed=k)
+            if k >= args.warmup:
+                vals.append(v)
+                samples.append(nt)
+    finally:
+        pool.close()
+        pool.join()
+    value = statistics.mean(vals)
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * G_P_EVALS / value if value else None,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "impl": "reference",
+        "config": {"workload": WORKLOAD, "graphs": 4, "n": N_VERT, "degree": DEG, "p": P_DEPTH,
+                   "points_per_graph": N_POINTS, "orbit_reduction": True,
+                   "parallelism": f"{cores} host processes"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"per step {statistics.mean(samples):.0f} random cone terms at point 0 "
+                                   f"(FP64 energy + adjoint gradient), scaled to whole evals of 3000 terms"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+G_P_EVALS = len(SEEDS) * N_POINTS
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        log("warning: fewer than 3 warm-up steps")
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        if world > 1:
+            import torch
+            import torch.distributed as dist
+            torch.cuda.set_device(local_rank)
+            dist.init_process_group("nccl")
+        out = run_ours(args, rank, world, local_rank)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -142,10 +142,13 @@ int qaoa_plan_orbits(const qaoa_plan *plan, int32_t graph, int32_t *orbit_id,
 /*
  * Representatives, in plan order (the row order of terms_dev).  Each array
  * is host memory of length n_reps and may be NULL.  weight = orbit size.
+ * mix_qubits (host int32[n_reps][p], may be NULL): qubits mixed in each
+ * layer -- the local qubits within distance p-l of the edge for layer l
+ * (all n_qubits with QAOA_FULL_CONE).
  */
 int qaoa_plan_reps(const qaoa_plan *plan, int32_t *graph, int64_t *edge,
                    int32_t *weight, int32_t *n_qubits, int32_t *n_inner,
-                   int32_t *n_cone_edges);
+                   int32_t *n_cone_edges, int32_t *mix_qubits);
 
 /*
  * One representative's cone.  verts: host int32[n_qubits] global vertex of
@@ -216,6 +219,18 @@ int qaoa_energy_grad(const qaoa_plan *plan, int64_t n_points,
  * nonzero code (1: descriptor out of range, 2: non-finite result).
  */
 int qaoa_device_status(const qaoa_plan *plan, int32_t *status);
+
+/*
+ * Kernel timing, for measurement.  With enable != 0 every later energy or
+ * gradient call records a pair of CUDA events on its own stream around each
+ * of its cone kernels (the FP64 phase-table kernel that precedes them is not
+ * included).  qaoa_kernel_time waits for those events, returns the summed
+ * kernel milliseconds in *ms, the number of cone-kernel launches timed in
+ * *launches and the number of all kernel launches made by those calls in
+ * *all_launches (any of the three may be NULL), and forgets them.
+ */
+int qaoa_plan_timing(qaoa_plan *plan, int32_t enable);
+int qaoa_kernel_time(qaoa_plan *plan, double *ms, int64_t *launches, int64_t *all_launches);
 
 /* Last error message of the calling thread ("" if none). */
 const char *qaoa_last_error(void);

@@ -29,6 +29,9 @@ struct qaoa_device_plan {
     int32_t *status = nullptr;
     int32_t cmax1 = 1;
     int64_t n_big = 0;
+    bool timing = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
+    int64_t all_launches = 0;
 };
 
 namespace {
@@ -139,6 +142,14 @@ int run(const qaoa_plan *plan, int64_t n_points, const double *params, double *e
     pa.terms = terms;
     pa.n_reps = d->n_cones;
     e = launch_prep(pa, s);
+    qaoa_device_plan *dm = const_cast<qaoa_device_plan *>(d);
+    dm->all_launches += 1;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (d->timing && e == cudaSuccess) {
+        cudaEventCreate(&ev0);
+        cudaEventCreate(&ev1);
+        cudaEventRecord(ev0, s);
+    }
     if (e == cudaSuccess) {
         RegLaunch L;
         L.n_points = n_points;
@@ -163,6 +174,11 @@ int run(const qaoa_plan *plan, int64_t n_points, const double *params, double *e
                 e = launch_reg_energy(L, int(std::max<int64_t>(grid, 1)), s);
             }
         }
+        if (L.work.warps > 0) dm->all_launches += 1;
+    }
+    if (ev0) {
+        cudaEventRecord(ev1, s);
+        dm->events.emplace_back(ev0, ev1);
     }
     cudaFreeAsync(mix, s);
     cudaFreeAsync(lut, s);
@@ -183,6 +199,10 @@ extern "C" void qaoa_device_release(qaoa_plan *plan) {
     free_work(d->reg5);
     cudaFree(d->half_edges);
     cudaFree(d->status);
+    for (auto &pr : d->events) {
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
     if (cur >= 0) cudaSetDevice(cur);
     delete d;
     plan->dev = nullptr;
@@ -330,5 +350,45 @@ extern "C" int qaoa_device_status(const qaoa_plan *plan, int32_t *status) {
         return cuda_fail(e, "cudaMemcpy");
     cudaMemset(plan->dev->status, 0, sizeof(int32_t));
     *status = v;
+    return QAOA_OK;
+}
+
+extern "C" int qaoa_plan_timing(qaoa_plan *plan, int32_t enable) {
+    if (!plan) {
+        set_error("plan is NULL");
+        return QAOA_E_INVALID;
+    }
+    int rc = ensure_uploaded(plan);
+    if (rc != QAOA_OK) return rc;
+    plan->dev->timing = enable != 0;
+    return QAOA_OK;
+}
+
+extern "C" int qaoa_kernel_time(qaoa_plan *plan, double *ms, int64_t *launches, int64_t *all_launches) {
+    if (!plan) {
+        set_error("plan is NULL");
+        return QAOA_E_INVALID;
+    }
+    double total = 0.0;
+    int64_t count = 0, all = 0;
+    if (plan->dev) {
+        qaoa_device_plan *d = plan->dev;
+        for (auto &pr : d->events) {
+            cudaError_t e = cudaEventSynchronize(pr.second);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+            float t = 0.f;
+            cudaEventElapsedTime(&t, pr.first, pr.second);
+            total += t;
+            ++count;
+            cudaEventDestroy(pr.first);
+            cudaEventDestroy(pr.second);
+        }
+        d->events.clear();
+        all = d->all_launches;
+        d->all_launches = 0;
+    }
+    if (ms) *ms = total;
+    if (launches) *launches = count;
+    if (all_launches) *all_launches = all;
     return QAOA_OK;
 }

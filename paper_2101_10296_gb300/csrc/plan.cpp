@@ -296,7 +296,8 @@ extern "C" int qaoa_plan_orbits(const qaoa_plan *plan, int32_t graph, int32_t *o
 }
 
 extern "C" int qaoa_plan_reps(const qaoa_plan *plan, int32_t *graph, int64_t *edge, int32_t *weight,
-                              int32_t *n_qubits, int32_t *n_inner, int32_t *n_cone_edges) {
+                              int32_t *n_qubits, int32_t *n_inner, int32_t *n_cone_edges,
+                              int32_t *mix_qubits) {
     if (!plan) {
         set_error("plan is NULL");
         return QAOA_E_INVALID;
@@ -309,6 +310,8 @@ extern "C" int qaoa_plan_reps(const qaoa_plan *plan, int32_t *graph, int64_t *ed
         if (n_qubits) n_qubits[i] = c.n;
         if (n_inner) n_inner[i] = c.n_in;
         if (n_cone_edges) n_cone_edges[i] = int32_t(c.ea.size());
+        if (mix_qubits)
+            for (int32_t l = 0; l < plan->p; ++l) mix_qubits[i * plan->p + l] = c.k[l];
     }
     return QAOA_OK;
 }

@@ -57,7 +57,7 @@ _SIGS = {
     "qaoa_plan_free": (None, [_P]),
     "qaoa_plan_info": (C.c_int, [_P, C.POINTER(PlanInfo)]),
     "qaoa_plan_orbits": (C.c_int, [_P, C.c_int32, _I32P, _I64P, _F64P, _I32P]),
-    "qaoa_plan_reps": (C.c_int, [_P, _I32P, _I64P, _I32P, _I32P, _I32P, _I32P]),
+    "qaoa_plan_reps": (C.c_int, [_P, _I32P, _I64P, _I32P, _I32P, _I32P, _I32P, _I32P]),
     "qaoa_plan_cone": (C.c_int, [_P, C.c_int64, _I32P, _I32P, _I32P]),
     "qaoa_edge_orbits": (C.c_int, [C.c_int32, C.c_int64, _I32P, C.c_int64, _I32P, _I64P, _I64P, _F64P, _I32P]),
     "qaoa_plan_upload": (C.c_int, [_P]),
@@ -65,6 +65,8 @@ _SIGS = {
     "qaoa_energy": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P]),
     "qaoa_energy_grad": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P, _P]),
     "qaoa_device_status": (C.c_int, [_P, _I32P]),
+    "qaoa_plan_timing": (C.c_int, [_P, C.c_int32]),
+    "qaoa_kernel_time": (C.c_int, [_P, _F64P, _I64P, _I64P]),
     "qaoa_last_error": (C.c_char_p, []),
     "qaoa_version": (C.c_char_p, []),
 }
@@ -171,10 +173,13 @@ class Plan:
         r = self.info()["n_reps"]
         out = {k: np.zeros(r, dtype=np.int32) for k in ("graph", "weight", "n_qubits", "n_inner", "n_cone_edges")}
         edge = np.zeros(r, dtype=np.int64)
+        mix = np.zeros((r, self.p), dtype=np.int32)
         _check(lib().qaoa_plan_reps(self._h, _ptr(out["graph"], C.c_int32), _ptr(edge, C.c_int64),
                                     _ptr(out["weight"], C.c_int32), _ptr(out["n_qubits"], C.c_int32),
-                                    _ptr(out["n_inner"], C.c_int32), _ptr(out["n_cone_edges"], C.c_int32)))
+                                    _ptr(out["n_inner"], C.c_int32), _ptr(out["n_cone_edges"], C.c_int32),
+                                    _ptr(mix, C.c_int32)))
         out["edge"] = edge
+        out["mix_qubits"] = mix
         return out
 
     def cone(self, rep):
@@ -231,6 +236,18 @@ class Plan:
                                       C.c_void_p(g.data_ptr()), C.c_void_p(t.data_ptr()) if terms else None,
                                       _stream_handle(stream)))
         return (e, g, t) if terms else (e, g)
+
+    def set_timing(self, enable=True):
+        """Record CUDA events around every later call's cone kernel(s)."""
+        _check(lib().qaoa_plan_timing(self._h, 1 if enable else 0))
+
+    def kernel_time(self):
+        """(summed cone-kernel ms, cone-kernel launches, all launches) since the last read."""
+        ms = C.c_double()
+        n = C.c_int64()
+        a = C.c_int64()
+        _check(lib().qaoa_kernel_time(self._h, C.byref(ms), C.byref(n), C.byref(a)))
+        return ms.value, n.value, a.value
 
     def device_status(self):
         s = C.c_int32()

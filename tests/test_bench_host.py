@@ -1,0 +1,66 @@
+"""bench.py host logic on CPU: the max-over-ranks timing reduction and the
+whole-job value on two gloo ranks, the FLOP model, the clock-log parser."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    ms = bench.max_over_ranks(10.0 + rank, dist, "cpu")
+    out.put((rank, ms, bench.whole_job_value(world, 256, ms)))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_reduce_max_and_scale_value():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in range(2))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, ms, v in res:
+        assert ms == 11.0
+        assert abs(v - 2 * 256 / 0.011) < 1e-6
+
+
+def test_flop_model_counts():
+    import bench
+    reps = {"n_qubits": np.array([14, 3]), "mix_qubits": np.array([[6, 2], [2, 2]])}
+    fwd = bench.algorithmic_flops(reps, 2, grad=False)
+    assert fwd == 2 ** 14 * (6 + 6 * 8 + 4) + 2 ** 3 * (6 + 6 * 4 + 4)
+    both = bench.algorithmic_flops(reps, 2, grad=True)
+    assert both == fwd + 2 ** 14 * (2 + 16 * 8 + 10 + 12) + 2 ** 3 * (2 + 16 * 4 + 10 + 12)
+
+
+def test_clock_log_parser(tmp_path):
+    import bench
+    c = bench.ClockSampler(0)
+    c.path = str(tmp_path / "c.csv")
+    c.proc = object()
+    with open(c.path, "w") as f:
+        f.write("0, 1900, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active\n")
+        f.write("0, 1950, 2070, 950.2, 0x4, Not Active, Not Active, Not Active, Active\n")
+        f.write("0, 2000, 2070, 990.0, 0x0, Not Active, Not Active, Not Active, Not Active\n")
+    s = c.summary()
+    assert s["sm_mhz"] == 1950 and s["sm_max_mhz"] == 2070 and s["reasons"] == ["sw_power_cap"]

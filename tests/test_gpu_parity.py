@@ -1,0 +1,261 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (the accuracy targets of this port): cut tables bit-exact; per-term
+|dE| <= 1e-5; total energy relative error <= 1e-6; gradients norm-wise
+relative error <= 1e-4 with a per-component floor of 1e-4 * max|g*|.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import qaoa_oracle as O
+from paper_2101_10296_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TERM_TOL = 1e-5
+E_REL_TOL = 1e-6
+G_REL_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def q(qlib):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return qlib
+
+
+def _params(theta, G=1):
+    t = np.asarray(theta, dtype=np.float64)
+    if t.ndim == 2:
+        t = np.broadcast_to(t, (G,) + t.shape)
+    return torch.tensor(np.ascontiguousarray(t), device="cuda")
+
+
+def _check_grad(g, gref):
+    g = np.asarray(g, dtype=np.float64)
+    gref = np.asarray(gref, dtype=np.float64)
+    nrm = np.linalg.norm(gref)
+    assert np.linalg.norm(g - gref) <= G_REL_TOL * max(nrm, 1e-12)
+    assert np.max(np.abs(g - gref)) <= 1e-4 * max(np.max(np.abs(gref)), 1e-12)
+
+
+# ------------------------------------------------------------- cut tables
+
+@pytest.mark.parametrize("graph,p", [
+    (I.petersen(), 1), (I.random_regular(60, 3, 2), 2), (I.torus(8, 8), 2), (I.hypercube(8), 1),
+    (I.complete(5), 1), ((2, np.array([[0, 1]])), 1), (I.erdos_renyi(80, 0.05, 4), 1),
+])
+def test_cut_tables_bit_exact(q, graph, p):
+    n, edges = graph
+    plan = q.Plan((n, edges), p, orbits=False)
+    reps = plan.reps()
+    adj = O.adjacency(n, edges)
+    for r in range(0, len(edges), max(1, len(edges) // 6)):
+        e = edges[reps["edge"][r]]
+        ov, od, oe = O.lightcone(n, edges, e, p, adj)
+        keep = sorted((min(a, b), max(a, b)) for a, b in oe.tolist() if min(od[a], od[b]) <= p - 1)
+        ref = O.cut_table(len(ov), np.array(keep).reshape(-1, 2)).astype(np.uint8)
+        got = plan.cut_table(r).cpu().numpy()
+        assert got.shape == ref.shape and np.array_equal(got, ref)
+    assert plan.device_status() == 0
+
+
+# ---------------------------------------------------------- energies
+
+def test_c20_single_point_matches_oracle_and_closed_form(q):
+    n, edges = I.circulant(20, [1, 4])
+    theta = I.draw_params(1, 1, 0)
+    plan = q.Plan((n, edges), 1)
+    assert plan.info()["n_reps"] == 2
+    e = plan.energy(_params(theta)).item()
+    ref = O.lightcone_energy(n, edges, theta[0], 1)
+    cf = sum(O.closed_form_p1_term(n, edges, ed, theta[0, 0], theta[0, 1]) for ed in edges)
+    assert abs(ref - cf) < 1e-12
+    assert abs(e - ref) <= E_REL_TOL * abs(ref)
+
+
+@pytest.mark.parametrize("graph,p,P", [
+    (I.petersen(), 1, 5), (I.petersen(), 2, 4), (I.cycle(30), 3, 3), (I.random_regular(40, 3, 3), 2, 3),
+    (I.torus(8, 8), 2, 2), (I.circulant(30, [1, 4]), 2, 3), (I.wheel(7), 1, 4), (I.complete(6), 1, 3),
+    (I.star(5), 2, 2), ((2, np.array([[0, 1]])), 3, 3), (I.path(7), 3, 2),
+])
+def test_terms_and_energy_match_oracle(q, graph, p, P):
+    n, edges = graph
+    theta = I.draw_params(p, P, 7 + p)
+    plan = q.Plan((n, edges), p, orbits=False)
+    e, t = plan.energy(_params(theta), terms=True)
+    e = e.cpu().numpy()[0]
+    t = t.cpu().numpy()
+    reps = plan.reps()
+    adj = O.adjacency(n, edges)
+    for j in range(P):
+        tot = 0.0
+        for r in range(len(edges)):
+            ref = O.lightcone_term(n, edges, edges[reps["edge"][r]], theta[j], p, adj)
+            assert abs(0.5 * (1 - t[r, j]) - 0.5 * (1 - ref)) <= TERM_TOL
+            tot += 0.5 * (1 - ref)
+        assert abs(e[j] - tot) <= E_REL_TOL * abs(tot)
+    assert plan.device_status() == 0
+
+
+@pytest.mark.parametrize("graph,p", [
+    (I.circulant(5000, [1, 7, 23]), 1), (I.hypercube(8), 1), (I.erdos_renyi(300, 4 / 299, 9), 1),
+    (I.torus(30, 30), 1), (I.random_regular(500, 5, 2), 1),
+])
+def test_p1_energy_matches_closed_form(q, graph, p):
+    n, edges = graph
+    P = 6
+    theta = I.draw_params(p, P, 3)
+    plan = q.Plan((n, edges), p)
+    e = plan.energy(_params(theta)).cpu().numpy()[0]
+    adj = O.adjacency(n, edges)
+    for j in range(P):
+        ref = sum(O.closed_form_p1_term(n, edges, ed, theta[j, 0], theta[j, 1], adj) for ed in edges)
+        assert abs(e[j] - ref) <= E_REL_TOL * abs(ref)
+
+
+def test_orbit_reduction_and_full_cone_agree(q):
+    for (n, edges), p in [(I.torus(6, 6), 1), (I.circulant(24, [1, 5]), 1), (I.hypercube(4), 1)]:
+        theta = I.draw_params(p, 4, 11)
+        pa = _params(theta)
+        e_orb = q.Plan((n, edges), p).energy(pa).cpu().numpy()
+        e_all = q.Plan((n, edges), p, orbits=False).energy(pa).cpu().numpy()
+        e_full = q.Plan((n, edges), p, full_cone=True).energy(pa).cpu().numpy()
+        assert np.allclose(e_orb, e_all, rtol=E_REL_TOL, atol=0)
+        assert np.allclose(e_full, e_all, rtol=E_REL_TOL, atol=0)
+        ref = O.orbit_energy(n, edges, theta[0], p, O.brute_edge_orbits(n, edges) if n <= 10 else
+                             q.edge_orbits(n, edges)[0])
+        assert abs(e_orb[0, 0] - ref) <= E_REL_TOL * abs(ref)
+
+
+def test_theorem1_equal_terms_within_orbits(q):
+    n, edges = I.circulant(30, [1, 4, 9])
+    p = 2
+    theta = I.draw_params(p, 5, 2)
+    plan = q.Plan((n, edges), p, orbits=False)
+    _, t = plan.energy(_params(theta), terms=True)
+    t = t.cpu().numpy()
+    oid = q.edge_orbits(n, edges)[0]
+    for r in np.unique(oid):
+        assert np.max(np.ptp(t[oid == r], axis=0)) <= 2 * TERM_TOL
+
+
+def test_zero_beta_gives_half_the_edges(q):
+    n, edges = I.random_regular(100, 3, 5)
+    theta = I.draw_params(2, 3, 1)
+    theta[:, 2:] = 0.0
+    e = q.Plan((n, edges), 2).energy(_params(theta)).cpu().numpy()
+    assert np.allclose(e, len(edges) / 2, rtol=E_REL_TOL, atol=0)
+
+
+def test_multi_graph_batch_matches_single_graphs(q):
+    gs = [I.circulant(20, [1, 4]), I.petersen(), I.torus(6, 6), (2, np.array([[0, 1]])), I.random_regular(20, 3, 3)]
+    p = 2
+    P = 3
+    rng = np.random.default_rng(0)
+    theta = np.stack([I.draw_params(p, P, int(s)) for s in rng.integers(0, 1000, len(gs))])
+    plan = q.Plan(gs, p)
+    e, g = plan.energy_grad(_params(theta))
+    for k, graph in enumerate(gs):
+        single = q.Plan(graph, p)
+        e1, g1 = single.energy_grad(_params(theta[k:k + 1]))
+        assert np.allclose(e.cpu().numpy()[k], e1.cpu().numpy()[0], rtol=1e-12, atol=1e-12)
+        assert np.allclose(g.cpu().numpy()[k], g1.cpu().numpy()[0], rtol=1e-9, atol=1e-12)
+
+
+def test_empty_graph_and_isolated_vertices(q):
+    plan = q.Plan((5, np.zeros((0, 2), dtype=np.int32)), 1)
+    assert np.all(plan.energy(_params(I.draw_params(1, 3, 0))).cpu().numpy() == 0.0)
+    n, edges = 12, np.array([[0, 1], [1, 2], [5, 6]])
+    theta = I.draw_params(2, 2, 4)
+    e = q.Plan((n, edges), 2).energy(_params(theta)).cpu().numpy()[0]
+    for j in range(2):
+        ref = O.full_energy(n, edges, theta[j], 2)
+        assert abs(e[j] - ref) <= E_REL_TOL * abs(ref)
+
+
+# ---------------------------------------------------------- gradients
+
+@pytest.mark.parametrize("graph,p,P", [
+    (I.petersen(), 1, 4), (I.petersen(), 2, 3), (I.cycle(20), 3, 2), (I.torus(8, 8), 2, 2),
+    (I.random_regular(30, 3, 4), 2, 2), (I.star(6), 2, 2), ((2, np.array([[0, 1]])), 2, 2),
+])
+def test_gradient_matches_oracle_adjoint(q, graph, p, P):
+    n, edges = graph
+    theta = I.draw_params(p, P, 5 + p)
+    plan = q.Plan((n, edges), p)
+    e, g = plan.energy_grad(_params(theta))
+    e = e.cpu().numpy()[0]
+    g = g.cpu().numpy()[0]
+    e_only = plan.energy(_params(theta)).cpu().numpy()[0]
+    oid = plan.orbits(0)[0]
+    for j in range(P):
+        eref, gref = O.orbit_grad_adjoint(n, edges, theta[j], p, oid)
+        assert abs(e[j] - eref) <= E_REL_TOL * abs(eref)
+        assert abs(e_only[j] - eref) <= E_REL_TOL * abs(eref)
+        _check_grad(g[j], gref)
+    assert plan.device_status() == 0
+
+
+def test_gradient_matches_finite_differences(q):
+    n, edges = I.random_regular(12, 3, 2)
+    p = 2
+    theta = I.draw_params(p, 2, 9)
+    _, g = q.Plan((n, edges), p).energy_grad(_params(theta))
+    for j in range(2):
+        _check_grad(g.cpu().numpy()[0, j], O.grad_fd(n, edges, theta[j], p, h=1e-4))
+
+
+def test_autograd_function(q):
+    n, edges = I.torus(6, 6)
+    p = 2
+    plan = q.Plan((n, edges), p)
+    theta = _params(I.draw_params(p, 3, 1)).requires_grad_(True)
+    e = q.qaoa_energy(theta, plan)
+    (gt,) = torch.autograd.grad(e.sum(), theta)
+    _, g = plan.energy_grad(theta.detach())
+    assert torch.allclose(gt, g)
+    w = torch.arange(1, 4, dtype=torch.float64, device="cuda")
+    theta2 = theta.detach()[0].clone().requires_grad_(True)  # 2-D params [P, 2p]
+    e2 = q.qaoa_energy(theta2, plan)
+    (gt2,) = torch.autograd.grad((e2[0] * w).sum(), theta2)
+    assert torch.allclose(gt2, g[0] * w[:, None])
+
+
+# ------------------------------------------ full-size configuration, sampled
+
+def test_rr3_2000_p2_batch_sampled_terms(q):
+    """4 random 3-regular graphs, n = 2000, p = 2, 64 points in one launch
+    (the benchmark workload); sampled terms against the oracle, every energy
+    against the per-rep sum, and 2 pi periodicity at full size."""
+    graphs = [I.random_regular(2000, 3, s) for s in (1, 2, 3, 4)]
+    p, P = 2, 64
+    theta = np.stack([I.draw_params(p, P, s) for s in (1, 2, 3, 4)])
+    plan = q.Plan(graphs, p)
+    assert plan.info()["max_qubits"] <= 14
+    e, t = plan.energy(_params(theta), terms=True)
+    e = e.cpu().numpy()
+    t = t.cpu().numpy()
+    reps = plan.reps()
+    rng = np.random.default_rng(1)
+    adjs = [O.adjacency(n, ed) for n, ed in graphs]
+    for r in rng.choice(len(reps["edge"]), 24, replace=False):
+        g = reps["graph"][r]
+        n, ed = graphs[g]
+        for j in rng.choice(P, 2, replace=False):
+            ref = O.lightcone_term(n, ed, ed[reps["edge"][r]], theta[g, j], p, adjs[g])
+            assert abs(t[r, j] - ref) <= 2 * TERM_TOL
+    for g in range(4):
+        sel = reps["graph"] == g
+        recon = (reps["weight"][sel][:, None] * 0.5 * (1 - t[sel])).sum(axis=0)
+        assert np.allclose(e[g], recon, rtol=1e-12, atol=1e-9)
+    shifted = theta.copy()
+    shifted[..., :p] += 2 * math.pi
+    e2 = plan.energy(_params(shifted)).cpu().numpy()
+    assert np.allclose(e2, e, rtol=1e-5, atol=0)
+    eg, gg = plan.energy_grad(_params(theta))
+    assert np.allclose(eg.cpu().numpy(), e, rtol=E_REL_TOL, atol=0)
+    assert plan.device_status() == 0
