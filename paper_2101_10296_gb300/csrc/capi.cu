@@ -24,7 +24,7 @@ struct qaoa_device_plan {
     int device = -1;
     DevCone *cones = nullptr;
     int64_t n_cones = 0;
-    DevWork reg6, reg5;
+    DevWork reg_e, reg_g;  // work lists of the energy and the adjoint kernels
     double *half_edges = nullptr;
     int32_t *status = nullptr;
     int32_t cmax1 = 1;
@@ -48,19 +48,31 @@ void free_work(DevWork &w) {
     w = DevWork{};
 }
 
-// Builds the slot list for R register qubits over the given plan indices.
+// Builds the slot list for R register qubits over the given plan indices:
+// cones sorted by (T_c descending, graph, plan order), each starting at an
+// offset aligned to min(T_c, 32); a new graph starts on a fresh warp.
 int build_work(const std::vector<DevCone> &hc, const std::vector<int32_t> &idx, int R, DevWork &w) {
     std::vector<int32_t> order(idx);
     auto T = [&](int32_t i) { return int64_t(1) << std::max(hc[i].n - R, 0); };
-    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return T(a) > T(b); });
-    std::vector<int64_t> prefix(order.size() + 1, 0);
-    for (size_t i = 0; i < order.size(); ++i) prefix[i + 1] = prefix[i] + T(order[i]);
-    const int64_t slots = prefix.back();
-    const int64_t warps = (slots + 31) / 32;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+        if (T(a) != T(b)) return T(a) > T(b);
+        return hc[a].graph < hc[b].graph;
+    });
+    std::vector<int64_t> start(order.size() + 1, 0);
+    int64_t pos = 0;
+    for (size_t i = 0; i < order.size(); ++i) {
+        if (i > 0 && hc[order[i]].graph != hc[order[i - 1]].graph) pos = (pos + 31) / 32 * 32;
+        start[i] = pos;
+        pos += T(order[i]);
+    }
+    pos = (pos + 31) / 32 * 32;
+    start[order.size()] = pos;
+    const int64_t slots = pos;
+    const int64_t warps = slots / 32;
     std::vector<int32_t> first(size_t(std::max<int64_t>(warps, 1)), 0);
     size_t ci = 0;
     for (int64_t wi = 0; wi < warps; ++wi) {
-        while (prefix[ci + 1] <= wi * 32) ++ci;
+        while (ci + 1 < order.size() && start[ci + 1] <= wi * 32) ++ci;
         first[wi] = int32_t(ci);
     }
     w.slots = slots;
@@ -69,11 +81,11 @@ int build_work(const std::vector<DevCone> &hc, const std::vector<int32_t> &idx, 
     if (order.empty()) return QAOA_OK;
     cudaError_t e;
     if ((e = cudaMalloc(&w.order, order.size() * sizeof(int32_t))) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
-    if ((e = cudaMalloc(&w.prefix, prefix.size() * sizeof(int64_t))) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&w.prefix, start.size() * sizeof(int64_t))) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
     if ((e = cudaMalloc(&w.warp_first, first.size() * sizeof(int32_t))) != cudaSuccess)
         return cuda_fail(e, "cudaMalloc");
     cudaMemcpy(w.order, order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
-    cudaMemcpy(w.prefix, prefix.data(), prefix.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+    cudaMemcpy(w.prefix, start.data(), start.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
     if ((e = cudaMemcpy(w.warp_first, first.data(), first.size() * sizeof(int32_t), cudaMemcpyHostToDevice)) !=
         cudaSuccess)
         return cuda_fail(e, "cudaMemcpy");
@@ -84,7 +96,7 @@ RegWork as_reg(const qaoa_device_plan *d, const DevWork &w) {
     RegWork r;
     r.cones = d->cones;
     r.order = w.order;
-    r.prefix = w.prefix;
+    r.start = w.prefix;
     r.warp_first = w.warp_first;
     r.n_cones = w.n;
     r.slots = w.slots;
@@ -120,6 +132,7 @@ int run(const qaoa_plan *plan, int64_t n_points, const double *params, double *e
     const qaoa_device_plan *d = plan->dev;
     const int32_t G = plan->n_graphs, p = plan->p;
     float2 *lut = nullptr, *mix = nullptr;
+    float *kpow = nullptr;
     const size_t nlut = size_t(G) * n_points * p * d->cmax1;
     const size_t nmix = size_t(G) * n_points * p;
     cudaError_t e;
@@ -128,6 +141,12 @@ int run(const qaoa_plan *plan, int64_t n_points, const double *params, double *e
         cudaFreeAsync(lut, s);
         return cuda_fail(e, "cudaMallocAsync");
     }
+    if ((e = cudaMallocAsync(&kpow, nmix * kKpow * sizeof(float), s)) != cudaSuccess) {
+        cudaFreeAsync(mix, s);
+        cudaFreeAsync(lut, s);
+        return cuda_fail(e, "cudaMallocAsync");
+    }
+    const bool wide = d->cmax1 - 1 > 32;
     PrepArgs pa;
     pa.params = params;
     pa.G = G;
@@ -137,6 +156,7 @@ int run(const qaoa_plan *plan, int64_t n_points, const double *params, double *e
     pa.half_edges = d->half_edges;
     pa.lut = lut;
     pa.mix = mix;
+    pa.kpow = kpow;
     pa.energy = energy;
     pa.grad = grad;
     pa.terms = terms;
@@ -154,24 +174,33 @@ int run(const qaoa_plan *plan, int64_t n_points, const double *params, double *e
         RegLaunch L;
         L.n_points = n_points;
         L.p = p;
+        // points per warp task: up to 8, phase tables of at most 6 KB per warp
+        {
+            const int64_t row_bytes = int64_t(p) * d->cmax1 * int64_t(sizeof(float2));
+            int64_t jpt = std::min<int64_t>(8, std::max<int64_t>(1, 6144 / row_bytes));
+            L.jpt = int32_t(std::min<int64_t>(jpt, n_points));
+        }
+        const size_t smem = size_t(kRegBlock / 32) * L.jpt * p * d->cmax1 * sizeof(float2);
+        const int64_t tasks_per = (n_points + L.jpt - 1) / L.jpt;
         L.cmax1 = d->cmax1;
         L.lut = lut;
         L.mix = mix;
+        L.kpow = kpow;
         L.energy = energy;
         L.grad = grad;
         L.terms = terms;
         L.status = d->status;
         if (grad) {
-            L.work = as_reg(d, d->reg5);
+            L.work = as_reg(d, d->reg_g);
             if (L.work.warps > 0) {
-                int64_t grid = std::min<int64_t>(reg_grad_grid(), (L.work.warps * n_points + 3) / 4);
-                e = launch_reg_grad(L, int(std::max<int64_t>(grid, 1)), s);
+                int64_t grid = std::min<int64_t>(reg_grad_grid(wide, smem), (L.work.warps * tasks_per + 3) / 4);
+                e = launch_reg_grad(L, wide, int(std::max<int64_t>(grid, 1)), s);
             }
         } else {
-            L.work = as_reg(d, d->reg6);
+            L.work = as_reg(d, d->reg_e);
             if (L.work.warps > 0) {
-                int64_t grid = std::min<int64_t>(reg_energy_grid(), (L.work.warps * n_points + 3) / 4);
-                e = launch_reg_energy(L, int(std::max<int64_t>(grid, 1)), s);
+                int64_t grid = std::min<int64_t>(reg_energy_grid(wide, smem), (L.work.warps * tasks_per + 3) / 4);
+                e = launch_reg_energy(L, wide, int(std::max<int64_t>(grid, 1)), s);
             }
         }
         if (L.work.warps > 0) dm->all_launches += 1;
@@ -180,6 +209,7 @@ int run(const qaoa_plan *plan, int64_t n_points, const double *params, double *e
         cudaEventRecord(ev1, s);
         dm->events.emplace_back(ev0, ev1);
     }
+    cudaFreeAsync(kpow, s);
     cudaFreeAsync(mix, s);
     cudaFreeAsync(lut, s);
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
@@ -195,8 +225,8 @@ extern "C" void qaoa_device_release(qaoa_plan *plan) {
     cudaGetDevice(&cur);
     if (d->device >= 0) cudaSetDevice(d->device);
     cudaFree(d->cones);
-    free_work(d->reg6);
-    free_work(d->reg5);
+    free_work(d->reg_e);
+    free_work(d->reg_g);
     cudaFree(d->half_edges);
     cudaFree(d->status);
     for (auto &pr : d->events) {
@@ -234,13 +264,14 @@ extern "C" int qaoa_plan_upload(qaoa_plan *plan) {
             d.col[c.eb[e]] |= 1ull << e;
         }
         cmax = std::max(cmax, d.m);
-        if (c.n_in <= kRegBitsGrad + kLaneBits)
+        if (c.n_in <= kRegMaxInner)
             reg_idx.push_back(int32_t(i));
         else
             ++n_big;
     }
     if (n_big > 0) {
-        set_error("cones whose inner part exceeds 10 qubits need the large-state path");
+        set_error("cones whose inner part exceeds " + std::to_string(kRegMaxInner) +
+                  " qubits need the large-state path");
         return QAOA_E_CONE_TOO_LARGE;
     }
     auto *d = new qaoa_device_plan;
@@ -259,8 +290,8 @@ extern "C" int qaoa_plan_upload(qaoa_plan *plan) {
             rc = cuda_fail(e, "cudaMemcpy");
         }
     }
-    if (rc == QAOA_OK) rc = build_work(hc, reg_idx, kRegBitsEnergy, d->reg6);
-    if (rc == QAOA_OK) rc = build_work(hc, reg_idx, kRegBitsGrad, d->reg5);
+    if (rc == QAOA_OK) rc = build_work(hc, reg_idx, kRegBitsEnergy, d->reg_e);
+    if (rc == QAOA_OK) rc = build_work(hc, reg_idx, kRegBitsGrad, d->reg_g);
     if (rc == QAOA_OK) {
         std::vector<double> half(size_t(plan->n_graphs));
         for (int32_t g = 0; g < plan->n_graphs; ++g) half[g] = 0.5 * double(plan->n_edges[g]);
@@ -297,7 +328,7 @@ extern "C" int qaoa_plan_info(const qaoa_plan *plan, qaoa_plan_info_t *info) {
         info->max_inner = std::max(info->max_inner, c.n_in);
         info->max_edges = std::max(info->max_edges, int32_t(c.ea.size()));
         info->amps_per_point += std::ldexp(1.0, c.n);
-        if (c.n_in > kRegBitsGrad + kLaneBits) info->n_big++;
+        if (c.n_in > kRegMaxInner) info->n_big++;
     }
     info->on_device = plan->dev ? 1 : 0;
     info->t_orbits_s = plan->t_orbits;

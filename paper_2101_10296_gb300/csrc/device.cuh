@@ -29,26 +29,37 @@ struct alignas(16) DevCone {
 
 // Work list of the register-resident kernels.  Each (cone, point) needs
 // T_c = 2^max(n_c - R, 0) threads (R register qubits per thread).  Cones are
-// sorted by T_c descending so that every cone's first slot is aligned to
-// min(T_c, 32) lanes; slots of one point are the concatenation of all cones'
-// T_c slots and a warp covers 32 consecutive slots of one point.
+// sorted by (T_c descending, graph) and each cone's slots start at start[i];
+// a graph change inside a T_c class is padded to the next multiple of 32
+// slots, so every cone's first slot is aligned to min(T_c, 32) lanes and no
+// warp spans two graphs.  A warp task covers 32 consecutive slots for
+// `jpt` consecutive parameter points of that graph.
 struct RegWork {
     const DevCone *cones = nullptr;     // plan order
     const int32_t *order = nullptr;     // sorted position -> plan index
-    const int64_t *prefix = nullptr;    // [n+1] slot prefix over sorted cones
+    const int64_t *start = nullptr;     // [n+1] first slot of each sorted cone
     const int32_t *warp_first = nullptr;  // sorted index of the cone at slot 32*w
     int32_t n_cones = 0;
-    int64_t slots = 0;                  // slots per point
+    int64_t slots = 0;                  // slots per point (with padding)
     int64_t warps = 0;                  // warps per point
 };
+
+// Per-point mixer data.  exp(-i beta X) = kappa (I - i tau X) with
+// tau = tan(beta), kappa = cos(beta) when |tan(beta)| <= 1; otherwise the
+// kernel applies exp(-i (beta - pi/2) X) (tau = -cot(beta), kappa = sin(beta))
+// followed by exp(-i pi/2 X) = -i X, whose bit flip it tracks instead of
+// applying (flip = 1).  kpow[k] = kappa^(2k), rounded once from FP64.
+constexpr int kKpow = QAOA_MAX_CONE_QUBITS + 1;
 
 struct RegLaunch {
     RegWork work;
     int64_t n_points;
+    int32_t jpt;              // parameter points per warp task
     int32_t p;
     int32_t cmax1;            // phase-table row length (max cone edges + 1)
     const float2 *lut;        // [G][P][p][cmax1]  exp(-i gamma_l c)
-    const float2 *mix;        // [G][P][p]         (cos beta_l, sin beta_l)
+    const float2 *mix;        // [G][P][p]         (tau_l, flip_l)
+    const float *kpow;        // [G][P][p][kKpow]  kappa_l^(2k)
     double *energy;           // [G][P]
     double *grad;             // [G][P][2p] or null
     double *terms;            // [reps][P] or null
@@ -62,6 +73,7 @@ struct PrepArgs {
     const double *half_edges; // [G]
     float2 *lut;
     float2 *mix;
+    float *kpow;
     double *energy;
     double *grad;             // may be null
     double *terms;            // may be null
@@ -70,15 +82,33 @@ struct PrepArgs {
 
 // launchers (kernels.cu)
 cudaError_t launch_prep(const PrepArgs &a, cudaStream_t s);
-cudaError_t launch_reg_energy(const RegLaunch &a, int grid, cudaStream_t s);
-cudaError_t launch_reg_grad(const RegLaunch &a, int grid, cudaStream_t s);
+// wide = some cone has more than 32 edges (64-bit cut words).  Dynamic
+// shared memory: 4 warps x jpt x p x cmax1 float2 (phase tables).
+cudaError_t launch_reg_energy(const RegLaunch &a, bool wide, int grid, cudaStream_t s);
+cudaError_t launch_reg_grad(const RegLaunch &a, bool wide, int grid, cudaStream_t s);
 cudaError_t launch_cut_table(const DevCone *cone, uint8_t *out, int32_t n, int32_t *status, cudaStream_t s);
-// occupancy-sized persistent grids
-int reg_energy_grid();
-int reg_grad_grid();
+// occupancy-sized persistent grids for a given dynamic shared memory size
+int reg_energy_grid(bool wide, size_t smem);
+int reg_grad_grid(bool wide, size_t smem);
+constexpr int kRegBlock = 128;
 
-constexpr int kRegBitsEnergy = 5;
-constexpr int kRegBitsGrad = 5;
+#ifndef QAOA_REG_BITS_ENERGY
+#define QAOA_REG_BITS_ENERGY 5
+#endif
+#ifndef QAOA_REG_BITS_GRAD
+#define QAOA_REG_BITS_GRAD 4
+#endif
+// register qubits per thread of the energy and the adjoint kernels
+constexpr int kRegBitsEnergy = QAOA_REG_BITS_ENERGY;
+constexpr int kRegBitsGrad = QAOA_REG_BITS_GRAD;
 constexpr int kLaneBits = 5;
+// resident 128-thread blocks per SM the register allocation is sized for
+#ifndef QAOA_GRAD_MIN_BLOCKS
+#define QAOA_GRAD_MIN_BLOCKS 4
+#endif
+constexpr int kGradMinBlocks = QAOA_GRAD_MIN_BLOCKS;
+constexpr int kEnergyMinBlocks = 3;
+// largest inner part the register kernels take (both must fit)
+constexpr int kRegMaxInner = (kRegBitsEnergy < kRegBitsGrad ? kRegBitsEnergy : kRegBitsGrad) + kLaneBits;
 
 }  // namespace qaoa

@@ -131,9 +131,10 @@ def test_orbit_reduction_and_full_cone_agree(q):
         assert abs(e_orb[0, 0] - ref) <= E_REL_TOL * abs(ref)
 
 
-def test_theorem1_equal_terms_within_orbits(q):
-    n, edges = I.circulant(30, [1, 4, 9])
-    p = 2
+@pytest.mark.parametrize("graph,p", [(I.circulant(30, [1, 4, 9]), 1), (I.circulant(30, [1, 4]), 2),
+                                     (I.torus(7, 7), 2), (I.petersen(), 2)])
+def test_theorem1_equal_terms_within_orbits(q, graph, p):
+    n, edges = graph
     theta = I.draw_params(p, 5, 2)
     plan = q.Plan((n, edges), p, orbits=False)
     _, t = plan.energy(_params(theta), terms=True)
@@ -162,8 +163,9 @@ def test_multi_graph_batch_matches_single_graphs(q):
     for k, graph in enumerate(gs):
         single = q.Plan(graph, p)
         e1, g1 = single.energy_grad(_params(theta[k:k + 1]))
-        assert np.allclose(e.cpu().numpy()[k], e1.cpu().numpy()[0], rtol=1e-12, atol=1e-12)
-        assert np.allclose(g.cpu().numpy()[k], g1.cpu().numpy()[0], rtol=1e-9, atol=1e-12)
+        # same kernels; only the FP32 warp-sum grouping of lanes differs
+        assert np.allclose(e.cpu().numpy()[k], e1.cpu().numpy()[0], rtol=1e-7, atol=1e-9)
+        assert np.allclose(g.cpu().numpy()[k], g1.cpu().numpy()[0], rtol=1e-5, atol=1e-7)
 
 
 def test_empty_graph_and_isolated_vertices(q):
@@ -251,7 +253,7 @@ def test_rr3_2000_p2_batch_sampled_terms(q):
     for g in range(4):
         sel = reps["graph"] == g
         recon = (reps["weight"][sel][:, None] * 0.5 * (1 - t[sel])).sum(axis=0)
-        assert np.allclose(e[g], recon, rtol=1e-12, atol=1e-9)
+        assert np.allclose(e[g], recon, rtol=1e-8, atol=0)
     shifted = theta.copy()
     shifted[..., :p] += 2 * math.pi
     e2 = plan.energy(_params(shifted)).cpu().numpy()
