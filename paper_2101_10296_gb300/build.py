@@ -23,8 +23,8 @@ LIB = os.path.join(PKG, "libqaoa.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 HOST_SRC = ["graph.cpp", "orbits.cpp", "plan.cpp"]
-CUDA_SRC = ["kernels.cu", "capi.cu"]
-HEADERS = ["host.hpp", "device.cuh"]
+CUDA_SRC = ["kernels.cu", "big.cu", "capi.cu"]
+HEADERS = ["host.hpp", "device.cuh", "big.cuh"]
 
 
 def _nvcc():

@@ -7,6 +7,7 @@
 #include <string>
 #include <vector>
 
+#include "big.cuh"
 #include "device.cuh"
 #include "host.hpp"
 
@@ -20,11 +21,22 @@ struct DevWork {
     int32_t n = 0;
 };
 
+// Cones of one shape (n, n_in, k_1..k_p) on the large-state path.
+struct BigShape {
+    int32_t n = 0, n_in = 0;
+    std::vector<int32_t> k;
+    std::vector<int32_t> cones;  // plan indices
+    int32_t *d_cones = nullptr;
+    std::vector<qaoa::BigPass> fwd, grad;
+};
+
 struct qaoa_device_plan {
     int device = -1;
     DevCone *cones = nullptr;
     int64_t n_cones = 0;
     DevWork reg_e, reg_g;  // work lists of the energy and the adjoint kernels
+    std::vector<BigShape> big;
+    size_t big_budget = size_t(1) << 30;  // scratch bytes per call for big cones
     double *half_edges = nullptr;
     int32_t *status = nullptr;
     int32_t cmax1 = 1;
@@ -121,6 +133,62 @@ int ensure_uploaded(const qaoa_plan *plan) {
     return check_device(plan);
 }
 
+// Large-state cones: per shape, waves of blocks that fit the scratch budget,
+// each wave streamed through the shape's pass list.
+cudaError_t run_big(const qaoa_device_plan *d, const qaoa_plan *plan, int64_t P, const double *params,
+                    const float2 *lut, double *energy, double *grad, double *terms, cudaStream_t s) {
+    qaoa_device_plan *dm = const_cast<qaoa_device_plan *>(d);
+    const int p = plan->p;
+    float2 *cs = nullptr;
+    cudaError_t e = cudaMallocAsync(&cs, size_t(plan->n_graphs) * P * p * sizeof(float2), s);
+    if (e != cudaSuccess) return e;
+    e = launch_big_prep(params, int64_t(plan->n_graphs) * P, p, cs, s);
+    dm->all_launches += 1;
+    const bool g = grad != nullptr;
+    const int grid = big_grid(g);
+    for (const BigShape &bs : d->big) {
+        if (e != cudaSuccess) break;
+        const int64_t block_bytes = (int64_t(1) << bs.n_in) * int64_t(sizeof(float2)) * (g ? 2 : 1);
+        const int64_t Y = int64_t(1) << (bs.n - bs.n_in);
+        const int64_t items = int64_t(bs.cones.size()) * P * Y;
+        const int64_t wave = std::max<int64_t>(1, std::min<int64_t>(items, int64_t(d->big_budget) / block_bytes));
+        float2 *scratch = nullptr;
+        e = cudaMallocAsync(&scratch, size_t(wave) * block_bytes, s);
+        if (e != cudaSuccess) break;
+        BigLaunch B{};
+        B.cones = d->cones;
+        B.cone_ids = bs.d_cones;
+        B.n = bs.n;
+        B.n_in = bs.n_in;
+        B.Y = Y;
+        B.P = P;
+        B.p = p;
+        B.cmax1 = d->cmax1;
+        B.lut = lut;
+        B.cs = cs;
+        B.psi = scratch;
+        B.lam = g ? scratch + size_t(wave) * (size_t(1) << bs.n_in) : nullptr;
+        B.energy = energy;
+        B.grad = grad;
+        B.terms = terms;
+        B.status = d->status;
+        const std::vector<BigPass> &passes = g ? bs.grad : bs.fwd;
+        for (int64_t i0 = 0; i0 < items && e == cudaSuccess; i0 += wave) {
+            B.item0 = i0;
+            B.n_items = std::min(wave, items - i0);
+            for (const BigPass &ps : passes) {
+                B.pass = ps;
+                e = launch_big_pass(B, g, grid, s);
+                dm->all_launches += 1;
+                if (e != cudaSuccess) break;
+            }
+        }
+        cudaFreeAsync(scratch, s);
+    }
+    cudaFreeAsync(cs, s);
+    return e;
+}
+
 int run(const qaoa_plan *plan, int64_t n_points, const double *params, double *energy, double *grad,
         double *terms, cudaStream_t s) {
     if (!plan || n_points < 1 || !params || !energy) {
@@ -204,6 +272,7 @@ int run(const qaoa_plan *plan, int64_t n_points, const double *params, double *e
             }
         }
         if (L.work.warps > 0) dm->all_launches += 1;
+        if (e == cudaSuccess && !d->big.empty()) e = run_big(d, plan, n_points, params, lut, energy, grad, terms, s);
     }
     if (ev0) {
         cudaEventRecord(ev1, s);
@@ -227,6 +296,7 @@ extern "C" void qaoa_device_release(qaoa_plan *plan) {
     cudaFree(d->cones);
     free_work(d->reg_e);
     free_work(d->reg_g);
+    for (auto &bs : d->big) cudaFree(bs.d_cones);
     cudaFree(d->half_edges);
     cudaFree(d->status);
     for (auto &pr : d->events) {
@@ -269,12 +339,25 @@ extern "C" int qaoa_plan_upload(qaoa_plan *plan) {
         else
             ++n_big;
     }
-    if (n_big > 0) {
-        set_error("cones whose inner part exceeds " + std::to_string(kRegMaxInner) +
-                  " qubits need the large-state path");
-        return QAOA_E_CONE_TOO_LARGE;
-    }
     auto *d = new qaoa_device_plan;
+    for (size_t i = 0; i < plan->cones.size(); ++i) {
+        const Cone &c = plan->cones[i];
+        if (c.n_in <= kRegMaxInner) continue;
+        std::vector<int32_t> kv(c.k, c.k + plan->p);
+        BigShape *shape = nullptr;
+        for (auto &bs : d->big)
+            if (bs.n == c.n && bs.n_in == c.n_in && bs.k == kv) shape = &bs;
+        if (!shape) {
+            d->big.emplace_back();
+            shape = &d->big.back();
+            shape->n = c.n;
+            shape->n_in = c.n_in;
+            shape->k = kv;
+            shape->fwd = big_forward_passes(c.n_in, plan->p, kv.data());
+            shape->grad = big_grad_passes(c.n_in, plan->p, kv.data());
+        }
+        shape->cones.push_back(int32_t(i));
+    }
     cudaGetDevice(&d->device);
     d->n_cones = int64_t(hc.size());
     d->cmax1 = cmax + 1;
@@ -289,6 +372,13 @@ extern "C" int qaoa_plan_upload(qaoa_plan *plan) {
                    cudaSuccess) {
             rc = cuda_fail(e, "cudaMemcpy");
         }
+    }
+    for (auto &bs : d->big) {
+        if (rc != QAOA_OK) break;
+        if ((e = cudaMalloc(&bs.d_cones, bs.cones.size() * sizeof(int32_t))) != cudaSuccess)
+            rc = cuda_fail(e, "cudaMalloc");
+        else
+            cudaMemcpy(bs.d_cones, bs.cones.data(), bs.cones.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
     }
     if (rc == QAOA_OK) rc = build_work(hc, reg_idx, kRegBitsEnergy, d->reg_e);
     if (rc == QAOA_OK) rc = build_work(hc, reg_idx, kRegBitsGrad, d->reg_g);

@@ -118,7 +118,7 @@ def test_p1_energy_matches_closed_form(q, graph, p):
 
 
 def test_orbit_reduction_and_full_cone_agree(q):
-    for (n, edges), p in [(I.torus(6, 6), 1), (I.circulant(24, [1, 5]), 1), (I.hypercube(4), 1)]:
+    for (n, edges), p in [(I.torus(6, 6), 2), (I.circulant(24, [1, 5]), 2), (I.hypercube(6), 1)]:
         theta = I.draw_params(p, 4, 11)
         pa = _params(theta)
         e_orb = q.Plan((n, edges), p).energy(pa).cpu().numpy()
@@ -261,3 +261,72 @@ def test_rr3_2000_p2_batch_sampled_terms(q):
     eg, gg = plan.energy_grad(_params(theta))
     assert np.allclose(eg.cpu().numpy(), e, rtol=E_REL_TOL, atol=0)
     assert plan.device_status() == 0
+
+
+# ------------------------------------------------ large-state (big) path
+
+def _cone_shapes(q, graph, p, **kw):
+    info = q.Plan(graph, p, **kw).info()
+    return info["max_inner"], info["max_qubits"], info["n_big"]
+
+
+@pytest.mark.parametrize("d", [8, 9, 10])
+def test_big_full_cone_p1_matches_closed_form(q, d):
+    n, edges = I.hypercube(d)
+    plan = q.Plan((n, edges), 1, full_cone=True)
+    info = plan.info()
+    assert info["n_big"] == 1 and info["max_inner"] == 2 * d
+    theta = I.draw_params(1, 3, d)
+    e, g = plan.energy_grad(_params(theta))
+    e_only = plan.energy(_params(theta))
+    ref_plan = q.Plan((n, edges), 1)
+    e_ref, g_ref = ref_plan.energy_grad(_params(theta))
+    adj = O.adjacency(n, edges)
+    for j in range(3):
+        cf = len(edges) * O.closed_form_p1_term(n, edges, edges[0], theta[j, 0], theta[j, 1], adj)
+        assert abs(e[0, j].item() - cf) <= E_REL_TOL * abs(cf)
+        assert abs(e_only[0, j].item() - cf) <= E_REL_TOL * abs(cf)
+        _check_grad(g[0, j].cpu().numpy(), g_ref[0, j].cpu().numpy())
+    assert plan.device_status() == 0
+
+
+@pytest.mark.parametrize("graph,p", [(I.torus(8, 8), 2), (I.random_regular(60, 3, 7), 2), (I.circulant(40, [1, 3]), 2)])
+def test_big_full_cone_matches_register_path(q, graph, p):
+    n, edges = graph
+    full = q.Plan((n, edges), p, full_cone=True)
+    assert full.info()["n_big"] >= 1
+    theta = I.draw_params(p, 4, 5)
+    e1, g1 = full.energy_grad(_params(theta))
+    e2, g2 = q.Plan((n, edges), p).energy_grad(_params(theta))
+    assert np.allclose(e1.cpu().numpy(), e2.cpu().numpy(), rtol=E_REL_TOL, atol=0)
+    for j in range(4):
+        _check_grad(g1[0, j].cpu().numpy(), g2[0, j].cpu().numpy())
+    assert full.device_status() == 0
+
+
+@pytest.mark.parametrize("graph,p", [(I.petersen(), 3), (I.circulant(30, [1, 2]), 3), (I.circulant(40, [1, 3]), 3),
+                                     (I.random_regular(16, 3, 3), 3)])
+def test_big_path_terms_energy_grad_match_oracle(q, graph, p):
+    n, edges = graph
+    plan = q.Plan((n, edges), p, orbits=False)
+    info = plan.info()
+    assert info["n_big"] >= 1 and info["max_qubits"] <= 20
+    theta = I.draw_params(p, 2, 13)
+    e, t = plan.energy(_params(theta), terms=True)
+    t = t.cpu().numpy()
+    reps = plan.reps()
+    adj = O.adjacency(n, edges)
+    rng = np.random.default_rng(0)
+    for r in rng.choice(len(edges), min(6, len(edges)), replace=False):
+        for j in range(2):
+            ref = O.lightcone_term(n, edges, edges[reps["edge"][r]], theta[j], p, adj)
+            assert abs(t[r, j] - ref) <= 2 * TERM_TOL
+    oplan = q.Plan((n, edges), p)
+    e2, g2 = oplan.energy_grad(_params(theta))
+    oid = oplan.orbits(0)[0]
+    for j in range(2):
+        eref, gref = O.orbit_grad_adjoint(n, edges, theta[j], p, oid, adj)
+        assert abs(e[0, j].item() - eref) <= E_REL_TOL * abs(eref)
+        assert abs(e2[0, j].item() - eref) <= E_REL_TOL * abs(eref)
+        _check_grad(g2[0, j].cpu().numpy(), gref)
+    assert plan.device_status() == 0 and oplan.device_status() == 0
