@@ -24,7 +24,7 @@ LIB = os.path.join(PKG, "libqaoa.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 HOST_SRC = ["graph.cpp", "orbits.cpp", "plan.cpp"]
 CUDA_SRC = ["kernels.cu", "big.cu", "capi.cu"]
-HEADERS = ["host.hpp", "device.cuh", "big.cuh"]
+HEADERS = ["host.hpp", "device.cuh", "big.cuh", "devplan.cuh"]
 
 
 def _nvcc():

@@ -1,0 +1,43 @@
+// Device copy of a plan: cone descriptors, register-kernel work lists and
+// large-state shapes (shared by the C-ABI translation units).
+#pragma once
+
+#include <utility>
+#include <vector>
+
+#include "big.cuh"
+#include "device.cuh"
+
+struct DevWork {
+    int32_t *order = nullptr;
+    int64_t *prefix = nullptr;
+    int32_t *warp_first = nullptr;
+    int64_t slots = 0, warps = 0;
+    int32_t n = 0;
+};
+
+// Cones of one shape (n, n_in, k_1..k_p) on the large-state path.
+struct BigShape {
+    int32_t n = 0, n_in = 0;
+    std::vector<int32_t> k;
+    std::vector<int32_t> cones;  // plan indices
+    int32_t *d_cones = nullptr;
+    std::vector<qaoa::BigPass> fwd, grad;
+};
+
+struct qaoa_device_plan {
+    int device = -1;
+    qaoa::DevCone *cones = nullptr;
+    int64_t n_cones = 0;
+    DevWork reg_e, reg_g;  // work lists of the energy and the adjoint kernels
+    std::vector<BigShape> big;
+    size_t big_budget = size_t(1) << 30;  // scratch bytes per call for big cones
+    double *half_edges = nullptr;
+    int32_t *status = nullptr;
+    int32_t cmax1 = 1;
+    int64_t n_big = 0;
+    bool timing = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
+    int64_t all_launches = 0;
+};
+
