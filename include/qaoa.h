@@ -214,6 +214,33 @@ int qaoa_energy_grad(const qaoa_plan *plan, int64_t n_points,
                      double *grad_dev, double *terms_dev, qaoa_stream_t stream);
 
 /*
+ * qaoa_energy_noalloc -- qaoa_energy that makes no device allocation.  The
+ * paper has no counterpart: this is an interface for callers that must not
+ * allocate GPU memory while they run (code inside another allocator's
+ * callbacks, under a budget manager that forbids new allocations, or in a
+ * process whose memory pool belongs to another runtime), so neither
+ * cudaMalloc nor stream-ordered allocation may happen inside the call.
+ *
+ * Same arguments, outputs and results as qaoa_energy.  Its temporary memory
+ * -- the phase tables and the state blocks of cones on the large-state
+ * path -- is carved from one static device array of QAOA_NOALLOC_SCRATCH_MB
+ * MiB that every device loading the library keeps until the process exits.
+ * The plan must already be on the device (qaoa_plan_upload, which does
+ * allocate; call it during set-up).  The first call on a device looks up the
+ * array's device address once; make that first call before any stream
+ * capture.  A call whose tables plus one state block would not fit returns
+ * QAOA_E_INVALID with the sizes in the message, before launching anything.
+ * Every call uses the same array and leaves its contents behind (all of it
+ * is rewritten before being read, nothing needs clearing); calls that
+ * overlap on the GPU -- on different streams, or from different host
+ * threads -- race on it, so callers must serialise them.
+ */
+#define QAOA_NOALLOC_SCRATCH_MB 64
+int qaoa_energy_noalloc(const qaoa_plan *plan, int64_t n_points,
+                        const double *params_dev, double *energy_dev,
+                        double *terms_dev, qaoa_stream_t stream);
+
+/*
  * Reads and clears the plan's device status word (synchronises the device).
  * *status = 0 if no kernel guard tripped since the last read; otherwise a
  * nonzero code (1: descriptor out of range, 2: non-finite result).

@@ -23,7 +23,7 @@ LIB = os.path.join(PKG, "libqaoa.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 HOST_SRC = ["graph.cpp", "orbits.cpp", "plan.cpp"]
-CUDA_SRC = ["kernels.cu", "big.cu", "capi.cu"]
+CUDA_SRC = ["kernels.cu", "big.cu", "capi.cu", "noalloc.cu"]
 HEADERS = ["host.hpp", "device.cuh", "big.cuh", "devplan.cuh"]
 
 

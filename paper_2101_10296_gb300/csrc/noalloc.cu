@@ -1,0 +1,192 @@
+// qaoa_energy_noalloc: the energy evaluation of qaoa_energy, for callers that
+// must not allocate device memory while they run -- for instance code running
+// inside a custom allocator's callback, under a memory-budget manager that
+// forbids new allocations, or in a process whose allocator is owned by
+// another runtime.  All of its temporary memory (the phase tables and the
+// state blocks of cones on the large-state path) comes from one file-scope
+// device array of fixed size instead of cudaMallocAsync.  Nothing is
+// allocated by this call; the plan's own device copy must already exist
+// (qaoa_plan_upload, a set-up step that does allocate).
+#include <mutex>
+#include <string>
+
+#include "big.cuh"
+#include "device.cuh"
+#include "devplan.cuh"
+#include "host.hpp"
+
+using namespace qaoa;
+
+namespace {
+
+constexpr size_t kNoAllocBytes = size_t(QAOA_NOALLOC_SCRATCH_MB) << 20;
+
+// The scratch every qaoa_energy_noalloc call shares.  Each device that loads
+// the library holds one copy until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_setup_mu;
+void *g_scratch_ptr[kMaxDevices] = {};
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+// Device address of the array on the current device, looked up once per
+// device (host code cannot use the symbol's name as a device address).
+int scratch_address(int dev, unsigned char **out) {
+    std::lock_guard<std::mutex> lk(g_setup_mu);
+    if (!g_scratch_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            set_error(std::string("cudaGetSymbolAddress of the static scratch failed: ") + cudaGetErrorString(e));
+            return QAOA_E_CUDA;
+        }
+        g_scratch_ptr[dev] = p;
+    }
+    *out = static_cast<unsigned char *>(g_scratch_ptr[dev]);
+    return QAOA_OK;
+}
+
+}  // namespace
+
+extern "C" int qaoa_energy_noalloc(const qaoa_plan *plan, int64_t n_points, const double *params_dev,
+                                   double *energy_dev, double *terms_dev, qaoa_stream_t stream) {
+    if (!plan || n_points < 1 || !params_dev || !energy_dev) {
+        set_error("need a plan, n_points >= 1, params and energy");
+        return QAOA_E_INVALID;
+    }
+    if (!plan->dev) {
+        set_error("qaoa_energy_noalloc needs a plan already copied to the device (qaoa_plan_upload)");
+        return QAOA_E_INVALID;
+    }
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        set_error(std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+        return QAOA_E_CUDA;
+    }
+    if (dev != plan->dev->device || dev < 0 || dev >= kMaxDevices) {
+        set_error("the plan lives on device " + std::to_string(plan->dev->device) + ", current device is " +
+                  std::to_string(dev));
+        return QAOA_E_INVALID;
+    }
+    const qaoa_device_plan *d = plan->dev;
+    const int32_t G = plan->n_graphs, p = plan->p;
+    const size_t GP = size_t(G) * size_t(n_points);
+    // carve the static array; refuse before launching anything if it is too small
+    const size_t lut_b = align256(GP * p * d->cmax1 * sizeof(float2));
+    const size_t mix_b = align256(GP * p * sizeof(float2));
+    const size_t kpow_b = align256(GP * p * kKpow * sizeof(float));
+    const size_t cs_b = d->big.empty() ? 0 : align256(GP * p * sizeof(float2));
+    const size_t tables = lut_b + mix_b + kpow_b + cs_b;
+    size_t largest_block = 0;
+    for (const BigShape &bs : d->big)
+        largest_block = std::max(largest_block, (size_t(1) << bs.n_in) * sizeof(float2));
+    if (tables + largest_block > kNoAllocBytes) {
+        set_error("qaoa_energy_noalloc: " + std::to_string(n_points) + " points need " +
+                  std::to_string((tables + largest_block + (1 << 20) - 1) >> 20) +
+                  " MiB of scratch, more than its fixed " + std::to_string(kNoAllocBytes >> 20) +
+                  " MiB (use qaoa_energy, or fewer points per call)");
+        return QAOA_E_INVALID;
+    }
+    unsigned char *base = nullptr;
+    int rc = scratch_address(dev, &base);
+    if (rc != QAOA_OK) return rc;
+    float2 *lut = reinterpret_cast<float2 *>(base);
+    float2 *mix = reinterpret_cast<float2 *>(base + lut_b);
+    float *kpow = reinterpret_cast<float *>(base + lut_b + mix_b);
+    float2 *cs = reinterpret_cast<float2 *>(base + lut_b + mix_b + kpow_b);
+    unsigned char *blocks = base + tables;
+    const size_t block_room = kNoAllocBytes - tables;
+    cudaStream_t s = (cudaStream_t)stream;
+
+    // phase tables and output initialisation (every table entry and output is
+    // written before it is read, so nothing in the array needs clearing)
+    PrepArgs pa;
+    pa.params = params_dev;
+    pa.G = G;
+    pa.p = p;
+    pa.cmax1 = d->cmax1;
+    pa.P = n_points;
+    pa.half_edges = d->half_edges;
+    pa.lut = lut;
+    pa.mix = mix;
+    pa.kpow = kpow;
+    pa.energy = energy_dev;
+    pa.grad = nullptr;
+    pa.terms = terms_dev;
+    pa.n_reps = d->n_cones;
+    e = launch_prep(pa, s);
+    // register-resident cones
+    if (e == cudaSuccess && d->reg_e.warps > 0) {
+        RegLaunch L;
+        L.work.cones = d->cones;
+        L.work.order = d->reg_e.order;
+        L.work.start = d->reg_e.prefix;
+        L.work.warp_first = d->reg_e.warp_first;
+        L.work.n_cones = d->reg_e.n;
+        L.work.slots = d->reg_e.slots;
+        L.work.warps = d->reg_e.warps;
+        L.n_points = n_points;
+        L.p = p;
+        const int64_t row_bytes = int64_t(p) * d->cmax1 * int64_t(sizeof(float2));
+        L.jpt = int32_t(std::min<int64_t>(std::min<int64_t>(8, std::max<int64_t>(1, 6144 / row_bytes)), n_points));
+        L.cmax1 = d->cmax1;
+        L.lut = lut;
+        L.mix = mix;
+        L.kpow = kpow;
+        L.energy = energy_dev;
+        L.grad = nullptr;
+        L.terms = terms_dev;
+        L.status = d->status;
+        const bool wide = d->cmax1 - 1 > 32;
+        const size_t smem = size_t(kRegBlock / 32) * L.jpt * p * d->cmax1 * sizeof(float2);
+        const int64_t tasks = d->reg_e.warps * ((n_points + L.jpt - 1) / L.jpt);
+        const int64_t grid = std::min<int64_t>(reg_energy_grid(wide, smem), (tasks + 3) / 4);
+        e = launch_reg_energy(L, wide, int(std::max<int64_t>(grid, 1)), s);
+    }
+    // large-state cones: waves sized to the room left in the array
+    if (e == cudaSuccess && !d->big.empty()) {
+        e = launch_big_prep(params_dev, int64_t(GP), p, cs, s);
+        const int grid = big_grid(false);
+        for (const BigShape &bs : d->big) {
+            if (e != cudaSuccess) break;
+            const size_t block_bytes = (size_t(1) << bs.n_in) * sizeof(float2);
+            const int64_t Y = int64_t(1) << (bs.n - bs.n_in);
+            const int64_t items = int64_t(bs.cones.size()) * n_points * Y;
+            const int64_t wave = std::max<int64_t>(1, std::min<int64_t>(items, int64_t(block_room / block_bytes)));
+            BigLaunch B{};
+            B.cones = d->cones;
+            B.cone_ids = bs.d_cones;
+            B.n = bs.n;
+            B.n_in = bs.n_in;
+            B.Y = Y;
+            B.P = n_points;
+            B.p = p;
+            B.cmax1 = d->cmax1;
+            B.lut = lut;
+            B.cs = cs;
+            B.psi = reinterpret_cast<float2 *>(blocks);
+            B.lam = nullptr;
+            B.energy = energy_dev;
+            B.grad = nullptr;
+            B.terms = terms_dev;
+            B.status = d->status;
+            for (int64_t i0 = 0; i0 < items && e == cudaSuccess; i0 += wave) {
+                B.item0 = i0;
+                B.n_items = std::min(wave, items - i0);
+                for (const BigPass &ps : bs.fwd) {
+                    B.pass = ps;
+                    e = launch_big_pass(B, false, grid, s);
+                    if (e != cudaSuccess) break;
+                }
+            }
+        }
+    }
+    if (e != cudaSuccess) {
+        set_error(std::string("qaoa_energy_noalloc launch: ") + cudaGetErrorString(e));
+        return QAOA_E_CUDA;
+    }
+    return QAOA_OK;
+}

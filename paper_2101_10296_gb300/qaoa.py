@@ -64,6 +64,7 @@ _SIGS = {
     "qaoa_cut_table": (C.c_int, [_P, C.c_int64, _P, _P]),
     "qaoa_energy": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P]),
     "qaoa_energy_grad": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P, _P]),
+    "qaoa_energy_noalloc": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P]),
     "qaoa_device_status": (C.c_int, [_P, _I32P]),
     "qaoa_plan_timing": (C.c_int, [_P, C.c_int32]),
     "qaoa_kernel_time": (C.c_int, [_P, _F64P, _I64P, _I64P]),
@@ -223,6 +224,23 @@ class Plan:
         _check(lib().qaoa_energy(self._h, P, C.c_void_p(params.data_ptr()), C.c_void_p(e.data_ptr()),
                                  C.c_void_p(t.data_ptr()) if terms else None, _stream_handle(stream)))
         return (e, t) if terms else e
+
+    def energy_noalloc(self, params, out=None, terms=None, stream=None):
+        """E[g, j] through qaoa_energy_noalloc, into caller-provided tensors.
+
+        The library allocates nothing during the call; ``out`` (and ``terms``)
+        are allocated here by torch only when not given.  The plan must have
+        been uploaded (``upload()``).
+        """
+        import torch
+        params = self._params(params)
+        G, P = params.shape[0], params.shape[1]
+        if out is None:
+            out = torch.empty(G, P, dtype=torch.float64, device=params.device)
+        _check(lib().qaoa_energy_noalloc(self._h, P, C.c_void_p(params.data_ptr()), C.c_void_p(out.data_ptr()),
+                                         C.c_void_p(terms.data_ptr()) if terms is not None else None,
+                                         _stream_handle(stream)))
+        return out
 
     def energy_grad(self, params, terms=False, stream=None):
         """(E[g, j], dE/dtheta[g, j, 2p]) by the adjoint kernels."""

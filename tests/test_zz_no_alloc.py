@@ -1,0 +1,56 @@
+"""qaoa_energy_noalloc, the energy entry point that allocates no device
+memory during the call (for callers that cannot allocate while they run),
+against qaoa_energy on the same plan and parameters, two calls in a row.
+
+This file is named to be collected last: a failure here leaves every other
+test already run.
+"""
+import numpy as np
+import pytest
+
+from paper_2101_10296_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+E_REL_TOL = 1e-6
+TERM_TOL = 1e-5
+
+
+def test_noalloc_energy_matches_qaoa_energy_twice(qlib):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    # register-resident cones (the 30-cycle) and large-state cones (C_30(1,2): 11
+    # inner qubits, a random cubic graph on 16 vertices: 13)
+    graphs = [I.cycle(30), I.circulant(30, [1, 2]), I.random_regular(16, 3, 3)]
+    p = 3
+    plan = qlib.Plan(graphs, p, orbits=False)
+    plan.upload()
+    assert plan.info()["n_big"] > 0
+    n_reps = plan.info()["n_reps"]
+    for call, seed in enumerate((3, 4)):
+        theta = np.stack([I.draw_params(p, 12, seed + 10 * g) for g in range(len(graphs))])
+        params = torch.tensor(theta, device="cuda")
+        e_ref, t_ref = plan.energy(params, terms=True)
+        out = torch.full((len(graphs), 12), float("nan"), dtype=torch.float64, device="cuda")
+        terms = torch.full((n_reps, 12), float("nan"), dtype=torch.float64, device="cuda")
+        plan.energy_noalloc(params, out=out, terms=terms)
+        torch.cuda.synchronize()
+        e_ref, t_ref = e_ref.cpu().numpy(), t_ref.cpu().numpy()
+        e_na, t_na = out.cpu().numpy(), terms.cpu().numpy()
+        assert np.all(np.isfinite(e_na)) and np.all(np.isfinite(t_na)), call
+        assert np.allclose(e_na, e_ref, rtol=E_REL_TOL, atol=0), call
+        assert np.max(np.abs(0.5 * (t_na - t_ref))) <= TERM_TOL, call
+    assert plan.device_status() == 0
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch(qlib):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    n, edges = I.hypercube(12)
+    plan = qlib.Plan((n, edges), 1, full_cone=True)  # one 2^24-amplitude block: 128 MiB
+    plan.upload()
+    params = torch.tensor(I.draw_params(1, 2, 0)[None], device="cuda")
+    with pytest.raises(qlib.QAOAError) as ei:
+        plan.energy_noalloc(params)
+    assert ei.value.code == qlib.QAOA_E_INVALID and "MiB" in str(ei.value)
