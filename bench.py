@@ -43,7 +43,7 @@ N_VERT, DEG, P_DEPTH, N_POINTS = 2000, 3, 2, 64
 # DRAM bytes per launch of the adjoint cone kernel from one ncu capture of this
 # workload, with the hash of the kernel source they were taken on (a changed
 # kernel reports null until it is profiled again).
-TRAFFIC = {"kernels_sha1": None, "bytes_per_launch": None}
+TRAFFIC = {"kernels_sha1": "b8ae06e9e86304cf95ee08324015ecbb584eefe4", "bytes_per_launch": 5875640}
 
 
 def log(*a):
@@ -89,6 +89,56 @@ def fp32_peak_tflops():
         except Exception:
             pass
     return 152 * 128 * 2 * mhz * 1e6 / 1e12, mhz
+
+
+def hbm_peak_gbs():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            return float(json.load(open(path))["hbm_gbs"]), "measured"
+        except Exception:
+            pass
+    return 6800.0, "fallback"
+
+
+def hbm_path_measurement(device, flush, stream):
+    """The large-state path on 24-qubit cones: Q_12 with QAOA_FULL_CONE at p = 1
+    (the whole 2^24 cone state mixed on every qubit, one orbit), 32 points.
+    Algorithmic bytes per (cone, point) block = one write and one read of the
+    complex64 state (8 * 2^24 bytes each): the minimum once a block exceeds
+    on-chip memory.  Schedule bytes = the block transfers the pass list makes."""
+    import torch
+    from paper_2101_10296_gb300 import inputs as I
+    from paper_2101_10296_gb300 import qaoa
+    P = 32
+    plan = qaoa.Plan(I.hypercube(12), 1, full_cone=True)
+    plan.upload()
+    params = torch.tensor(I.draw_params(1, P, 12)[None], device=device)
+    for _ in range(2):
+        plan.energy(params)
+    torch.cuda.synchronize()
+    plan.set_timing(True)
+    plan.kernel_time()
+    for k in range(5):
+        flush.fill_(k & 0xFF)
+        plan.energy(params)
+    ms, launches, _ = plan.kernel_time()
+    plan.set_timing(False)
+    ms /= max(launches, 1)
+    block = 8 * 2 ** 24
+    alg = 2 * block * P
+    sched = 6 * block * P  # write, read+write, read+write, read (4 passes)
+    peak, basis = hbm_peak_gbs()
+    return {
+        "workload": "Q12 full cone, p=1, 32 points: 24-qubit blocks (energy)",
+        "ms_per_call": ms,
+        "achieved_algorithmic_gbs": alg / (ms / 1e3) / 1e9,
+        "achieved_schedule_gbs": sched / (ms / 1e3) / 1e9,
+        "peak_gbs": peak,
+        "peak_basis": basis,
+        "frac_algorithmic": alg / (ms / 1e3) / 1e9 / peak,
+        "frac_schedule": sched / (ms / 1e3) / 1e9 / peak,
+    }
 
 
 def kernels_sha1():
@@ -337,6 +387,7 @@ def run_ours(args, rank, world, local_rank):
     traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["kernels_sha1"] == kernels_sha1() else None
     amp_updates = float((np.ldexp(1.0, reps["n_qubits"].astype(np.int64)) * p).sum()) * P
 
+    hbm = hbm_path_measurement(device, flush, stream) if not args.no_aux else None
     status = plan.device_status()
     if rank != 0:
         return None
@@ -384,6 +435,7 @@ def run_ours(args, rank, world, local_rank):
         "t_orbits_s": info["t_orbits_s"],
         "wall_s_timed_region": wall,
         "device_status": status,
+        "hbm_path": hbm,
     }
     if pool is not None:
         try:
@@ -443,6 +495,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-aux", action="store_true", help="skip the auxiliary large-state measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         log("warning: fewer than 3 warm-up steps")

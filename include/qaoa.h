@@ -248,6 +248,45 @@ int qaoa_energy_noalloc(const qaoa_plan *plan, int64_t n_points,
 int qaoa_device_status(const qaoa_plan *plan, int32_t *status);
 
 /*
+ * Launch tuning of a plan (applies to every later call).  Any field 0 means
+ * "default".
+ *   points_per_task  parameter points one warp task of the register kernels
+ *                    evaluates for the same cone slots (default: up to 8,
+ *                    while their phase tables fit 6 KB of shared memory)
+ *   blocks_per_sm    resident blocks per SM of the persistent grid (default:
+ *                    the occupancy limit)
+ *   big_scratch_bytes scratch per call for large-state cones, which sets how
+ *                    many state blocks a wave holds (default 1 GiB; a wave
+ *                    that fits the 129 MB L2 keeps its passes on chip)
+ * Errors: QAOA_E_INVALID for negative values.
+ */
+typedef struct qaoa_tuning_t {
+    int32_t points_per_task;
+    int32_t blocks_per_sm;
+    int64_t big_scratch_bytes;
+} qaoa_tuning_t;
+
+int qaoa_plan_set_tuning(qaoa_plan *plan, const qaoa_tuning_t *tuning);
+int qaoa_plan_get_tuning(const qaoa_plan *plan, qaoa_tuning_t *tuning);
+
+/*
+ * Captured CUDA graphs (batching: one replayable graph per evaluation).
+ * qaoa_graph_create records one qaoa_energy (grad_dev == NULL) or
+ * qaoa_energy_grad call with these fixed device buffers into a CUDA graph
+ * (its scratch becomes graph-owned memory nodes) and instantiates it; the
+ * plan is uploaded first if needed.  qaoa_graph_launch replays it on
+ * `stream`: write new parameters into params_dev before each launch; the
+ * outputs are overwritten.  The plan and the buffers must outlive the graph.
+ * Errors: as qaoa_energy / qaoa_energy_grad, or QAOA_E_CUDA if capture fails.
+ */
+typedef struct qaoa_graph qaoa_graph;
+int qaoa_graph_create(qaoa_plan *plan, int64_t n_points, const double *params_dev,
+                      double *energy_dev, double *grad_dev, double *terms_dev,
+                      qaoa_graph **out);
+int qaoa_graph_launch(qaoa_graph *graph, qaoa_stream_t stream);
+void qaoa_graph_free(qaoa_graph *graph);
+
+/*
  * Kernel timing, for measurement.  With enable != 0 every later energy or
  * gradient call records a pair of CUDA events on its own stream around each
  * of its cone kernels (the FP64 phase-table kernel that precedes them is not

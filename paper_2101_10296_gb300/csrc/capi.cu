@@ -101,6 +101,16 @@ int ensure_uploaded(const qaoa_plan *plan) {
     return check_device(plan);
 }
 
+// Persistent grid: the occupancy-sized grid, or blocks_per_sm per SM if tuned
+// (never above the occupancy limit).
+int64_t tuned_grid(const qaoa_device_plan *d, int occupancy_grid) {
+    if (d->blocks_per_sm <= 0) return occupancy_grid;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return std::min<int64_t>(occupancy_grid, int64_t(sms) * d->blocks_per_sm);
+}
+
 // Large-state cones: per shape, waves of blocks that fit the scratch budget,
 // each wave streamed through the shape's pass list.
 cudaError_t run_big(const qaoa_device_plan *d, const qaoa_plan *plan, int64_t P, const double *params,
@@ -213,7 +223,8 @@ int run(const qaoa_plan *plan, int64_t n_points, const double *params, double *e
         // points per warp task: up to 8, phase tables of at most 6 KB per warp
         {
             const int64_t row_bytes = int64_t(p) * d->cmax1 * int64_t(sizeof(float2));
-            int64_t jpt = std::min<int64_t>(8, std::max<int64_t>(1, 6144 / row_bytes));
+            int64_t jpt = d->points_per_task > 0 ? d->points_per_task
+                                                 : std::min<int64_t>(8, std::max<int64_t>(1, 6144 / row_bytes));
             L.jpt = int32_t(std::min<int64_t>(jpt, n_points));
         }
         const size_t smem = size_t(kRegBlock / 32) * L.jpt * p * d->cmax1 * sizeof(float2);
@@ -229,13 +240,13 @@ int run(const qaoa_plan *plan, int64_t n_points, const double *params, double *e
         if (grad) {
             L.work = as_reg(d, d->reg_g);
             if (L.work.warps > 0) {
-                int64_t grid = std::min<int64_t>(reg_grad_grid(wide, smem), (L.work.warps * tasks_per + 3) / 4);
+                int64_t grid = std::min<int64_t>(tuned_grid(d, reg_grad_grid(wide, smem)), (L.work.warps * tasks_per + 3) / 4);
                 e = launch_reg_grad(L, wide, int(std::max<int64_t>(grid, 1)), s);
             }
         } else {
             L.work = as_reg(d, d->reg_e);
             if (L.work.warps > 0) {
-                int64_t grid = std::min<int64_t>(reg_energy_grid(wide, smem), (L.work.warps * tasks_per + 3) / 4);
+                int64_t grid = std::min<int64_t>(tuned_grid(d, reg_energy_grid(wide, smem)), (L.work.warps * tasks_per + 3) / 4);
                 e = launch_reg_energy(L, wide, int(std::max<int64_t>(grid, 1)), s);
             }
         }
@@ -480,4 +491,94 @@ extern "C" int qaoa_kernel_time(qaoa_plan *plan, double *ms, int64_t *launches, 
     if (launches) *launches = count;
     if (all_launches) *all_launches = all;
     return QAOA_OK;
+}
+
+extern "C" int qaoa_plan_set_tuning(qaoa_plan *plan, const qaoa_tuning_t *t) {
+    if (!plan || !t || t->points_per_task < 0 || t->blocks_per_sm < 0 || t->big_scratch_bytes < 0) {
+        set_error("bad plan or tuning values");
+        return QAOA_E_INVALID;
+    }
+    int rc = ensure_uploaded(plan);
+    if (rc != QAOA_OK) return rc;
+    plan->dev->points_per_task = t->points_per_task;
+    plan->dev->blocks_per_sm = t->blocks_per_sm;
+    plan->dev->big_budget = t->big_scratch_bytes > 0 ? size_t(t->big_scratch_bytes) : size_t(1) << 30;
+    return QAOA_OK;
+}
+
+extern "C" int qaoa_plan_get_tuning(const qaoa_plan *plan, qaoa_tuning_t *t) {
+    if (!plan || !t) {
+        set_error("plan or tuning is NULL");
+        return QAOA_E_INVALID;
+    }
+    t->points_per_task = plan->dev ? plan->dev->points_per_task : 0;
+    t->blocks_per_sm = plan->dev ? plan->dev->blocks_per_sm : 0;
+    t->big_scratch_bytes = plan->dev ? int64_t(plan->dev->big_budget) : int64_t(1) << 30;
+    return QAOA_OK;
+}
+
+struct qaoa_graph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" int qaoa_graph_create(qaoa_plan *plan, int64_t n_points, const double *params_dev, double *energy_dev,
+                                 double *grad_dev, double *terms_dev, qaoa_graph **out) {
+    if (!out) {
+        set_error("out is NULL");
+        return QAOA_E_INVALID;
+    }
+    *out = nullptr;
+    if (!plan || n_points < 1 || !params_dev || !energy_dev) {
+        set_error("need a plan, n_points >= 1, params and energy");
+        return QAOA_E_INVALID;
+    }
+    int rc = ensure_uploaded(plan);
+    if (rc != QAOA_OK) return rc;
+    const bool timing = plan->dev->timing;
+    plan->dev->timing = false;  // no event records inside the graph
+    cudaStream_t cap = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        plan->dev->timing = timing;
+        return cuda_fail(e, "cudaStreamCreate");
+    }
+    auto *g = new qaoa_graph;
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        rc = run(plan, n_points, params_dev, energy_dev, grad_dev, terms_dev, cap);
+        cudaError_t e2 = cudaStreamEndCapture(cap, &g->graph);
+        if (rc == QAOA_OK && e2 != cudaSuccess) rc = cuda_fail(e2, "cudaStreamEndCapture");
+    } else {
+        rc = cuda_fail(e, "cudaStreamBeginCapture");
+    }
+    if (rc == QAOA_OK) {
+        e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+        if (e != cudaSuccess) rc = cuda_fail(e, "cudaGraphInstantiate");
+    }
+    cudaStreamDestroy(cap);
+    plan->dev->timing = timing;
+    if (rc != QAOA_OK) {
+        qaoa_graph_free(g);
+        return rc;
+    }
+    *out = g;
+    return QAOA_OK;
+}
+
+extern "C" int qaoa_graph_launch(qaoa_graph *graph, qaoa_stream_t stream) {
+    if (!graph || !graph->exec) {
+        set_error("graph is NULL");
+        return QAOA_E_INVALID;
+    }
+    cudaError_t e = cudaGraphLaunch(graph->exec, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    return QAOA_OK;
+}
+
+extern "C" void qaoa_graph_free(qaoa_graph *graph) {
+    if (!graph) return;
+    if (graph->exec) cudaGraphExecDestroy(graph->exec);
+    if (graph->graph) cudaGraphDestroy(graph->graph);
+    delete graph;
 }

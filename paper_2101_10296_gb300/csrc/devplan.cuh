@@ -36,6 +36,8 @@ struct qaoa_device_plan {
     int32_t *status = nullptr;
     int32_t cmax1 = 1;
     int64_t n_big = 0;
+    int32_t points_per_task = 0;  // 0: default (see qaoa_tuning_t)
+    int32_t blocks_per_sm = 0;
     bool timing = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
     int64_t all_launches = 0;

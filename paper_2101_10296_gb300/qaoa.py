@@ -33,6 +33,10 @@ class QAOAError(RuntimeError):
         self.code = code
 
 
+class Tuning(C.Structure):
+    _fields_ = [("points_per_task", C.c_int32), ("blocks_per_sm", C.c_int32), ("big_scratch_bytes", C.c_int64)]
+
+
 class PlanInfo(C.Structure):
     _fields_ = [
         ("p", C.c_int32), ("n_graphs", C.c_int32), ("n_edges_total", C.c_int64),
@@ -67,6 +71,11 @@ _SIGS = {
     "qaoa_energy_noalloc": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P]),
     "qaoa_device_status": (C.c_int, [_P, _I32P]),
     "qaoa_plan_timing": (C.c_int, [_P, C.c_int32]),
+    "qaoa_plan_set_tuning": (C.c_int, [_P, C.POINTER(Tuning)]),
+    "qaoa_plan_get_tuning": (C.c_int, [_P, C.POINTER(Tuning)]),
+    "qaoa_graph_create": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P, C.POINTER(_P)]),
+    "qaoa_graph_launch": (C.c_int, [_P, _P]),
+    "qaoa_graph_free": (None, [_P]),
     "qaoa_kernel_time": (C.c_int, [_P, _F64P, _I64P, _I64P]),
     "qaoa_last_error": (C.c_char_p, []),
     "qaoa_version": (C.c_char_p, []),
@@ -255,6 +264,20 @@ class Plan:
                                       _stream_handle(stream)))
         return (e, g, t) if terms else (e, g)
 
+    def set_tuning(self, points_per_task=0, blocks_per_sm=0, big_scratch_bytes=0):
+        """Launch tuning for later calls (0 = default); see qaoa_tuning_t."""
+        t = Tuning(points_per_task, blocks_per_sm, big_scratch_bytes)
+        _check(lib().qaoa_plan_set_tuning(self._h, C.byref(t)))
+
+    def get_tuning(self):
+        t = Tuning()
+        _check(lib().qaoa_plan_get_tuning(self._h, C.byref(t)))
+        return {k: getattr(t, k) for k, _ in Tuning._fields_}
+
+    def graph(self, params, grad=True, terms=False):
+        """A captured CUDA graph of one evaluation with fixed buffers (see PlanGraph)."""
+        return PlanGraph(self, params, grad=grad, terms=terms)
+
     def set_timing(self, enable=True):
         """Record CUDA events around every later call's cone kernel(s)."""
         _check(lib().qaoa_plan_timing(self._h, 1 if enable else 0))
@@ -271,6 +294,44 @@ class Plan:
         s = C.c_int32()
         _check(lib().qaoa_device_status(self._h, C.byref(s)))
         return s.value
+
+
+class PlanGraph:
+    """One energy (or energy + gradient) evaluation captured as a CUDA graph.
+
+    ``params`` is copied into a buffer the graph owns a pointer to; call
+    :meth:`run` with new parameters (same shape) to replay the graph; the
+    outputs ``energy``, ``grad`` and ``terms`` are overwritten in place.
+    """
+
+    def __init__(self, plan, params, grad=True, terms=False):
+        import torch
+        params = plan._params(params)
+        G, P = params.shape[0], params.shape[1]
+        self.plan = plan
+        self.params = params.clone()
+        dev = params.device
+        self.energy = torch.empty(G, P, dtype=torch.float64, device=dev)
+        self.grad = torch.empty(G, P, 2 * plan.p, dtype=torch.float64, device=dev) if grad else None
+        self.terms = torch.empty(plan.info()["n_reps"], P, dtype=torch.float64, device=dev) if terms else None
+        h = C.c_void_p()
+        ptr = lambda t: C.c_void_p(t.data_ptr()) if t is not None else None
+        _check(lib().qaoa_graph_create(plan.handle, P, ptr(self.params), ptr(self.energy), ptr(self.grad),
+                                       ptr(self.terms), C.byref(h)))
+        self._h = h
+
+    def run(self, params=None, stream=None):
+        if params is not None:
+            self.params.copy_(self.plan._params(params))
+        _check(lib().qaoa_graph_launch(self._h, _stream_handle(stream)))
+        return (self.energy, self.grad) if self.grad is not None else self.energy
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().qaoa_graph_free(self._h)
+            self._h = C.c_void_p()
+
+    __del__ = close
 
 
 def _autograd_cls():

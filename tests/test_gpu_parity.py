@@ -330,3 +330,61 @@ def test_big_path_terms_energy_grad_match_oracle(q, graph, p):
         assert abs(e2[0, j].item() - eref) <= E_REL_TOL * abs(eref)
         _check_grad(g2[0, j].cpu().numpy(), gref)
     assert plan.device_status() == 0 and oplan.device_status() == 0
+
+
+# ------------------------------------------ batching: CUDA graphs, tuning
+
+def _mixed_plan(q):
+    graphs = [I.cycle(30), I.circulant(30, [1, 2]), I.random_regular(40, 3, 5)]
+    return q.Plan(graphs, 3), len(graphs)
+
+
+def test_cuda_graph_replay_matches_direct_calls(q):
+    plan, G = _mixed_plan(q)
+    assert plan.info()["n_big"] > 0
+    th_a = _params(np.stack([I.draw_params(3, 6, 10 + g) for g in range(G)]))
+    th_b = _params(np.stack([I.draw_params(3, 6, 20 + g) for g in range(G)]))
+    graph = plan.graph(th_a, grad=True)
+    for th in (th_a, th_b, th_a):
+        e, g = graph.run(th)
+        e_ref, g_ref = plan.energy_grad(th)
+        torch.cuda.synchronize()
+        assert np.allclose(e.cpu().numpy(), e_ref.cpu().numpy(), rtol=E_REL_TOL, atol=0)
+        for k in range(G):
+            for j in range(6):
+                _check_grad(g[k, j].cpu().numpy(), g_ref[k, j].cpu().numpy())
+    eg = plan.graph(th_b, grad=False)
+    e = eg.run()
+    assert np.allclose(e.cpu().numpy(), plan.energy(th_b).cpu().numpy(), rtol=E_REL_TOL, atol=0)
+    graph.close()
+    eg.close()
+    assert plan.device_status() == 0
+
+
+def test_tuning_leaves_results_unchanged(q):
+    plan, G = _mixed_plan(q)
+    th = _params(np.stack([I.draw_params(3, 7, 30 + g) for g in range(G)]))
+    e0, g0 = plan.energy_grad(th)
+    for tune in ({"points_per_task": 1}, {"points_per_task": 3, "blocks_per_sm": 1},
+                 {"points_per_task": 16, "big_scratch_bytes": 1 << 20}):
+        plan.set_tuning(**tune)
+        assert all(plan.get_tuning()[k] == v for k, v in tune.items())
+        e1, g1 = plan.energy_grad(th)
+        assert np.allclose(e1.cpu().numpy(), e0.cpu().numpy(), rtol=E_REL_TOL, atol=0)
+        assert np.allclose(g1.cpu().numpy(), g0.cpu().numpy(), rtol=1e-4, atol=1e-6)
+    plan.set_tuning()
+    assert plan.device_status() == 0
+
+
+def test_autotune_picks_and_caches(q, tmp_path):
+    from paper_2101_10296_gb300 import autotune
+    plan, G = _mixed_plan(q)
+    th = _params(np.stack([I.draw_params(3, 8, 40 + g) for g in range(G)]))
+    cache = str(tmp_path / "tune.json")
+    best, results = autotune.autotune(plan, th, grad=False, reps=1, cache_path=cache)
+    assert results and min(results.values()) > 0 and plan.get_tuning()["points_per_task"] == best["points_per_task"]
+    again, res2 = autotune.autotune(plan, th, grad=False, cache_path=cache)
+    assert again == best and res2 == {}
+    e = plan.energy(th)
+    plan.set_tuning()
+    assert np.allclose(e.cpu().numpy(), plan.energy(th).cpu().numpy(), rtol=E_REL_TOL, atol=0)
