@@ -143,7 +143,7 @@ def hbm_path_measurement(device, flush, stream):
 
 def kernels_sha1():
     h = hashlib.sha1()
-    for f in ("kernels.cu", "device.cuh"):
+    for f in ("cone_kernel.cuh", "kernels_grad.cu", "device.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2101_10296_gb300", "csrc", f), "rb").read())
     return h.hexdigest()
 
@@ -414,7 +414,7 @@ def run_ours(args, rank, world, local_rank):
         },
         "roofline": {
             "bound": "alu",
-            "kernel": "reg_cone_kernel<5,true> (adjoint)",
+            "kernel": "reg_cone_kernel<4, u32, adjoint, p=2>",
             "achieved": achieved,
             "peak": peak,
             "unit": "TFLOP/s",

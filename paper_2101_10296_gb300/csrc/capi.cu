@@ -240,7 +240,7 @@ int run(const qaoa_plan *plan, int64_t n_points, const double *params, double *e
         if (grad) {
             L.work = as_reg(d, d->reg_g);
             if (L.work.warps > 0) {
-                int64_t grid = std::min<int64_t>(tuned_grid(d, reg_grad_grid(wide, smem)), (L.work.warps * tasks_per + 3) / 4);
+                int64_t grid = std::min<int64_t>(tuned_grid(d, reg_grad_grid(wide, smem, p)), (L.work.warps * tasks_per + 3) / 4);
                 e = launch_reg_grad(L, wide, int(std::max<int64_t>(grid, 1)), s);
             }
         } else {

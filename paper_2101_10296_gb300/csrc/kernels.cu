@@ -30,342 +30,10 @@
 // exp(-i gamma c), tan and the kappa powers are computed in FP64 and rounded
 // once; lane partial sums are reduced across the warp in FP32 and
 // accumulated across warps, cones and orbits in FP64 (atomicAdd).
-#include "device.cuh"
+#include "cone_kernel.cuh"
 
 namespace qaoa {
 namespace {
-
-constexpr unsigned kFull = 0xffffffffu;
-
-template <typename MT>
-__device__ __forceinline__ int popc_t(MT x);
-template <>
-__device__ __forceinline__ int popc_t<uint32_t>(uint32_t x) {
-    return __popc(x);
-}
-template <>
-__device__ __forceinline__ int popc_t<uint64_t>(uint64_t x) {
-    return __popcll(x);
-}
-
-// Cut word of basis index z = (t << R) | i, split as lo[i & 3] ^ hi[i >> 2]
-// so that every register index's word is one XOR away (no serial chain).
-// hi[] also carries the shell part of the thread and the flip word M(F).
-template <int R, typename MT>
-struct CutWords {
-    MT lo[4];
-    MT hi[1 << (R - 2)];
-
-    __device__ __forceinline__ void init(const DevCone *__restrict__ C, int n, int64_t t) {
-        const MT c0 = MT(C->col[0]), c1 = MT(C->col[1]);
-        lo[0] = 0;
-        lo[1] = c0;
-        lo[2] = c1;
-        lo[3] = c0 ^ c1;
-        MT base = 0;
-        for (int q = R; q < n; ++q)
-            if ((t >> (q - R)) & 1) base ^= MT(C->col[q]);
-        MT cm[R - 2];
-#pragma unroll
-        for (int b = 0; b < R - 2; ++b) cm[b] = (2 + b < n) ? MT(C->col[2 + b]) : MT(0);
-#pragma unroll
-        for (int k = 0; k < (1 << (R - 2)); ++k) {
-            MT v = base;
-#pragma unroll
-            for (int b = 0; b < R - 2; ++b)
-                if ((k >> b) & 1) v ^= cm[b];
-            hi[k] = v;
-        }
-    }
-    __device__ __forceinline__ void flip(MT f) {
-#pragma unroll
-        for (int k = 0; k < (1 << (R - 2)); ++k) hi[k] ^= f;
-    }
-    // f(i, C(z_i xor F)) for every register index i
-    template <class F>
-    __device__ __forceinline__ void visit(F &&f) const {
-#pragma unroll
-        for (int i = 0; i < (1 << R); ++i) f(i, popc_t<MT>(lo[i & 3] ^ hi[i >> 2]));
-    }
-};
-
-// M of the qubit set [0, k): the flip word of a layer that mixes k qubits.
-template <typename MT>
-__device__ __forceinline__ MT prefix_word(const DevCone *__restrict__ C, int k) {
-    MT v = 0;
-    for (int q = 0; q < k; ++q) v ^= MT(C->col[q]);
-    return v;
-}
-
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
-    return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
-}
-// Im(conj(a) b)
-__device__ __forceinline__ float imconj(float2 a, float2 b) { return a.x * b.y - a.y * b.x; }
-// u - i tau v
-__device__ __forceinline__ float2 bfly(float2 u, float2 v, float tau) {
-    return make_float2(fmaf(tau, v.y, u.x), fmaf(-tau, v.x, u.y));
-}
-
-// (I - i tau X_q) on register qubits q < KQ (compile-time count)
-template <int R, int KQ>
-__device__ __forceinline__ void mix_reg_fixed(float2 (&x)[1 << R], float tau) {
-#pragma unroll
-    for (int q = 0; q < KQ; ++q) {
-#pragma unroll
-        for (int i = 0; i < (1 << R); ++i) {
-            if (i & (1 << q)) continue;
-            const int j = i | (1 << q);
-            const float2 a = x[i], b = x[j];
-            x[i] = bfly(a, b, tau);
-            x[j] = bfly(b, a, tau);
-        }
-    }
-}
-
-// (I - i tau X_q) on every register qubit q < k.  A layer mixes either all
-// register qubits or only qubits 0 and 1 (the last layer) except in small
-// cones, so those two cases are straight-line code.
-template <int R>
-__device__ __forceinline__ void mix_reg(float2 (&x)[1 << R], int k, float tau) {
-    if (__all_sync(kFull, k >= R)) {
-        mix_reg_fixed<R, R>(x, tau);
-    } else if (__all_sync(kFull, k == 2)) {
-        mix_reg_fixed<R, 2>(x, tau);
-    } else {
-#pragma unroll
-        for (int q = 0; q < R; ++q) {
-            if (q < k) {
-#pragma unroll
-                for (int i = 0; i < (1 << R); ++i) {
-                    if (i & (1 << q)) continue;
-                    const int j = i | (1 << q);
-                    const float2 a = x[i], b = x[j];
-                    x[i] = bfly(a, b, tau);
-                    x[j] = bfly(b, a, tau);
-                }
-            }
-        }
-    }
-}
-
-// (I - i tau X_q) on lane qubits q = R..R+4 below k (partner lane = xor).
-// Mixed qubits are a prefix, so the loop stops at the first lane bit no lane
-// of the warp mixes; it is not unrolled (shuffle distance is a register).
-template <int R>
-__device__ __forceinline__ void mix_lane(float2 (&x)[1 << R], int k, float tau) {
-#pragma unroll 1
-    for (int L = 0; L < kLaneBits; ++L) {
-        const bool mine = (R + L) < k;
-        if (!__any_sync(kFull, mine)) break;
-        const int m = 1 << L;
-#pragma unroll
-        for (int i = 0; i < (1 << R); ++i) {
-            float2 o;
-            o.x = __shfl_xor_sync(kFull, x[i].x, m);
-            o.y = __shfl_xor_sync(kFull, x[i].y, m);
-            if (mine) x[i] = bfly(x[i], o, tau);
-        }
-    }
-}
-
-// sum_i |x_i|^2 (-1)^(i_0 xor i_1)
-template <int R>
-__device__ __forceinline__ float zz_partial(const float2 (&x)[1 << R]) {
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int i = 0; i < (1 << R); ++i) acc[i & 3] = fmaf(x[i].x, x[i].x, fmaf(x[i].y, x[i].y, acc[i & 3]));
-    return (acc[0] + acc[3]) - (acc[1] + acc[2]);
-}
-
-// Adds v (summed over the warp in FP32) into base[(g*P + j)*stride + comp]
-// with one FP64 atomic per warp when every lane's graph is the same.
-__device__ __forceinline__ void add_gp(float v, double *base, int g, int64_t P, int64_t j, int stride, int comp) {
-    const int g0 = __shfl_sync(kFull, g, 0);
-    if (__all_sync(kFull, g == g0)) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-        if ((threadIdx.x & 31) == 0) atomicAdd(base + (int64_t(g0) * P + j) * stride + comp, double(v));
-    } else if (v != 0.f) {
-        atomicAdd(base + (int64_t(g) * P + j) * stride + comp, double(v));
-    }
-}
-
-template <int R, typename MT, bool GRAD>
-__global__ void __launch_bounds__(kRegBlock, GRAD ? kGradMinBlocks : kEnergyMinBlocks) reg_cone_kernel(const RegLaunch L) {
-    constexpr int NA = 1 << R;
-    extern __shared__ float2 s_tab[];
-    const int lane = threadIdx.x & 31;
-    const RegWork &W = L.work;
-    const int p = L.p;
-    const int row = p * L.cmax1;  // one point's phase table
-    float2 *my_tab = s_tab + (threadIdx.x >> 5) * (L.jpt * row);
-    const int64_t gw = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
-    const int64_t nblk = (L.n_points + L.jpt - 1) / L.jpt;
-    const int64_t ntask = W.warps * nblk;
-    for (int64_t task = gw; task < ntask; task += nw) {
-        const int64_t jb = task / W.warps;
-        const int64_t w = task - jb * W.warps;
-        const int64_t j0 = jb * L.jpt;
-        const int jn = int(L.n_points - j0 < L.jpt ? L.n_points - j0 : L.jpt);
-        const int64_t slot = w * 32 + lane;
-        int ci = W.warp_first[w];
-        if (slot < W.slots)
-            while (W.start[ci + 1] <= slot) ++ci;
-        const DevCone *__restrict__ C = W.cones + W.order[ci];
-        int n = C->n;
-        bool active = slot < W.slots && slot < W.start[ci] + (int64_t(1) << (n > R ? n - R : 0));
-        if (n < 2 || n > QAOA_MAX_CONE_QUBITS || C->n_in > R + kLaneBits) {
-            if (active) atomicOr(L.status, 1);
-            active = false;
-            n = 2;
-        }
-        const int g = C->graph;  // the same on every lane (padded work list)
-        const int64_t t = active ? slot - W.start[ci] : 0;
-        const int nreg = n < R ? n : R;
-        const bool unpadded = __all_sync(kFull, n >= R);
-        const float wgt = float(C->weight);
-        CutWords<R, MT> cw;
-        cw.init(C, n, t);
-        // stage the phase tables of points j0 .. j0+jn-1 of graph g
-        __syncwarp();
-        {
-            const float2 *__restrict__ src = L.lut + (int64_t(g) * L.n_points + j0) * row;
-            for (int e = lane; e < jn * row; e += 32) my_tab[e] = __ldg(src + e);
-        }
-        __syncwarp();
-        for (int jj = 0; jj < jn; ++jj) {
-            const int64_t j = j0 + jj;
-            const float2 *lut = my_tab + jj * row;
-            const int64_t gj = int64_t(g) * L.n_points + j;
-            const float2 *__restrict__ mix = L.mix + gj * p;
-            const float *__restrict__ kp = L.kpow + gj * p * kKpow;
-
-            float2 x[NA];
-            // layer 1 phase on |+>: amplitude exp(-i gamma_1 C(z)) (2^-n/2 kept in sigma)
-            if (unpadded) {
-                cw.visit([&](int i, int c) { x[i] = lut[c]; });
-            } else {
-                cw.visit([&](int i, int c) {
-                    const float2 ph = lut[c];
-                    x[i] = (i >> nreg) ? make_float2(0.f, 0.f) : ph;
-                });
-            }
-            float sig = __int_as_float((127 - n) << 23);  // 2^-n
-            MT fw = 0;                                      // accumulated flip word
-            for (int l = 0; l < p; ++l) {
-                if (l > 0) {
-                    const float2 *lt = lut + l * L.cmax1;
-                    cw.visit([&](int i, int c) { x[i] = cmul(x[i], lt[c]); });
-                }
-                const float2 mx = __ldg(mix + l);
-                const int k = C->k[l];
-                mix_reg<R>(x, k, mx.x);
-                mix_lane<R>(x, k, mx.x);
-                sig *= __ldg(kp + l * kKpow + k);
-                if (mx.y != 0.f) {
-                    const MT f = prefix_word<MT>(C, k);
-                    cw.flip(f);
-                    fw ^= f;
-                }
-            }
-            const float tl = active ? zz_partial<R>(x) : 0.f;
-            add_gp(-0.5f * wgt * sig * tl, L.energy, g, L.n_points, j, 1, 0);
-            if (L.terms) {
-                const int64_t Tc = int64_t(1) << (n > R ? n - R : 0);
-                float tv = sig * tl;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const float ov = __shfl_xor_sync(kFull, tv, o);
-                    if (o < Tc) tv += ov;
-                }
-                const int64_t grp = Tc < 32 ? Tc : 32;
-                if (active && (t & (grp - 1)) == 0) atomicAdd(L.terms + C->rep * L.n_points + j, double(tv));
-            }
-            if constexpr (!GRAD) {
-                cw.flip(fw);  // back to no flips for the next point
-            } else {
-                // co-state lambda = -1/2 Z_0 Z_1 psi, in the same stored form
-                float2 r[NA];
-#pragma unroll
-                for (int i = 0; i < NA; ++i) {
-                    const float sg = ((i ^ (i >> 1)) & 1) ? 0.5f : -0.5f;
-                    r[i] = make_float2(sg * x[i].x, sg * x[i].y);
-                }
-                const float gw2 = active ? 2.f * wgt : 0.f;
-                for (int l = p - 1; l >= 0; --l) {
-                    const float2 mx = __ldg(mix + l);
-                    const float tau = mx.x;
-                    const int k = C->k[l];
-                    const int kr = k < R ? k : R;
-                    const float *__restrict__ kpl = kp + l * kKpow;
-                    // d/d beta_l = 2 sigma Im <r| sum_q X_q |s>, register qubits
-                    // on the untouched state first
-                    float d[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-                    for (int q = 0; q < R; ++q) {
-                        if (q < k) {
-#pragma unroll
-                            for (int i = 0; i < NA; ++i) {
-                                if (i & (1 << q)) continue;
-                                const int i2 = i | (1 << q);
-                                d[i & 3] += imconj(r[i], x[i2]) + imconj(r[i2], x[i]);
-                            }
-                        }
-                    }
-                    float db = (d[0] + d[1]) + (d[2] + d[3]);
-                    // lane qubits: each term is taken after the lane qubits before
-                    // it were undone, which scales it by (1 + tau^2) each; kappa^2
-                    // per undone qubit takes that back out
-#pragma unroll 1
-                    for (int Lb = 0; Lb < kLaneBits; ++Lb) {
-                        const bool mine = (R + Lb) < k;
-                        if (!__any_sync(kFull, mine)) break;
-                        const int m = 1 << Lb;
-                        float e4[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-                        for (int i = 0; i < NA; ++i) {
-                            float2 xo, ro;
-                            xo.x = __shfl_xor_sync(kFull, x[i].x, m);
-                            xo.y = __shfl_xor_sync(kFull, x[i].y, m);
-                            ro.x = __shfl_xor_sync(kFull, r[i].x, m);
-                            ro.y = __shfl_xor_sync(kFull, r[i].y, m);
-                            if (mine) {
-                                e4[i & 3] += imconj(r[i], xo);
-                                x[i] = bfly(x[i], xo, -tau);
-                                r[i] = bfly(r[i], ro, -tau);
-                            }
-                        }
-                        if (mine) db += ((e4[0] + e4[1]) + (e4[2] + e4[3])) * __ldg(kpl + Lb);
-                    }
-                    // undo the register-qubit butterflies on both states
-                    mix_reg<R>(x, kr, -tau);
-                    mix_reg<R>(r, kr, -tau);
-                    add_gp(gw2 * sig * db, L.grad, g, L.n_points, j, 2 * p, p + l);
-                    sig *= __ldg(kpl + k);
-                    if (mx.y != 0.f) cw.flip(prefix_word<MT>(C, k));
-                    // d/d gamma_l = 2 sigma Im <r| C |s>; then undo the phase
-                    float dg4[4] = {0.f, 0.f, 0.f, 0.f};
-                    const float2 *lt = lut + l * L.cmax1;
-                    cw.visit([&](int i, int cv) {
-                        dg4[i & 3] = fmaf(float(cv), imconj(r[i], x[i]), dg4[i & 3]);
-                        if (l > 0) {
-                            const float2 ph = lt[cv];
-                            x[i] = cmulc(x[i], ph);
-                            r[i] = cmulc(r[i], ph);
-                        }
-                    });
-                    add_gp(gw2 * sig * ((dg4[0] + dg4[1]) + (dg4[2] + dg4[3])), L.grad, g, L.n_points, j, 2 * p,
-                           l);
-                }
-            }
-        }
-    }
-}
 
 __global__ void prep_kernel(const PrepArgs a) {
     const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -422,6 +90,8 @@ __global__ void cut_table_kernel(const DevCone *__restrict__ C, uint8_t *__restr
     if (n != C->n && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, 1);
 }
 
+}  // namespace
+
 int occupancy_grid(const void *fn, int block, size_t smem) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
@@ -430,8 +100,6 @@ int occupancy_grid(const void *fn, int block, size_t smem) {
     if (per < 1) per = 1;
     return sms * per;
 }
-
-}  // namespace
 
 cudaError_t launch_prep(const PrepArgs &a, cudaStream_t s) {
     int64_t work = int64_t(a.G) * a.P * a.p * (a.cmax1 > kKpow ? a.cmax1 : kKpow);
@@ -443,33 +111,19 @@ cudaError_t launch_prep(const PrepArgs &a, cudaStream_t s) {
 }
 
 int reg_energy_grid(bool wide, size_t smem) {
-    return wide ? occupancy_grid((const void *)reg_cone_kernel<kRegBitsEnergy, uint64_t, false>, kRegBlock, smem)
-                : occupancy_grid((const void *)reg_cone_kernel<kRegBitsEnergy, uint32_t, false>, kRegBlock, smem);
+    return wide ? occupancy_grid((const void *)reg_cone_kernel<kRegBitsEnergy, uint64_t, false, 0>, kRegBlock, smem)
+                : occupancy_grid((const void *)reg_cone_kernel<kRegBitsEnergy, uint32_t, false, 0>, kRegBlock, smem);
 }
-int reg_grad_grid(bool wide, size_t smem) {
-    return wide ? occupancy_grid((const void *)reg_cone_kernel<kRegBitsGrad, uint64_t, true>, kRegBlock, smem)
-                : occupancy_grid((const void *)reg_cone_kernel<kRegBitsGrad, uint32_t, true>, kRegBlock, smem);
-}
-
-static size_t reg_smem(const RegLaunch &a) {
+size_t reg_smem(const RegLaunch &a) {
     return size_t(kRegBlock / 32) * a.jpt * a.p * a.cmax1 * sizeof(float2);
 }
 
 cudaError_t launch_reg_energy(const RegLaunch &a, bool wide, int grid, cudaStream_t s) {
     const size_t sm = reg_smem(a);
     if (wide)
-        reg_cone_kernel<kRegBitsEnergy, uint64_t, false><<<grid, kRegBlock, sm, s>>>(a);
+        reg_cone_kernel<kRegBitsEnergy, uint64_t, false, 0><<<grid, kRegBlock, sm, s>>>(a);
     else
-        reg_cone_kernel<kRegBitsEnergy, uint32_t, false><<<grid, kRegBlock, sm, s>>>(a);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_reg_grad(const RegLaunch &a, bool wide, int grid, cudaStream_t s) {
-    const size_t sm = reg_smem(a);
-    if (wide)
-        reg_cone_kernel<kRegBitsGrad, uint64_t, true><<<grid, kRegBlock, sm, s>>>(a);
-    else
-        reg_cone_kernel<kRegBitsGrad, uint32_t, true><<<grid, kRegBlock, sm, s>>>(a);
+        reg_cone_kernel<kRegBitsEnergy, uint32_t, false, 0><<<grid, kRegBlock, sm, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,58 @@
+// Adjoint instantiations of the register-resident cone kernel: the depth p
+// is a compile-time constant for p = 1, 2, 3 (layer loops fully unrolled),
+// read at run time otherwise.
+#include "cone_kernel.cuh"
+
+namespace qaoa {
+
+int occupancy_grid(const void *fn, int block, size_t smem);
+size_t reg_smem(const RegLaunch &a);
+
+namespace {
+
+template <typename MT, int PC>
+const void *grad_fn() {
+    return (const void *)reg_cone_kernel<kRegBitsGrad, MT, true, PC>;
+}
+
+template <typename MT>
+const void *grad_fn_for(int p) {
+    switch (p) {
+        case 1: return grad_fn<MT, 1>();
+        case 2: return grad_fn<MT, 2>();
+        case 3: return grad_fn<MT, 3>();
+        default: return grad_fn<MT, 0>();
+    }
+}
+
+template <typename MT, int PC>
+void launch(const RegLaunch &a, int grid, size_t sm, cudaStream_t s) {
+    reg_cone_kernel<kRegBitsGrad, MT, true, PC><<<grid, kRegBlock, sm, s>>>(a);
+}
+
+template <typename MT>
+void launch_for(const RegLaunch &a, int grid, size_t sm, cudaStream_t s) {
+    switch (a.p) {
+        case 1: launch<MT, 1>(a, grid, sm, s); break;
+        case 2: launch<MT, 2>(a, grid, sm, s); break;
+        case 3: launch<MT, 3>(a, grid, sm, s); break;
+        default: launch<MT, 0>(a, grid, sm, s); break;
+    }
+}
+
+}  // namespace
+
+int reg_grad_grid(bool wide, size_t smem, int p) {
+    return occupancy_grid(wide ? grad_fn_for<uint64_t>(p) : grad_fn_for<uint32_t>(p), kRegBlock, smem);
+}
+
+cudaError_t launch_reg_grad(const RegLaunch &a, bool wide, int grid, cudaStream_t s) {
+    const size_t sm = reg_smem(a);
+    if (wide)
+        launch_for<uint64_t>(a, grid, sm, s);
+    else
+        launch_for<uint32_t>(a, grid, sm, s);
+    return cudaGetLastError();
+}
+
+}  // namespace qaoa

@@ -184,6 +184,7 @@ def test_empty_graph_and_isolated_vertices(q):
 @pytest.mark.parametrize("graph,p,P", [
     (I.petersen(), 1, 4), (I.petersen(), 2, 3), (I.cycle(20), 3, 2), (I.torus(8, 8), 2, 2),
     (I.random_regular(30, 3, 4), 2, 2), (I.star(6), 2, 2), ((2, np.array([[0, 1]])), 2, 2),
+    (I.cycle(24), 4, 2), (I.path(9), 5, 2),
 ])
 def test_gradient_matches_oracle_adjoint(q, graph, p, P):
     n, edges = graph
