@@ -312,6 +312,8 @@ extern "C" int qaoa_plan_upload(qaoa_plan *plan) {
             d.col[c.ea[e]] |= 1ull << e;
             d.col[c.eb[e]] |= 1ull << e;
         }
+        for (int l = 0; l < QAOA_MAX_P; ++l)
+            for (int q = 0; q < c.k[l]; ++q) d.pw[l] ^= d.col[q];
         cmax = std::max(cmax, d.m);
         if (c.n_in <= kRegMaxInner)
             reg_idx.push_back(int32_t(i));

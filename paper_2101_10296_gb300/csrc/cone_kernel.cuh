@@ -93,14 +93,6 @@ struct CutWords {
     }
 };
 
-// M of the qubit set [0, k): the flip word of a layer that mixes k qubits.
-template <typename MT>
-__device__ __forceinline__ MT prefix_word(const DevCone *__restrict__ C, int k) {
-    MT v = 0;
-    for (int q = 0; q < k; ++q) v ^= MT(C->col[q]);
-    return v;
-}
-
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
@@ -275,7 +267,7 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? kGradMinBlocks : kEnergyMinB
                 mix_lane<R>(x, k, mx.x);
                 sig *= __ldg(kp + l * kKpow + k);
                 if (mx.y != 0.f) {
-                    const MT f = prefix_word<MT>(C, k);
+                    const MT f = MT(C->pw[l]);
                     cw.flip(f);
                     fw ^= f;
                 }
@@ -304,6 +296,7 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? kGradMinBlocks : kEnergyMinB
                     r[i] = make_float2(sg * x[i].x, sg * x[i].y);
                 }
                 const float gw2 = active ? 2.f * wgt : 0.f;
+                const float sig_end = sig;
 #pragma unroll(PC > 0 ? PC : 1)
                 for (int l = p - 1; l >= 0; --l) {
                     const float2 mx = __ldg(mix + l);
@@ -350,25 +343,35 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? kGradMinBlocks : kEnergyMinB
                         }
                         if (mine) db += ((e4[0] + e4[1]) + (e4[2] + e4[3])) * __ldg(kpl + Lb);
                     }
-                    // undo the register-qubit butterflies on both states
-                    mix_reg<R>(x, kr, -tau);
+                    // undo the register-qubit butterflies (psi only above layer 1: below
+                    // it psi is the layer-1 phase table itself, read back for d/d gamma_1)
+                    if (l > 0) mix_reg<R>(x, kr, -tau);
                     mix_reg<R>(r, kr, -tau);
                     add_gp(gw2 * sig * db, L.grad, g, L.n_points, j, 2 * p, p + l);
                     sig *= __ldg(kpl + k);
-                    if (mx.y != 0.f) cw.flip(prefix_word<MT>(C, k));
+                    if (mx.y != 0.f) cw.flip(MT(C->pw[l]));
                     // d/d gamma_l = 2 sigma Im <r| C |s>; then undo the phase
                     float dg4[4] = {0.f, 0.f, 0.f, 0.f};
                     const float2 *lt = lut + l * L.cmax1;
-                    cw.visit([&](int i, int cv) {
-                        dg4[i & 3] = fmaf(float(cv), imconj(r[i], x[i]), dg4[i & 3]);
-                        if (l > 0) {
+                    if (l > 0) {
+                        cw.visit([&](int i, int cv) {
+                            dg4[i & 3] = fmaf(float(cv), imconj(r[i], x[i]), dg4[i & 3]);
                             const float2 ph = lt[cv];
                             x[i] = cmulc(x[i], ph);
                             r[i] = cmulc(r[i], ph);
-                        }
-                    });
-                    add_gp(gw2 * sig * ((dg4[0] + dg4[1]) + (dg4[2] + dg4[3])), L.grad, g, L.n_points, j, 2 * p,
-                           l);
+                        });
+                    } else {
+                        // The un-mixed psi would be Lambda * exp(-i gamma_1 C) with
+                        // Lambda = prod_l (1 + tau_l^2)^k_l from the unnormalised inverse
+                        // butterflies, and sigma * Lambda = sigma at the end of the forward
+                        // sweep: use the table and that sigma.
+                        cw.visit([&](int i, int cv) {
+                            const float2 ph = (i >> nreg) ? make_float2(0.f, 0.f) : lt[cv];
+                            dg4[i & 3] = fmaf(float(cv), imconj(r[i], ph), dg4[i & 3]);
+                        });
+                    }
+                    add_gp(gw2 * (l > 0 ? sig : sig_end) * ((dg4[0] + dg4[1]) + (dg4[2] + dg4[3])), L.grad, g,
+                           L.n_points, j, 2 * p, l);
                 }
             }
         }

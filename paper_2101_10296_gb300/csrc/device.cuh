@@ -25,6 +25,7 @@ struct alignas(16) DevCone {
     double weight;   // orbit size
     int64_t rep;     // row of this cone in terms[]
     uint64_t col[QAOA_MAX_CONE_QUBITS];
+    uint64_t pw[QAOA_MAX_P];  // M of the qubits layer l mixes, [0, k[l])
 };
 
 // Work list of the register-resident kernels.  Each (cone, point) needs

@@ -389,3 +389,121 @@ def test_autotune_picks_and_caches(q, tmp_path):
     e = plan.energy(th)
     plan.set_tuning()
     assert np.allclose(e.cpu().numpy(), plan.energy(th).cpu().numpy(), rtol=E_REL_TOL, atol=0)
+
+
+# -------------------------------------- full-size configurations, sampled
+
+def _cf_energy(n, edges, g, b, adj):
+    return sum(O.closed_form_p1_term(n, edges, e, g, b, adj) for e in edges)
+
+
+def test_symmetric_families_full_size(q):
+    """Torus 100x100 (p=2), Q_12 and C_5000(1,7,23) (p=1), C_5000(1,7) (p=2),
+    32 points each in one batched plan, orbit-reduced, against the closed form
+    (p = 1), the oracle cone terms (p = 2) and the plain all-edge plan."""
+    graphs1 = [I.hypercube(12), I.circulant(5000, [1, 7, 23])]
+    graphs2 = [I.torus(100, 100), I.circulant(5000, [1, 7])]
+    P = 32
+    for graphs, p in ((graphs1, 1), (graphs2, 2)):
+        theta = np.stack([I.draw_params(p, P, 50 + k) for k in range(len(graphs))])
+        plan = q.Plan(graphs, p)
+        info = plan.info()
+        assert info["n_reps"] == {1: 1 + 3, 2: 1 + 2}[p]
+        e, t = plan.energy(_params(theta), terms=True)
+        e = e.cpu().numpy()
+        t = t.cpu().numpy()
+        plain = q.Plan(graphs, p, orbits=False).energy(_params(theta)).cpu().numpy()
+        assert np.allclose(e, plain, rtol=E_REL_TOL, atol=0)
+        reps = plan.reps()
+        for k, (n, edges) in enumerate(graphs):
+            adj = O.adjacency(n, edges)
+            for j in (0, 17, 31):
+                if p == 1:
+                    ref = _cf_energy(n, edges, theta[k, j, 0], theta[k, j, 1], adj)
+                    assert abs(e[k, j] - ref) <= E_REL_TOL * abs(ref)
+                else:
+                    for r in np.nonzero(reps["graph"] == k)[0]:
+                        ref = O.lightcone_term(n, edges, edges[reps["edge"][r]], theta[k, j], p, adj)
+                        assert abs(t[r, j] - ref) <= 2 * TERM_TOL
+        assert plan.device_status() == 0
+
+
+def test_gradient_configuration_full_size(q):
+    """Energy + gradient at 128 points: 8x8 torus p=2 against the FP64 oracle
+    adjoint; random 3-regular n=24 (seeds 1-4) p=3 (large-state cones) by the
+    orbit on/off agreement, periodicity and sampled oracle terms; 6x6 torus p=3
+    (28-qubit cones) pruned against full-cone large-state schedules."""
+    P = 128
+    n, edges = I.torus(8, 8)
+    theta = I.draw_params(2, P, 4)
+    plan = q.Plan((n, edges), 2)
+    e, g = plan.energy_grad(_params(theta))
+    oid = plan.orbits(0)[0]
+    adj = O.adjacency(n, edges)
+    for j in (0, 77):
+        eref, gref = O.orbit_grad_adjoint(n, edges, theta[j], 2, oid, adj)
+        assert abs(e[0, j].item() - eref) <= E_REL_TOL * abs(eref)
+        _check_grad(g[0, j].cpu().numpy(), gref)
+
+    graphs = [I.random_regular(24, 3, s) for s in (1, 2, 3, 4)]
+    theta = np.stack([I.draw_params(3, P, s) for s in (1, 2, 3, 4)])
+    plan = q.Plan(graphs, 3)
+    assert plan.info()["n_big"] > 0
+    e, g = plan.energy_grad(_params(theta))
+    e_off, g_off = q.Plan(graphs, 3, orbits=False).energy_grad(_params(theta))
+    assert np.allclose(e.cpu().numpy(), e_off.cpu().numpy(), rtol=E_REL_TOL, atol=0)
+    for k in range(4):
+        for j in (0, 64, 127):
+            _check_grad(g[k, j].cpu().numpy(), g_off[k, j].cpu().numpy())
+    shifted = theta.copy()
+    shifted[..., 3:] += np.pi / 2
+    e2 = plan.energy(_params(shifted)).cpu().numpy()
+    assert np.allclose(e2, e.cpu().numpy(), rtol=1e-5, atol=0)
+    _, t = q.Plan(graphs[:1], 3, orbits=False).energy(_params(theta[:1]), terms=True)
+    reps = q.Plan(graphs[:1], 3, orbits=False).reps()
+    small = np.argsort(reps["n_qubits"])[:2]
+    n0, ed0 = graphs[0]
+    for r in small:
+        ref = O.lightcone_term(n0, ed0, ed0[reps["edge"][r]], theta[0, 5], 3)
+        assert abs(t.cpu().numpy()[r, 5] - ref) <= 2 * TERM_TOL
+
+    n, edges = I.torus(6, 6)
+    theta = I.draw_params(3, 4, 6)
+    pr = q.Plan((n, edges), 3)
+    fc = q.Plan((n, edges), 3, full_cone=True)
+    assert pr.info()["max_inner"] == 18 and fc.info()["max_inner"] == 28
+    e1, g1 = pr.energy_grad(_params(theta))
+    e2 = fc.energy(_params(theta))
+    assert np.allclose(e1.cpu().numpy(), e2.cpu().numpy(), rtol=E_REL_TOL, atol=0)
+    e3 = pr.energy(_params(theta))
+    assert np.allclose(e1.cpu().numpy(), e3.cpu().numpy(), rtol=E_REL_TOL, atol=0)
+    assert pr.device_status() == 0 and fc.device_status() == 0
+
+
+def test_mixed_48_graph_batch_p1_256_points(q):
+    """The 48-graph benchmark-shaped mix at p=1 with 256 points per graph in one
+    plan: energies against the closed form and gradients against central
+    differences of the closed form (FP64) on sampled (graph, point) pairs."""
+    specs = I.mixed_benchmark_graphs()
+    graphs = [b() for _, b in specs]
+    P = 256
+    theta = np.stack([I.draw_params(1, P, 1000 + k) for k in range(len(graphs))])
+    plan = q.Plan(graphs, 1)
+    info = plan.info()
+    assert info["n_graphs"] == 48 and info["max_qubits"] <= 26
+    e, g = plan.energy_grad(_params(theta))
+    e = e.cpu().numpy()
+    g = g.cpu().numpy()
+    rng = np.random.default_rng(7)
+    h = 1e-5
+    for k in rng.choice(48, 10, replace=False):
+        n, edges = graphs[k]
+        adj = O.adjacency(n, edges)
+        for j in rng.choice(P, 2, replace=False):
+            gg, bb = theta[k, j]
+            ref = _cf_energy(n, edges, gg, bb, adj)
+            assert abs(e[k, j] - ref) <= E_REL_TOL * abs(ref), specs[k][0]
+            dg = (_cf_energy(n, edges, gg + h, bb, adj) - _cf_energy(n, edges, gg - h, bb, adj)) / (2 * h)
+            db = (_cf_energy(n, edges, gg, bb + h, adj) - _cf_energy(n, edges, gg, bb - h, adj)) / (2 * h)
+            _check_grad(g[k, j], [dg, db])
+    assert plan.device_status() == 0
