@@ -43,7 +43,7 @@ N_VERT, DEG, P_DEPTH, N_POINTS = 2000, 3, 2, 64
 # DRAM bytes per launch of the adjoint cone kernel from one ncu capture of this
 # workload, with the hash of the kernel source they were taken on (a changed
 # kernel reports null until it is profiled again).
-TRAFFIC = {"kernels_sha1": "b8ae06e9e86304cf95ee08324015ecbb584eefe4", "bytes_per_launch": 5875640}
+TRAFFIC = {"kernels_sha1": "fac1b9654b897db51340206c11ed722d7ca0645f", "bytes_per_launch": 6960000}
 
 
 def log(*a):
@@ -62,21 +62,26 @@ def workload():
 def algorithmic_flops(reps, p, grad):
     """FP32 FLOPs of the pruned state-vector circuit per point, summed over reps.
 
-    Per cone with A = 2^n amplitudes and k_l qubits mixed in layer l
-    (FMA = 2 FLOPs): forward = A (6 (p-1) + 6 sum_l k_l + 4) -- phase
-    complex multiply 6 per amplitude from layer 2 on (layer 1 is a table
-    read), RX butterfly 6 per amplitude per mixed qubit, |psi|^2 and the
-    signed accumulation 4; adjoint adds A (2 + 16 sum_l k_l + 5 p + 12 (p-1))
-    -- co-state 2, per mixed qubit the Im<lam|X|psi> term 4 and undoing RX
-    on both states 12, per layer the Im<lam|C|psi> term 5, undoing the phase
-    on both states 12.
+    Counted for the cheapest formulation the kernels use (FMA = 2 FLOPs), per
+    cone with A = 2^n amplitudes and k_l qubits mixed in layer l:
+      forward = A (6 (p-1) + 4 sum_l k_l + 4): the phase complex multiply (6)
+        from layer 2 on (layer 1 is a table read), exp(-i beta X) as
+        kappa (I - i tau X) with kappa kept as a scalar (one FMA per real
+        output: 4 per amplitude per mixed qubit), |psi|^2 with the signed
+        accumulation (4);
+      adjoint adds A (2 + 12 sum_{l>=2} k_l + 8 k_1 + 5 p + 12 (p-1)): the
+        co-state (2); per mixed qubit the Im<lam|X_q|psi> term (4) and undoing
+        the butterfly on both states (8), on the co-state only in layer 1 (4);
+        per layer the Im<lam|C|psi> term (5); undoing the phase on both states
+        above layer 1 (12).
     """
     A = np.ldexp(1.0, reps["n_qubits"].astype(np.int64))
-    ksum = reps["mix_qubits"][:, :p].sum(axis=1).astype(np.float64)
-    fwd = A * (6 * (p - 1) + 6 * ksum + 4)
+    k = reps["mix_qubits"][:, :p].astype(np.float64)
+    ksum = k.sum(axis=1)
+    flops = A * (6 * (p - 1) + 4 * ksum + 4)
     if grad:
-        fwd = fwd + A * (2 + 16 * ksum + 5 * p + 12 * (p - 1))
-    return float(fwd.sum())
+        flops = flops + A * (2 + 12 * (ksum - k[:, 0]) + 8 * k[:, 0] + 5 * p + 12 * (p - 1))
+    return float(flops.sum())
 
 
 def fp32_peak_tflops():

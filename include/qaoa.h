@@ -251,7 +251,7 @@ int qaoa_device_status(const qaoa_plan *plan, int32_t *status);
  * Launch tuning of a plan (applies to every later call).  Any field 0 means
  * "default".
  *   points_per_task  parameter points one warp task of the register kernels
- *                    evaluates for the same cone slots (default: up to 8,
+ *                    evaluates for the same cone slots (default: up to 16,
  *                    while their phase tables fit 6 KB of shared memory)
  *   blocks_per_sm    resident blocks per SM of the persistent grid (default:
  *                    the occupancy limit)

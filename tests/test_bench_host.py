@@ -48,9 +48,9 @@ def test_flop_model_counts():
     import bench
     reps = {"n_qubits": np.array([14, 3]), "mix_qubits": np.array([[6, 2], [2, 2]])}
     fwd = bench.algorithmic_flops(reps, 2, grad=False)
-    assert fwd == 2 ** 14 * (6 + 6 * 8 + 4) + 2 ** 3 * (6 + 6 * 4 + 4)
+    assert fwd == 2 ** 14 * (6 + 4 * 8 + 4) + 2 ** 3 * (6 + 4 * 4 + 4)
     both = bench.algorithmic_flops(reps, 2, grad=True)
-    assert both == fwd + 2 ** 14 * (2 + 16 * 8 + 10 + 12) + 2 ** 3 * (2 + 16 * 4 + 10 + 12)
+    assert both == fwd + 2 ** 14 * (2 + 12 * 2 + 8 * 6 + 10 + 12) + 2 ** 3 * (2 + 12 * 2 + 8 * 2 + 10 + 12)
 
 
 def test_clock_log_parser(tmp_path):
