@@ -38,7 +38,7 @@ __device__ __forceinline__ void add_gp(float v, double *base, int64_t idx) {
 }
 
 template <bool GRAD>
-__global__ void __launch_bounds__(128) big_pass_kernel(const BigLaunch L) {
+__global__ void __launch_bounds__(128) big_pass_kernel(const __grid_constant__ BigLaunch L) {
     const int lane = threadIdx.x & 31;
     const int64_t gw = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
@@ -241,6 +241,67 @@ __global__ void __launch_bounds__(128) big_pass_kernel(const BigLaunch L) {
     }
 }
 
+// A pass made only of mixers: load, butterflies on the tile's qubits, store.
+// No cut words or tables, so far fewer registers and more loads in flight.
+__global__ void __launch_bounds__(128, 4) big_mix_kernel(const __grid_constant__ BigLaunch L) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    const BigPass &ps = L.pass;
+    const int b = ps.b;
+    const int64_t tiles = int64_t(1) << (L.n_in - 10);
+    const int64_t ntask = L.n_items * tiles;
+    const int64_t block_amps = int64_t(1) << L.n_in;
+    for (int64_t task = gw; task < ntask; task += nw) {
+        const int64_t it = task / tiles;
+        const int64_t tile = task - it * tiles;
+        const int64_t item = L.item0 + it;
+        const int64_t per_cone = L.P * L.Y;
+        const int ci = int(item / per_cone);
+        const int64_t j = (item - int64_t(ci) * per_cone) / L.Y;
+        const DevCone *__restrict__ C = L.cones + L.cone_ids[ci];
+        const float2 *__restrict__ cs = L.cs + (int64_t(C->graph) * L.P + j) * L.p;
+        const int64_t lowmask = (int64_t(1) << (b - 5)) - 1;
+        const int64_t xb = ((tile & lowmask) << 5) | ((tile >> (b - 5)) << (b + 5));
+        float2 *__restrict__ sp = L.psi + it * block_amps + xb + lane;
+        float2 x[NR];
+#pragma unroll
+        for (int i = 0; i < NR; ++i) x[i] = sp[int64_t(i) << b];
+        for (int o = 0; o < ps.nops; ++o) {
+            const BigOp op = ps.ops[o];
+            const float2 c_s = __ldg(cs + op.layer);
+            for (int q = op.q0; q < op.q1; ++q) {
+                if (q < 5) {
+                    const int m = 1 << q;
+#pragma unroll
+                    for (int i = 0; i < NR; ++i) {
+                        float2 ot;
+                        ot.x = __shfl_xor_sync(kFull, x[i].x, m);
+                        ot.y = __shfl_xor_sync(kFull, x[i].y, m);
+                        x[i] = rot(x[i], ot, c_s.x, c_s.y);
+                    }
+                } else {
+                    const int rq = q - b;
+#pragma unroll
+                    for (int rb = 0; rb < kBigRegBits; ++rb) {
+                        if (rb != rq) continue;
+#pragma unroll
+                        for (int i = 0; i < NR; ++i) {
+                            if (i & (1 << rb)) continue;
+                            const int i2 = i | (1 << rb);
+                            const float2 a = x[i], bb = x[i2];
+                            x[i] = rot(a, bb, c_s.x, c_s.y);
+                            x[i2] = rot(bb, a, c_s.x, c_s.y);
+                        }
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < NR; ++i) sp[int64_t(i) << b] = x[i];
+    }
+}
+
 __global__ void big_prep_kernel(const double *params, int64_t GPp, int p, float2 *cs) {
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < GPp; i += int64_t(gridDim.x) * blockDim.x) {
         const int64_t gj = i / p, l = i % p;
@@ -270,9 +331,31 @@ int big_grid(bool grad) {
     return sms * (per < 1 ? 1 : per);
 }
 
+static int mix_grid() {
+    static int grid = [] {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, big_mix_kernel, 128, 0);
+        return sms * (per < 1 ? 1 : per);
+    }();
+    return grid;
+}
+
+static bool mix_only(const BigPass &ps) {
+    if (!ps.load_psi || !ps.store_psi || ps.load_lam || ps.store_lam) return false;
+    for (int o = 0; o < ps.nops; ++o)
+        if (ps.ops[o].type != kOpMix) return false;
+    return true;
+}
+
 cudaError_t launch_big_pass(const BigLaunch &a, bool grad, int grid, cudaStream_t s) {
     const int64_t tasks = a.n_items * (int64_t(1) << (a.n_in - 10));
     const int64_t need = (tasks + 3) / 4;
+    if (mix_only(a.pass)) {
+        big_mix_kernel<<<int(std::min<int64_t>(mix_grid(), need < 1 ? 1 : need)), 128, 0, s>>>(a);
+        return cudaGetLastError();
+    }
     const int g = int(std::min<int64_t>(grid, need < 1 ? 1 : need));
     if (grad)
         big_pass_kernel<true><<<g, 128, 0, s>>>(a);
