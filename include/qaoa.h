@@ -53,9 +53,12 @@ enum qaoa_status {
 enum qaoa_flags {
     QAOA_ORBITS_OFF = 0u, /* every edge is its own representative */
     QAOA_ORBITS = 1u,     /* one representative per edge orbit of Aut(G) */
-    QAOA_FULL_CONE = 2u   /* simulate the whole 2^n cone state with the mixer on
+    QAOA_FULL_CONE = 2u,  /* simulate the whole 2^n cone state with the mixer on
                              every cone qubit in every layer (no pruning of the
                              gates that cancel); slower, used for cross-checks */
+    QAOA_SHELL_PLAIN = 4u /* evolve every assignment of the never-mixed shell
+                             qubits as its own block instead of one block per
+                             shell class count vector; slower, for cross-checks */
 };
 
 /* Largest cone handled: qubits per cone and local edges per cone. */
@@ -158,6 +161,20 @@ int qaoa_plan_reps(const qaoa_plan *plan, int32_t *graph, int64_t *edge,
  */
 int qaoa_plan_cone(const qaoa_plan *plan, int64_t rep, int32_t *verts,
                    int32_t *dist, int32_t *cone_edges);
+
+/*
+ * Shell classes of one representative's cone.  The shell qubits (distance p,
+ * never mixed) with the same set of inner neighbours form a class; an inner
+ * block is evolved once per vector of per-class counts of shell qubits set
+ * to 1 and weighted by the product of binomial coefficients, which sums
+ * exactly the same terms as one block per shell assignment (Sec. 2.3: the
+ * shell enters only through the phase, and exchanging two shell qubits of a
+ * class leaves every cut value unchanged).  class_of: host int32[n_qubits],
+ * -1 for inner qubits, else the class index; n_blocks: number of blocks.
+ * Either pointer may be NULL.
+ */
+int qaoa_plan_shell(const qaoa_plan *plan, int64_t rep, int32_t *class_of,
+                    int64_t *n_blocks);
 
 /*
  * Host-only edge-orbit finder on one graph (the plan's orbit step alone),

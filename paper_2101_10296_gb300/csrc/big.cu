@@ -71,9 +71,8 @@ __global__ void __launch_bounds__(128) big_pass_kernel(const __grid_constant__ B
         const int64_t lowmask = (int64_t(1) << (b - 5)) - 1;
         const int64_t xb = ((tile & lowmask) << 5) | ((tile >> (b - 5)) << (b + 5));
         // cut word: shell part ^ fixed inner part ^ lane part, then per register index
-        uint64_t base = 0;
-        for (int q = nin; q < L.n; ++q)
-            if ((y >> (q - nin)) & 1) base ^= C->col[q];
+        float mult = 1.f;
+        uint64_t base = shell_block(C, L.shell, uint32_t(y), mult);
         for (int q = 5; q < nin; ++q)
             if ((xb >> q) & 1) base ^= C->col[q];
 #pragma unroll
@@ -102,7 +101,7 @@ __global__ void __launch_bounds__(128) big_pass_kernel(const __grid_constant__ B
 #pragma unroll
             for (int i = 0; i < NR; ++i) r[i] = lp[int64_t(i) << b];
         }
-        const float wgt = float(C->weight);
+        const float wgt = float(C->weight) * mult;  // orbit size x shell multiplicity
         const float sig = __int_as_float((127 - L.n) << 23);  // 2^-n
         for (int o = 0; o < ps.nops; ++o) {
             const BigOp op = ps.ops[o];

@@ -37,7 +37,8 @@ struct BigLaunch {
     const DevCone *cones;
     const int32_t *cone_ids;  // this shape's cones (plan indices)
     int32_t n, n_in;          // qubits, inner qubits (shared by the shape)
-    int64_t Y;                // shell assignments = 2^(n - n_in)
+    int64_t Y;                // shell blocks per (cone, point)
+    const uint64_t *shell;    // shell table
     int64_t P;
     int32_t p, cmax1;
     int64_t item0, n_items;   // items (cone, point, shell) of this wave

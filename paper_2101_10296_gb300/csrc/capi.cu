@@ -33,9 +33,13 @@ void free_work(DevWork &w) {
 // offset aligned to min(T_c, 32); a new graph starts on a fresh warp.
 int build_work(const std::vector<DevCone> &hc, const std::vector<int32_t> &idx, int R, DevWork &w) {
     std::vector<int32_t> order(idx);
-    auto T = [&](int32_t i) { return int64_t(1) << std::max(hc[i].n - R, 0); };
+    auto G = [&](int32_t i) { return int64_t(1) << std::max(hc[i].n_in - R, 0); };
+    auto T = [&](int32_t i) {
+        const int sb = std::max(R - hc[i].n_in, 0);
+        return ((hc[i].n_blocks + (int64_t(1) << sb) - 1) >> sb) * G(i);
+    };
     std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
-        if (T(a) != T(b)) return T(a) > T(b);
+        if (G(a) != G(b)) return G(a) > G(b);
         return hc[a].graph < hc[b].graph;
     });
     std::vector<int64_t> start(order.size() + 1, 0);
@@ -75,6 +79,7 @@ int build_work(const std::vector<DevCone> &hc, const std::vector<int32_t> &idx, 
 RegWork as_reg(const qaoa_device_plan *d, const DevWork &w) {
     RegWork r;
     r.cones = d->cones;
+    r.shell = d->shell;
     r.order = w.order;
     r.start = w.prefix;
     r.warp_first = w.warp_first;
@@ -127,7 +132,7 @@ cudaError_t run_big(const qaoa_device_plan *d, const qaoa_plan *plan, int64_t P,
     for (const BigShape &bs : d->big) {
         if (e != cudaSuccess) break;
         const int64_t block_bytes = (int64_t(1) << bs.n_in) * int64_t(sizeof(float2)) * (g ? 2 : 1);
-        const int64_t Y = int64_t(1) << (bs.n - bs.n_in);
+        const int64_t Y = bs.n_blocks;
         const int64_t items = int64_t(bs.cones.size()) * P * Y;
         const int64_t wave = std::max<int64_t>(1, std::min<int64_t>(items, int64_t(d->big_budget) / block_bytes));
         float2 *scratch = nullptr;
@@ -146,6 +151,7 @@ cudaError_t run_big(const qaoa_device_plan *d, const qaoa_plan *plan, int64_t P,
         B.cs = cs;
         B.psi = scratch;
         B.lam = g ? scratch + size_t(wave) * (size_t(1) << bs.n_in) : nullptr;
+        B.shell = d->shell;
         B.energy = energy;
         B.grad = grad;
         B.terms = terms;
@@ -278,6 +284,7 @@ extern "C" void qaoa_device_release(qaoa_plan *plan) {
     for (auto &bs : d->big) cudaFree(bs.d_cones);
     cudaFree(d->half_edges);
     cudaFree(d->status);
+    cudaFree(d->shell);
     for (auto &pr : d->events) {
         cudaEventDestroy(pr.first);
         cudaEventDestroy(pr.second);
@@ -294,6 +301,7 @@ extern "C" int qaoa_plan_upload(qaoa_plan *plan) {
     }
     if (plan->dev) return check_device(plan);
     std::vector<DevCone> hc(plan->cones.size());
+    std::vector<uint64_t> shell_tab;
     int32_t cmax = 0;
     std::vector<int32_t> reg_idx;
     int64_t n_big = 0;
@@ -314,6 +322,27 @@ extern "C" int qaoa_plan_upload(qaoa_plan *plan) {
         }
         for (int l = 0; l < QAOA_MAX_P; ++l)
             for (int q = 0; q < c.k[l]; ++q) d.pw[l] ^= d.col[q];
+        d.n_blocks = c.n_blocks;
+        d.n_cls = int32_t(c.shell_classes.size());
+        d.cls_off = int32_t(shell_tab.size());
+        for (const auto &cls : c.shell_classes) {
+            const size_t sz = cls.size();
+            shell_tab.push_back(sz);
+            uint64_t pm = 0;
+            shell_tab.push_back(0);
+            for (size_t a = 0; a < sz; ++a) {
+                pm ^= d.col[cls[a]];
+                shell_tab.push_back(pm);
+            }
+            double bin = 1.0;  // binomial(sz, nc), exact in double for sz <= 32
+            for (size_t nc = 0; nc <= sz; ++nc) {
+                const float f = float(bin);
+                uint32_t bits;
+                std::memcpy(&bits, &f, sizeof bits);
+                shell_tab.push_back(bits);
+                bin = bin * double(sz - nc) / double(nc + 1);
+            }
+        }
         cmax = std::max(cmax, d.m);
         if (c.n_in <= kRegMaxInner)
             reg_idx.push_back(int32_t(i));
@@ -327,12 +356,13 @@ extern "C" int qaoa_plan_upload(qaoa_plan *plan) {
         std::vector<int32_t> kv(c.k, c.k + plan->p);
         BigShape *shape = nullptr;
         for (auto &bs : d->big)
-            if (bs.n == c.n && bs.n_in == c.n_in && bs.k == kv) shape = &bs;
+            if (bs.n == c.n && bs.n_in == c.n_in && bs.k == kv && bs.n_blocks == c.n_blocks) shape = &bs;
         if (!shape) {
             d->big.emplace_back();
             shape = &d->big.back();
             shape->n = c.n;
             shape->n_in = c.n_in;
+            shape->n_blocks = c.n_blocks;
             shape->k = kv;
             shape->fwd = big_forward_passes(c.n_in, plan->p, kv.data());
             shape->grad = big_grad_passes(c.n_in, plan->p, kv.data());
@@ -360,6 +390,13 @@ extern "C" int qaoa_plan_upload(qaoa_plan *plan) {
             rc = cuda_fail(e, "cudaMalloc");
         else
             cudaMemcpy(bs.d_cones, bs.cones.data(), bs.cones.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    }
+    if (rc == QAOA_OK) {
+        if (shell_tab.empty()) shell_tab.push_back(0);
+        if ((e = cudaMalloc(&d->shell, shell_tab.size() * sizeof(uint64_t))) != cudaSuccess)
+            rc = cuda_fail(e, "cudaMalloc");
+        else
+            cudaMemcpy(d->shell, shell_tab.data(), shell_tab.size() * sizeof(uint64_t), cudaMemcpyHostToDevice);
     }
     if (rc == QAOA_OK) rc = build_work(hc, reg_idx, kRegBitsEnergy, d->reg_e);
     if (rc == QAOA_OK) rc = build_work(hc, reg_idx, kRegBitsGrad, d->reg_g);

@@ -81,6 +81,47 @@ struct CutWords {
             hi[k] = v;
         }
     }
+    // Register index i of thread t: bits [0, nr) are inner qubits (nr =
+    // min(n_in, R)), bits [nr, R) pick one of S = 2^(R - nr) blocks; thread t
+    // holds inner qubits R..n_in-1 in its low bits and the block group above.
+    // hi[k] gets the inner part, the block's shell word, and wk[k] the block's
+    // multiplicity (0 for block numbers past the cone's n_blocks).
+    __device__ __forceinline__ void init_blocks(const DevCone *__restrict__ C, const uint64_t *__restrict__ tab,
+                                                int64_t t, float (&wk)[1 << (R - 2)]) {
+        const int n_in = C->n_in;
+        const int nr = n_in < R ? n_in : R;
+        const int gb = n_in > R ? n_in - R : 0;
+        const MT c0 = MT(C->col[0]), c1 = MT(C->col[1]);
+        lo[0] = 0;
+        lo[1] = c0;
+        lo[2] = c1;
+        lo[3] = c0 ^ c1;
+        MT base = 0;
+        for (int q = R; q < n_in; ++q)
+            if ((t >> (q - R)) & 1) base ^= MT(C->col[q]);
+        const uint32_t group = uint32_t(t >> gb);
+        const int sb = R - nr;
+        MT cm[R - 2];
+#pragma unroll
+        for (int b = 0; b < R - 2; ++b) cm[b] = (2 + b < nr) ? MT(C->col[2 + b]) : MT(0);
+        const int inner_bits = nr - 2;  // register bits 2..nr-1 are inner
+        MT shell = 0;
+        float mult = 0.f;
+#pragma unroll
+        for (int k = 0; k < (1 << (R - 2)); ++k) {
+            if ((k & ((1 << inner_bits) - 1)) == 0) {
+                const uint32_t beta = (group << sb) + uint32_t(k >> inner_bits);
+                shell = MT(shell_block(C, tab, beta, mult));
+                if (beta >= uint64_t(C->n_blocks)) mult = 0.f;
+            }
+            MT v = base ^ shell;
+#pragma unroll
+            for (int b = 0; b < R - 2; ++b)
+                if ((k >> b) & 1) v ^= cm[b];
+            hi[k] = v;
+            wk[k] = mult;
+        }
+    }
     __device__ __forceinline__ void flip(MT f) {
 #pragma unroll
         for (int k = 0; k < (1 << (R - 2)); ++k) hi[k] ^= f;
@@ -168,13 +209,32 @@ __device__ __forceinline__ void mix_lane(float2 (&x)[1 << R], int k, float tau) 
     }
 }
 
-// sum_i |x_i|^2 (-1)^(i_0 xor i_1)
+// sum_i w_(i>>2) |x_i|^2 (-1)^(i_0 xor i_1)
 template <int R>
-__device__ __forceinline__ float zz_partial(const float2 (&x)[1 << R]) {
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+__device__ __forceinline__ float zz_partial(const float2 (&x)[1 << R], const float (&wk)[1 << (R - 2)]) {
+    float tot = 0.f;
 #pragma unroll
-    for (int i = 0; i < (1 << R); ++i) acc[i & 3] = fmaf(x[i].x, x[i].x, fmaf(x[i].y, x[i].y, acc[i & 3]));
-    return (acc[0] + acc[3]) - (acc[1] + acc[2]);
+    for (int k = 0; k < (1 << (R - 2)); ++k) {
+        const float2 a = x[4 * k], b = x[4 * k + 1], c = x[4 * k + 2], d = x[4 * k + 3];
+        const float pos = fmaf(a.x, a.x, fmaf(a.y, a.y, fmaf(d.x, d.x, d.y * d.y)));
+        const float neg = fmaf(b.x, b.x, fmaf(b.y, b.y, fmaf(c.x, c.x, c.y * c.y)));
+        tot = fmaf(wk[k], pos - neg, tot);
+    }
+    return tot;
+}
+
+// Sum of v over the lanes of each run of equal keys (runs are contiguous);
+// the result is valid in the run's first lane, which returns true.
+__device__ __forceinline__ bool seg_sum(float &v, int key) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float ov = __shfl_down_sync(kFull, v, o);
+        const int ok = __shfl_down_sync(kFull, key, o);
+        if (lane + o < 32 && ok == key) v += ov;
+    }
+    const int prev = __shfl_up_sync(kFull, key, 1);
+    return lane == 0 || prev != key;
 }
 
 // Adds v (summed over the warp in FP32) into base[(g*P + j)*stride + comp]
@@ -216,19 +276,25 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? kGradMinBlocks : kEnergyMinB
             while (W.start[ci + 1] <= slot) ++ci;
         const DevCone *__restrict__ C = W.cones + W.order[ci];
         int n = C->n;
-        bool active = slot < W.slots && slot < W.start[ci] + (int64_t(1) << (n > R ? n - R : 0));
-        if (n < 2 || n > QAOA_MAX_CONE_QUBITS || C->n_in > R + kLaneBits) {
+        const int gbits = C->n_in > R ? C->n_in - R : 0;
+        const int sbits = C->n_in < R ? R - C->n_in : 0;
+        const int64_t Tc = ((C->n_blocks + (int64_t(1) << sbits) - 1) >> sbits) << gbits;
+        bool active = slot < W.slots && slot < W.start[ci] + Tc;
+        if (n < 2 || n > QAOA_MAX_CONE_QUBITS || C->n_in < 2 || C->n_in > R + kLaneBits) {
             if (active) atomicOr(L.status, 1);
             active = false;
             n = 2;
         }
         const int g = C->graph;  // the same on every lane (padded work list)
         const int64_t t = active ? slot - W.start[ci] : 0;
-        const int nreg = n < R ? n : R;
-        const bool unpadded = __all_sync(kFull, n >= R);
         const float wgt = float(C->weight);
         CutWords<R, MT> cw;
-        cw.init(C, n, t);
+        float wk[NA / 4];
+        cw.init_blocks(C, W.shell, t, wk);
+        if (!active) {
+#pragma unroll
+            for (int k = 0; k < NA / 4; ++k) wk[k] = 0.f;
+        }
         // stage the phase tables of points j0 .. j0+jn-1 of graph g
         __syncwarp();
         {
@@ -245,14 +311,7 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? kGradMinBlocks : kEnergyMinB
 
             float2 x[NA];
             // layer 1 phase on |+>: amplitude exp(-i gamma_1 C(z)) (2^-n/2 kept in sigma)
-            if (unpadded) {
-                cw.visit([&](int i, int c) { x[i] = lut[c]; });
-            } else {
-                cw.visit([&](int i, int c) {
-                    const float2 ph = lut[c];
-                    x[i] = (i >> nreg) ? make_float2(0.f, 0.f) : ph;
-                });
-            }
+            cw.visit([&](int i, int c) { x[i] = lut[c]; });
             float sig = __int_as_float((127 - n) << 23);  // 2^-n
             MT fw = 0;                                      // accumulated flip word
 #pragma unroll(PC > 0 ? PC : 1)
@@ -272,18 +331,12 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? kGradMinBlocks : kEnergyMinB
                     fw ^= f;
                 }
             }
-            const float tl = active ? zz_partial<R>(x) : 0.f;
+            const float tl = zz_partial<R>(x, wk);
             add_gp(-0.5f * wgt * sig * tl, L.energy, g, L.n_points, j, 1, 0);
             if (L.terms) {
-                const int64_t Tc = int64_t(1) << (n > R ? n - R : 0);
                 float tv = sig * tl;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const float ov = __shfl_xor_sync(kFull, tv, o);
-                    if (o < Tc) tv += ov;
-                }
-                const int64_t grp = Tc < 32 ? Tc : 32;
-                if (active && (t & (grp - 1)) == 0) atomicAdd(L.terms + C->rep * L.n_points + j, double(tv));
+                if (seg_sum(tv, active ? ci : -1) && active)
+                    atomicAdd(L.terms + C->rep * L.n_points + j, double(tv));
             }
             if constexpr (!GRAD) {
                 cw.flip(fw);  // back to no flips for the next point
@@ -306,7 +359,9 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? kGradMinBlocks : kEnergyMinB
                     const float *__restrict__ kpl = kp + l * kKpow;
                     // d/d beta_l = 2 sigma Im <r| sum_q X_q |s>, register qubits
                     // on the untouched state first
-                    float d[4] = {0.f, 0.f, 0.f, 0.f};
+                    float d[NA / 4];
+#pragma unroll
+                    for (int kk = 0; kk < NA / 4; ++kk) d[kk] = 0.f;
 #pragma unroll
                     for (int q = 0; q < R; ++q) {
                         if (q < k) {
@@ -314,11 +369,13 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? kGradMinBlocks : kEnergyMinB
                             for (int i = 0; i < NA; ++i) {
                                 if (i & (1 << q)) continue;
                                 const int i2 = i | (1 << q);
-                                d[i & 3] += imconj(r[i], x[i2]) + imconj(r[i2], x[i]);
+                                d[i >> 2] += imconj(r[i], x[i2]) + imconj(r[i2], x[i]);
                             }
                         }
                     }
-                    float db = (d[0] + d[1]) + (d[2] + d[3]);
+                    float db = 0.f;
+#pragma unroll
+                    for (int kk = 0; kk < NA / 4; ++kk) db = fmaf(wk[kk], d[kk], db);
                     // lane qubits: each term is taken after the lane qubits before
                     // it were undone, which scales it by (1 + tau^2) each; kappa^2
                     // per undone qubit takes that back out
@@ -327,7 +384,9 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? kGradMinBlocks : kEnergyMinB
                         const bool mine = (R + Lb) < k;
                         if (!__any_sync(kFull, mine)) break;
                         const int m = 1 << Lb;
-                        float e4[4] = {0.f, 0.f, 0.f, 0.f};
+                        float e4[NA / 4];
+#pragma unroll
+                        for (int kk = 0; kk < NA / 4; ++kk) e4[kk] = 0.f;
 #pragma unroll
                         for (int i = 0; i < NA; ++i) {
                             float2 xo, ro;
@@ -336,12 +395,17 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? kGradMinBlocks : kEnergyMinB
                             ro.x = __shfl_xor_sync(kFull, r[i].x, m);
                             ro.y = __shfl_xor_sync(kFull, r[i].y, m);
                             if (mine) {
-                                e4[i & 3] += imconj(r[i], xo);
+                                e4[i >> 2] += imconj(r[i], xo);
                                 x[i] = bfly(x[i], xo, -tau);
                                 r[i] = bfly(r[i], ro, -tau);
                             }
                         }
-                        if (mine) db += ((e4[0] + e4[1]) + (e4[2] + e4[3])) * __ldg(kpl + Lb);
+                        if (mine) {
+                            float e = 0.f;
+#pragma unroll
+                            for (int kk = 0; kk < NA / 4; ++kk) e = fmaf(wk[kk], e4[kk], e);
+                            db += e * __ldg(kpl + Lb);
+                        }
                     }
                     // undo the register-qubit butterflies (psi only above layer 1: below
                     // it psi is the layer-1 phase table itself, read back for d/d gamma_1)
@@ -351,11 +415,13 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? kGradMinBlocks : kEnergyMinB
                     sig *= __ldg(kpl + k);
                     if (mx.y != 0.f) cw.flip(MT(C->pw[l]));
                     // d/d gamma_l = 2 sigma Im <r| C |s>; then undo the phase
-                    float dg4[4] = {0.f, 0.f, 0.f, 0.f};
+                    float dg4[NA / 4];
+#pragma unroll
+                    for (int kk = 0; kk < NA / 4; ++kk) dg4[kk] = 0.f;
                     const float2 *lt = lut + l * L.cmax1;
                     if (l > 0) {
                         cw.visit([&](int i, int cv) {
-                            dg4[i & 3] = fmaf(float(cv), imconj(r[i], x[i]), dg4[i & 3]);
+                            dg4[i >> 2] = fmaf(float(cv), imconj(r[i], x[i]), dg4[i >> 2]);
                             const float2 ph = lt[cv];
                             x[i] = cmulc(x[i], ph);
                             r[i] = cmulc(r[i], ph);
@@ -366,12 +432,13 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? kGradMinBlocks : kEnergyMinB
                         // butterflies, and sigma * Lambda = sigma at the end of the forward
                         // sweep: use the table and that sigma.
                         cw.visit([&](int i, int cv) {
-                            const float2 ph = (i >> nreg) ? make_float2(0.f, 0.f) : lt[cv];
-                            dg4[i & 3] = fmaf(float(cv), imconj(r[i], ph), dg4[i & 3]);
+                            dg4[i >> 2] = fmaf(float(cv), imconj(r[i], lt[cv]), dg4[i >> 2]);
                         });
                     }
-                    add_gp(gw2 * (l > 0 ? sig : sig_end) * ((dg4[0] + dg4[1]) + (dg4[2] + dg4[3])), L.grad, g,
-                           L.n_points, j, 2 * p, l);
+                    float dgs = 0.f;
+#pragma unroll
+                    for (int kk = 0; kk < NA / 4; ++kk) dgs = fmaf(wk[kk], dg4[kk], dgs);
+                    add_gp(gw2 * (l > 0 ? sig : sig_end) * dgs, L.grad, g, L.n_points, j, 2 * p, l);
                 }
             }
         }

@@ -24,22 +24,52 @@ struct alignas(16) DevCone {
     int32_t k[QAOA_MAX_P];  // layer l mixes qubits [0, k[l])
     double weight;   // orbit size
     int64_t rep;     // row of this cone in terms[]
+    int64_t n_blocks;  // shell blocks: prod over shell classes of (size + 1)
+    int32_t n_cls;     // shell classes
+    int32_t cls_off;   // this cone's entries in the shell table
     uint64_t col[QAOA_MAX_CONE_QUBITS];
     uint64_t pw[QAOA_MAX_P];  // M of the qubits layer l mixes, [0, k[l])
 };
 
-// Work list of the register-resident kernels.  Each (cone, point) needs
-// T_c = 2^max(n_c - R, 0) threads (R register qubits per thread).  Cones are
-// sorted by (T_c descending, graph) and each cone's slots start at start[i];
-// a graph change inside a T_c class is padded to the next multiple of 32
-// slots, so every cone's first slot is aligned to min(T_c, 32) lanes and no
-// warp spans two graphs.  A warp task covers 32 consecutive slots for
+// Shell table, per cone from cls_off, per class c of size s: word 0 = s,
+// words 1..s+1 = XOR of col[] over the class's first 0..s qubits, words
+// s+2..2s+2 = binomial(s, 0..s) as float bits.  Block beta of a cone is the
+// mixed-radix number (n_0, n_1, ...) with 0 <= n_c <= s_c, least significant
+// class first: its shell word is the XOR of the classes' prefix words for
+// n_c and its multiplicity the product of binomial(s_c, n_c).
+__device__ __forceinline__ uint64_t shell_block(const DevCone *__restrict__ C, const uint64_t *__restrict__ tab,
+                                                uint32_t beta, float &mult) {
+    const uint64_t *t = tab + C->cls_off;
+    uint64_t m = 0;
+    float w = 1.f;
+    for (int c = 0; c < C->n_cls; ++c) {
+        const uint32_t sz = uint32_t(t[0]);
+        const uint32_t q = beta / (sz + 1);
+        const uint32_t nc = beta - q * (sz + 1);
+        beta = q;
+        m ^= t[1 + nc];
+        w *= __uint_as_float(uint32_t(t[2 + sz + nc]));
+        t += 2 * sz + 3;
+    }
+    mult = w;
+    return m;
+}
+
+// Work list of the register-resident kernels.  An inner block of 2^n_in
+// amplitudes takes G = 2^max(n_in - R, 0) threads (R register qubits per
+// thread); when n_in < R a thread holds S = 2^(R - n_in) blocks.  A (cone,
+// point) needs T_c = ceil(B / S) * G threads for its B shell blocks.  Cones
+// are sorted by (G descending, graph) and each cone's slots start at
+// start[i]; a graph change is padded to the next multiple of 32 slots, so
+// every cone's first slot is aligned to min(G, 32) lanes and no warp spans
+// two graphs.  A warp task covers 32 consecutive slots for
 // `jpt` consecutive parameter points of that graph.
 struct RegWork {
     const DevCone *cones = nullptr;     // plan order
     const int32_t *order = nullptr;     // sorted position -> plan index
     const int64_t *start = nullptr;     // [n+1] first slot of each sorted cone
     const int32_t *warp_first = nullptr;  // sorted index of the cone at slot 32*w
+    const uint64_t *shell = nullptr;    // shell table
     int32_t n_cones = 0;
     int64_t slots = 0;                  // slots per point (with padding)
     int64_t warps = 0;                  // warps per point

@@ -19,6 +19,7 @@ struct DevWork {
 // Cones of one shape (n, n_in, k_1..k_p) on the large-state path.
 struct BigShape {
     int32_t n = 0, n_in = 0;
+    int64_t n_blocks = 1;  // shell blocks per (cone, point)
     std::vector<int32_t> k;
     std::vector<int32_t> cones;  // plan indices
     int32_t *d_cones = nullptr;
@@ -33,6 +34,7 @@ struct qaoa_device_plan {
     std::vector<BigShape> big;
     size_t big_budget = size_t(1) << 30;  // scratch bytes per call for big cones
     double *half_edges = nullptr;
+    uint64_t *shell = nullptr;  // shell table (see DevCone)
     int32_t *status = nullptr;
     int32_t cmax1 = 1;
     int64_t n_big = 0;

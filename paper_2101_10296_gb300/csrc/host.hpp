@@ -49,11 +49,16 @@ struct Cone {
     int32_t k[QAOA_MAX_P] = {0};  // layer l mixes local qubits [0, k[l])
     std::vector<int32_t> verts, dist;
     std::vector<int32_t> ea, eb;  // local edges (a < b), sorted
+    // Shell (never-mixed) qubits grouped by their set of inner neighbours;
+    // one block per vector of per-class counts of shell qubits set to 1.
+    std::vector<std::vector<int32_t>> shell_classes;
+    int64_t n_blocks = 1;  // prod over classes of (size + 1)
 };
 
 // Fills cone for edge `e` of g at depth p.  full_cone: mix every qubit in
-// every layer.  Returns QAOA_OK or QAOA_E_CONE_TOO_LARGE.
-int extract_cone(const Graph &g, int64_t e, int32_t p, bool full_cone, int32_t max_qubits,
+// every layer.  shell_plain: one class per shell qubit (every assignment its
+// own block).  Returns QAOA_OK or QAOA_E_CONE_TOO_LARGE.
+int extract_cone(const Graph &g, int64_t e, int32_t p, bool full_cone, bool shell_plain, int32_t max_qubits,
                  std::vector<int32_t> &dist_scratch, Cone &c, std::string &err);
 
 void set_error(const std::string &msg);

@@ -125,6 +125,7 @@ extern "C" int qaoa_energy_noalloc(const qaoa_plan *plan, int64_t n_points, cons
         L.work.order = d->reg_e.order;
         L.work.start = d->reg_e.prefix;
         L.work.warp_first = d->reg_e.warp_first;
+        L.work.shell = d->shell;
         L.work.n_cones = d->reg_e.n;
         L.work.slots = d->reg_e.slots;
         L.work.warps = d->reg_e.warps;
@@ -153,7 +154,7 @@ extern "C" int qaoa_energy_noalloc(const qaoa_plan *plan, int64_t n_points, cons
         for (const BigShape &bs : d->big) {
             if (e != cudaSuccess) break;
             const size_t block_bytes = (size_t(1) << bs.n_in) * sizeof(float2);
-            const int64_t Y = int64_t(1) << (bs.n - bs.n_in);
+            const int64_t Y = bs.n_blocks;
             const int64_t items = int64_t(bs.cones.size()) * n_points * Y;
             const int64_t wave = std::max<int64_t>(1, std::min<int64_t>(items, int64_t(block_room / block_bytes)));
             BigLaunch B{};
@@ -168,6 +169,7 @@ extern "C" int qaoa_energy_noalloc(const qaoa_plan *plan, int64_t n_points, cons
             B.lut = lut;
             B.cs = cs;
             B.psi = reinterpret_cast<float2 *>(blocks);
+            B.shell = d->shell;
             B.lam = nullptr;
             B.energy = energy_dev;
             B.grad = nullptr;

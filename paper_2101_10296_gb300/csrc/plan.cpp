@@ -22,7 +22,7 @@ void set_error(const std::string &msg) { g_last_error = msg; }
 // support is the ball of radius p around the edge.  Mixers of layer l only
 // matter on qubits within distance p-l, and the terms that matter are the
 // edges with an endpoint within distance p-1.
-int extract_cone(const Graph &g, int64_t e, int32_t p, bool full_cone, int32_t max_qubits,
+int extract_cone(const Graph &g, int64_t e, int32_t p, bool full_cone, bool shell_plain, int32_t max_qubits,
                  std::vector<int32_t> &dist, Cone &c, std::string &err) {
     const int32_t u = g.eu[e], v = g.ev[e];
     std::vector<int32_t> ball{u, v};
@@ -107,6 +107,35 @@ int extract_cone(const Graph &g, int64_t e, int32_t p, bool full_cone, int32_t m
         }
         c.k[l] = full_cone ? (l < p ? c.n : 0) : k;
     }
+    // Shell classes.  A shell qubit (distance p) is never mixed and meets the
+    // phases only through its cone edges, all of which go to inner qubits; two
+    // shell qubits with the same inner neighbours can be exchanged without
+    // changing any cut value, so an inner block's evolution depends on the
+    // shell assignment only through how many qubits of each class are 1.
+    c.shell_classes.clear();
+    c.n_blocks = 1;
+    if (c.n_in < c.n) {
+        std::vector<uint64_t> nb(size_t(c.n), 0);
+        for (size_t i = 0; i < c.ea.size(); ++i) {
+            const int32_t a = c.ea[i], b = c.eb[i];
+            if (a >= c.n_in && b < c.n_in) nb[a] |= 1ull << b;
+            if (b >= c.n_in && a < c.n_in) nb[b] |= 1ull << a;
+        }
+        for (int32_t q = c.n_in; q < c.n; ++q) {
+            bool placed = false;
+            if (!shell_plain) {
+                for (auto &cls : c.shell_classes) {
+                    if (nb[cls[0]] == nb[q]) {
+                        cls.push_back(q);
+                        placed = true;
+                        break;
+                    }
+                }
+            }
+            if (!placed) c.shell_classes.push_back({q});
+        }
+        for (auto &cls : c.shell_classes) c.n_blocks *= int64_t(cls.size()) + 1;
+    }
     return QAOA_OK;
 }
 
@@ -159,7 +188,7 @@ extern "C" int qaoa_plan_graphs(int32_t n_graphs, const int32_t *n_vertices, con
         set_error("p must be in [1, QAOA_MAX_P]");
         return QAOA_E_INVALID;
     }
-    if (flags & ~uint32_t(QAOA_ORBITS | QAOA_FULL_CONE)) {
+    if (flags & ~uint32_t(QAOA_ORBITS | QAOA_FULL_CONE | QAOA_SHELL_PLAIN)) {
         set_error("unknown flag bits");
         return QAOA_E_INVALID;
     }
@@ -236,8 +265,8 @@ extern "C" int qaoa_plan_graphs(int32_t n_graphs, const int32_t *n_vertices, con
             c.graph = g;
             c.edge = reps[i].second;
             c.weight = size_of[g][reps[i].second];
-            rcs[i] = extract_cone(graphs[g], c.edge, p, (flags & QAOA_FULL_CONE) != 0, max_cone_qubits, dist, c,
-                                  errs[t]);
+            rcs[i] = extract_cone(graphs[g], c.edge, p, (flags & QAOA_FULL_CONE) != 0,
+                                  (flags & QAOA_SHELL_PLAIN) != 0, max_cone_qubits, dist, c, errs[t]);
         });
         for (size_t i = 0; i < reps.size(); ++i) {
             if (rcs[i] != QAOA_OK) {
@@ -246,7 +275,7 @@ extern "C" int qaoa_plan_graphs(int32_t n_graphs, const int32_t *n_vertices, con
                 Cone c;
                 std::string err;
                 extract_cone(graphs[reps[i].first], reps[i].second, p, (flags & QAOA_FULL_CONE) != 0,
-                             max_cone_qubits, dist, c, err);
+                             (flags & QAOA_SHELL_PLAIN) != 0, max_cone_qubits, dist, c, err);
                 set_error("graph " + std::to_string(reps[i].first) + ": " + err);
                 int rc = rcs[i];
                 delete pl;
@@ -356,5 +385,20 @@ extern "C" int qaoa_edge_orbits(int32_t n_vertices, int64_t n_edges, const int32
     if (n_generators) *n_generators = o.n_generators;
     if (log10_aut) *log10_aut = o.log10_aut;
     if (complete) *complete = o.complete ? 1 : 0;
+    return QAOA_OK;
+}
+
+extern "C" int qaoa_plan_shell(const qaoa_plan *plan, int64_t rep, int32_t *class_of, int64_t *n_blocks) {
+    if (!plan || rep < 0 || rep >= int64_t(plan->cones.size())) {
+        set_error("bad plan or representative index");
+        return QAOA_E_INVALID;
+    }
+    const Cone &c = plan->cones[rep];
+    if (class_of) {
+        std::fill(class_of, class_of + c.n, -1);
+        for (size_t k = 0; k < c.shell_classes.size(); ++k)
+            for (int32_t q : c.shell_classes[k]) class_of[q] = int32_t(k);
+    }
+    if (n_blocks) *n_blocks = c.n_blocks;
     return QAOA_OK;
 }

@@ -25,6 +25,7 @@ QAOA_E_DEVICE = -5
 ORBITS_OFF = 0
 ORBITS = 1
 FULL_CONE = 2
+SHELL_PLAIN = 4
 
 
 class QAOAError(RuntimeError):
@@ -63,6 +64,7 @@ _SIGS = {
     "qaoa_plan_orbits": (C.c_int, [_P, C.c_int32, _I32P, _I64P, _F64P, _I32P]),
     "qaoa_plan_reps": (C.c_int, [_P, _I32P, _I64P, _I32P, _I32P, _I32P, _I32P, _I32P]),
     "qaoa_plan_cone": (C.c_int, [_P, C.c_int64, _I32P, _I32P, _I32P]),
+    "qaoa_plan_shell": (C.c_int, [_P, C.c_int64, _I32P, _I64P]),
     "qaoa_edge_orbits": (C.c_int, [C.c_int32, C.c_int64, _I32P, C.c_int64, _I32P, _I64P, _I64P, _F64P, _I32P]),
     "qaoa_plan_upload": (C.c_int, [_P]),
     "qaoa_cut_table": (C.c_int, [_P, C.c_int64, _P, _P]),
@@ -132,7 +134,8 @@ def _stream_handle(stream=None):
 class Plan:
     """A planned batch of graphs (orbits + cones), owning its device copy."""
 
-    def __init__(self, graphs, p, orbits=True, full_cone=False, max_cone_qubits=0, search_budget=0):
+    def __init__(self, graphs, p, orbits=True, full_cone=False, max_cone_qubits=0, search_budget=0,
+                 shell_plain=False):
         if isinstance(graphs, tuple):
             graphs = [graphs]
         nv = _i32([g[0] for g in graphs])
@@ -144,7 +147,7 @@ class Plan:
             offs.append(offs[-1] + e.shape[0])
         edges = _i32(np.concatenate(rows) if rows else np.zeros((0, 2)))
         offs = np.asarray(offs, dtype=np.int64)
-        flags = (ORBITS if orbits else ORBITS_OFF) | (FULL_CONE if full_cone else 0)
+        flags = (ORBITS if orbits else ORBITS_OFF) | (FULL_CONE if full_cone else 0) | (SHELL_PLAIN if shell_plain else 0)
         h = C.c_void_p()
         _check(lib().qaoa_plan_graphs(len(graphs), _ptr(nv, C.c_int32), _ptr(offs, C.c_int64),
                                       _ptr(edges, C.c_int32) if edges.size else None, p, flags,
@@ -202,6 +205,14 @@ class Plan:
         _check(lib().qaoa_plan_cone(self._h, rep, _ptr(verts, C.c_int32), _ptr(dist, C.c_int32),
                                     _ptr(ce, C.c_int32)))
         return verts, dist, ce[:ne]
+
+    def shell(self, rep):
+        """(class index per cone qubit, -1 for inner; number of shell blocks)."""
+        nq = int(self.reps()["n_qubits"][rep])
+        cls = np.zeros(nq, dtype=np.int32)
+        nb = C.c_int64()
+        _check(lib().qaoa_plan_shell(self._h, rep, _ptr(cls, C.c_int32), C.byref(nb)))
+        return cls, nb.value
 
     def upload(self):
         _check(lib().qaoa_plan_upload(self._h))

@@ -507,3 +507,32 @@ def test_mixed_48_graph_batch_p1_256_points(q):
             db = (_cf_energy(n, edges, gg, bb + h, adj) - _cf_energy(n, edges, gg, bb - h, adj)) / (2 * h)
             _check_grad(g[k, j], [dg, db])
     assert plan.device_status() == 0
+
+
+@pytest.mark.parametrize("graph,p", [(I.random_regular(200, 3, 4), 2), (I.hypercube(8), 1), (I.torus(10, 10), 2),
+                                     (I.petersen(), 2), (I.erdos_renyi(150, 4 / 149, 3), 1),
+                                     (I.circulant(30, [1, 2]), 3), (I.star(7), 2)])
+def test_shell_classes_match_every_shell_assignment(q, graph, p):
+    """One block per shell-class count vector against one block per shell
+    assignment: energies and terms against each other, gradients of both
+    against the FP64 oracle adjoint (the reference the tolerance is defined
+    against)."""
+    n, edges = graph
+    P = 2
+    theta = I.draw_params(p, P, 17)
+    a = q.Plan((n, edges), p)
+    b = q.Plan((n, edges), p, shell_plain=True)
+    e1, t1 = a.energy(_params(theta), terms=True)
+    e2, t2 = b.energy(_params(theta), terms=True)
+    assert np.allclose(e1.cpu().numpy(), e2.cpu().numpy(), rtol=E_REL_TOL, atol=0)
+    assert np.max(np.abs(t1.cpu().numpy() - t2.cpu().numpy())) <= 2 * TERM_TOL
+    _, g1 = a.energy_grad(_params(theta))
+    _, g2 = b.energy_grad(_params(theta))
+    oid = a.orbits(0)[0]
+    adj = O.adjacency(n, edges)
+    for j in range(P):
+        eref, gref = O.orbit_grad_adjoint(n, edges, theta[j], p, oid, adj)
+        assert abs(e1[0, j].item() - eref) <= E_REL_TOL * abs(eref)
+        _check_grad(g1[0, j].cpu().numpy(), gref)
+        _check_grad(g2[0, j].cpu().numpy(), gref)
+    assert a.device_status() == 0 and b.device_status() == 0

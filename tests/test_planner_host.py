@@ -267,3 +267,41 @@ def test_bad_call_arguments(qlib):
     assert qlib.lib().qaoa_plan_graph(3, 1, qlib._ptr(e, C.c_int32), 1, 1, 0, 0, None) == qlib.QAOA_E_INVALID
     assert qlib.lib().qaoa_plan_info(None, None) == qlib.QAOA_E_INVALID
     assert qlib.lib().qaoa_energy(None, 1, None, None, None, None) == qlib.QAOA_E_INVALID
+
+
+# ------------------------------------------------------------ shell classes
+
+@pytest.mark.parametrize("graph,p", [
+    (I.random_regular(2000, 3, 1), 2), (I.hypercube(12), 1), (I.torus(8, 8), 2), (I.petersen(), 2),
+    (I.erdos_renyi(300, 4 / 299, 9), 1), (I.circulant(5000, [1, 7, 23]), 1), (I.complete(6), 1),
+])
+def test_shell_classes_partition_the_shell(qlib, graph, p):
+    n, edges = graph
+    plan = qlib.Plan((n, edges), p, orbits=False)
+    plain = qlib.Plan((n, edges), p, orbits=False, shell_plain=True)
+    reps = plan.reps()
+    for r in range(0, len(edges), max(1, len(edges) // 20)):
+        verts, dist, ce = plan.cone(r)
+        cls, nb = plan.shell(r)
+        n_in = reps["n_inner"][r]
+        assert np.all(cls[:n_in] == -1) and np.all(cls[n_in:] >= 0)
+        assert np.all(np.asarray(dist)[n_in:] == p)
+        inner_nb = {q: frozenset(a for a, b in ce.tolist() for a, b in [(a, b), (b, a)] if b == q and a < n_in)
+                    for q in range(n_in, len(verts))}
+        # same class <=> same inner neighbours
+        for q1 in range(n_in, len(verts)):
+            for q2 in range(n_in, len(verts)):
+                assert (cls[q1] == cls[q2]) == (inner_nb[q1] == inner_nb[q2])
+        sizes = np.bincount(cls[n_in:]) if len(verts) > n_in else np.zeros(0, int)
+        assert nb == int(np.prod(sizes + 1))
+        pc, pnb = plain.shell(r)
+        assert pnb == 2 ** (len(verts) - n_in) and len(set(pc[n_in:].tolist())) == len(verts) - n_in
+
+
+def test_shell_blocks_of_known_cones(qlib):
+    # random cubic graph at p = 2: tree-like cones have 4 classes of 2 -> 3^4 blocks
+    n, edges = I.random_regular(2000, 3, 1)
+    nbs = [qlib.Plan((n, edges), 2, orbits=False).shell(r)[1] for r in range(50)]
+    assert max(set(nbs), key=nbs.count) == 81
+    # hypercube Q_12 at p = 1: neighbours of u only and of v only -> 12 x 12 blocks
+    assert qlib.Plan(I.hypercube(12), 1).shell(0)[1] == 144
