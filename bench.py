@@ -63,7 +63,8 @@ def algorithmic_flops(reps, p, grad):
     """FP32 FLOPs of the pruned state-vector circuit per point, summed over reps.
 
     Counted for the cheapest formulation the kernels use (FMA = 2 FLOPs), per
-    cone with A = 2^n amplitudes and k_l qubits mixed in layer l:
+    cone with A = n_blocks * 2^n_inner evolved amplitudes (one inner block per
+    shell-class count vector) and k_l qubits mixed in layer l:
       forward = A (6 (p-1) + 4 sum_l k_l + 4): the phase complex multiply (6)
         from layer 2 on (layer 1 is a table read), exp(-i beta X) as
         kappa (I - i tau X) with kappa kept as a scalar (one FMA per real
@@ -75,7 +76,7 @@ def algorithmic_flops(reps, p, grad):
         per layer the Im<lam|C|psi> term (5); undoing the phase on both states
         above layer 1 (12).
     """
-    A = np.ldexp(1.0, reps["n_qubits"].astype(np.int64))
+    A = reps["n_blocks"].astype(np.float64) * np.ldexp(1.0, reps["n_inner"].astype(np.int64))
     k = reps["mix_qubits"][:, :p].astype(np.float64)
     ksum = k.sum(axis=1)
     flops = A * (6 * (p - 1) + 4 * ksum + 4)
@@ -308,6 +309,7 @@ def run_ours(args, rank, world, local_rank):
     plan.upload()
     info = plan.info()
     reps = plan.reps()
+    reps["n_blocks"] = plan.shell_blocks()
     params = torch.tensor(theta, device=device)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=device)
     stream = torch.cuda.current_stream()
@@ -391,6 +393,7 @@ def run_ours(args, rank, world, local_rank):
     peak, mhz = fp32_peak_tflops()
     traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["kernels_sha1"] == kernels_sha1() else None
     amp_updates = float((np.ldexp(1.0, reps["n_qubits"].astype(np.int64)) * p).sum()) * P
+    evolved = float((reps["n_blocks"] * np.ldexp(1.0, reps["n_inner"].astype(np.int64)) * p).sum()) * P
 
     hbm = hbm_path_measurement(device, flush, stream) if not args.no_aux else None
     status = plan.device_status()
@@ -436,6 +439,7 @@ def run_ours(args, rank, world, local_rank):
         "energy_only_evals_per_s": world * evals / (energy_ms / 1e3),
         "plain_all_edge_evals_per_s": world * evals / (plain_ms / 1e3),
         "amp_updates_per_s": world * amp_updates / (ms_per_step / 1e3),
+        "evolved_amp_updates_per_s": world * evolved / (ms_per_step / 1e3),
         "plan_s": t_plan,
         "t_orbits_s": info["t_orbits_s"],
         "wall_s_timed_region": wall,

@@ -214,6 +214,16 @@ class Plan:
         _check(lib().qaoa_plan_shell(self._h, rep, _ptr(cls, C.c_int32), C.byref(nb)))
         return cls, nb.value
 
+    def shell_blocks(self):
+        """Number of shell blocks of every representative (plan order)."""
+        r = self.info()["n_reps"]
+        out = np.zeros(r, dtype=np.int64)
+        nb = C.c_int64()
+        for i in range(r):
+            _check(lib().qaoa_plan_shell(self._h, i, None, C.byref(nb)))
+            out[i] = nb.value
+        return out
+
     def upload(self):
         _check(lib().qaoa_plan_upload(self._h))
 

@@ -46,11 +46,12 @@ def test_two_gloo_ranks_reduce_max_and_scale_value():
 
 def test_flop_model_counts():
     import bench
-    reps = {"n_qubits": np.array([14, 3]), "mix_qubits": np.array([[6, 2], [2, 2]])}
+    reps = {"n_inner": np.array([6, 2]), "n_blocks": np.array([81, 3]), "mix_qubits": np.array([[6, 2], [2, 2]])}
     fwd = bench.algorithmic_flops(reps, 2, grad=False)
-    assert fwd == 2 ** 14 * (6 + 4 * 8 + 4) + 2 ** 3 * (6 + 4 * 4 + 4)
+    a0, a1 = 81 * 2 ** 6, 3 * 2 ** 2
+    assert fwd == a0 * (6 + 4 * 8 + 4) + a1 * (6 + 4 * 4 + 4)
     both = bench.algorithmic_flops(reps, 2, grad=True)
-    assert both == fwd + 2 ** 14 * (2 + 12 * 2 + 8 * 6 + 10 + 12) + 2 ** 3 * (2 + 12 * 2 + 8 * 2 + 10 + 12)
+    assert both == fwd + a0 * (2 + 12 * 2 + 8 * 6 + 10 + 12) + a1 * (2 + 12 * 2 + 8 * 2 + 10 + 12)
 
 
 def test_clock_log_parser(tmp_path):
