@@ -496,6 +496,126 @@ def run_reference(args, rank, world):
 G_P_EVALS = len(SEEDS) * N_POINTS
 
 
+# ------------------------------------------------------------------ suite
+
+def suite_configs():
+    """The five benchmark configurations (readings of their sizes as in the design doc)."""
+    from paper_2101_10296_gb300 import inputs as I
+    return [
+        ("1. C_20(1,4) p=1, 1 point", [I.circulant(20, [1, 4])], 1, 1),
+        ("2. rr3 n=2000 x4, p=2, 64 points", [I.random_regular(2000, 3, s) for s in SEEDS], 2, 64),
+        ("3a. torus 100x100 + C_5000(1,7), p=2, 32 points", [I.torus(100, 100), I.circulant(5000, [1, 7])], 2, 32),
+        ("3b. Q_12 + C_5000(1,7,23), p=1, 32 points", [I.hypercube(12), I.circulant(5000, [1, 7, 23])], 1, 32),
+        ("4a. rr3 n=24 x4, p=3, 128 points", [I.random_regular(24, 3, s) for s in SEEDS], 3, 128),
+        ("4b. torus 8x8, p=2, 128 points", [I.torus(8, 8)], 2, 128),
+        ("4c. torus 6x6, p=3, 128 points", [I.torus(6, 6)], 3, 128),
+        ("5. 48-graph mix, p=1, 256 points", [b() for _, b in I.mixed_benchmark_graphs()], 1, 256),
+    ]
+
+
+def _suite_term_job(job):
+    from oracle import qaoa_oracle as O
+    n, edges, e, theta, p = job
+    import time as _t
+    t0 = _t.perf_counter()
+    val = O.lightcone_term(n, edges, e, theta, p)
+    return val, _t.perf_counter() - t0
+
+
+def run_suite(args):
+    """Measures every configuration; prints one JSON object per configuration."""
+    import multiprocessing as mp
+    import torch
+    from oracle import qaoa_oracle as O
+    from paper_2101_10296_gb300 import inputs as I
+    from paper_2101_10296_gb300 import qaoa
+    cores = os.cpu_count() or 1
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+    pool = mp.get_context("spawn").Pool(cores)
+    device = torch.device("cuda", 0)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=device)
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        out = []
+        for k in range(reps):
+            flush.fill_(k & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            out.append(a.elapsed_time(b))
+        return sum(out) / len(out)
+
+    rows = []
+    for name, graphs, p, P in suite_configs():
+        theta = np.stack([I.draw_params(p, P, 1000 + k) for k in range(len(graphs))])
+        params = torch.tensor(theta, device=device)
+        evals = len(graphs) * P
+        t0 = time.perf_counter()
+        plan = qaoa.Plan(graphs, p)
+        t_plan = time.perf_counter() - t0
+        plan.upload()
+        info = plan.info()
+        plain = qaoa.Plan(graphs, p, orbits=False)
+        plain.upload()
+        ms_g = timed(lambda: plan.energy_grad(params))
+        ms_e = timed(lambda: plan.energy(params))
+        ms_pg = timed(lambda: plain.energy_grad(params))
+        e_gpu, terms = plan.energy(params, terms=True)
+        e_gpu = e_gpu.cpu().numpy()
+        terms = terms.cpu().numpy()
+        reps = plan.reps()
+        reps["n_blocks"] = plan.shell_blocks()
+        flops = algorithmic_flops(reps, p, grad=True) * P
+        amps = float((np.ldexp(1.0, reps["n_qubits"].astype(np.int64)) * p).sum()) * P
+        # accuracy: per-term against the FP64 oracle on sampled representatives
+        # (cones of at most 20 qubits), total energy against the closed form at p = 1
+        rng = np.random.default_rng(0)
+        small = np.nonzero(reps["n_qubits"] <= 20)[0]
+        pick = rng.choice(small, min(24, small.size), replace=False) if small.size else []
+        jobs = []
+        for r in pick:
+            gi = int(reps["graph"][r])
+            n, edges = graphs[gi]
+            jobs.append((n, edges, edges[reps["edge"][r]], theta[gi, 0], p))
+        res = pool.map(_suite_term_job, jobs) if jobs else []
+        dterm = max([abs(0.5 * (1 - terms[r, 0]) - 0.5 * (1 - v)) for r, (v, _) in zip(pick, res)] or [float("nan")])
+        t_term = float(np.mean([dt for _, dt in res])) if res else float("nan")
+        drel = float("nan")
+        if p == 1:
+            worst = 0.0
+            for gi in range(min(len(graphs), 8)):
+                n, edges = graphs[gi]
+                adj = O.adjacency(n, edges)
+                ref = sum(O.closed_form_p1_term(n, edges, e, theta[gi, 0, 0], theta[gi, 0, 1], adj) for e in edges)
+                worst = max(worst, abs(e_gpu[gi, 0] - ref) / abs(ref))
+            drel = worst
+        # oracle CPU rate: mean single-process time per cone term x terms per eval / processes
+        n_terms = int(info["n_reps"])
+        n_terms_plain = int(info["n_edges_total"])
+        cpu_eval_s = t_term * n_terms / len(graphs) / cores
+        row = {
+            "config": name, "graphs": len(graphs), "p": p, "points": P, "n_reps": n_terms,
+            "n_edges": n_terms_plain, "max_cone_qubits": int(info["max_qubits"]), "max_inner": int(info["max_inner"]),
+            "large_state_cones": int(info["n_big"]), "plan_s": t_plan, "t_orbits_s": info["t_orbits_s"],
+            "energy_grad_evals_per_s": evals / (ms_g / 1e3), "energy_evals_per_s": evals / (ms_e / 1e3),
+            "plain_energy_grad_evals_per_s": evals / (ms_pg / 1e3),
+            "amp_updates_per_s": amps / (ms_g / 1e3), "fp32_tflops_alg": flops / (ms_g / 1e3) / 1e12,
+            "max_term_err_vs_fp64": dterm, "max_rel_energy_err_vs_closed_form": drel,
+            "cpu_oracle_evals_per_s": (1.0 / cpu_eval_s) if cpu_eval_s == cpu_eval_s and cpu_eval_s > 0 else None,
+            "cpu_oracle_basis": f"{len(res)} sampled cone terms (<= 20 qubits) x {n_terms} terms per eval, {cores} processes",
+            "device_status": plan.device_status(),
+        }
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+    pool.close()
+    pool.join()
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -505,12 +625,16 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-aux", action="store_true", help="skip the auxiliary large-state measurement")
+    ap.add_argument("--suite", action="store_true", help="measure every benchmark configuration instead")
     args = ap.parse_args()
     if args.warmup < 3:
         log("warning: fewer than 3 warm-up steps")
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.suite:
+        run_suite(args)
+        return
     if args.impl == "reference":
         out = run_reference(args, rank, world)
     else:

@@ -153,8 +153,8 @@ __global__ void __launch_bounds__(128) big_pass_kernel(const __grid_constant__ B
                     float acc = 0.f;
 #pragma unroll
                     for (int i = 0; i < NR; ++i) acc = fmaf(x[i].x, x[i].x, fmaf(x[i].y, x[i].y, acc));
-                    const float tv = sg * acc * sig;
-                    add_gp(-0.5f * wgt * tv, L.energy, gj);
+                    const float tv = sg * acc * sig * mult;  // this block's share of <Z_0 Z_1>
+                    add_gp(-0.5f * float(C->weight) * tv, L.energy, gj);
                     if (L.terms) add_gp(tv, L.terms, C->rep * L.P + j);
                     break;
                 }

@@ -511,7 +511,7 @@ def test_mixed_48_graph_batch_p1_256_points(q):
 
 @pytest.mark.parametrize("graph,p", [(I.random_regular(200, 3, 4), 2), (I.hypercube(8), 1), (I.torus(10, 10), 2),
                                      (I.petersen(), 2), (I.erdos_renyi(150, 4 / 149, 3), 1),
-                                     (I.circulant(30, [1, 2]), 3), (I.star(7), 2)])
+                                     (I.circulant(30, [1, 2]), 3), (I.star(7), 2), (I.random_regular(24, 3, 1), 3)])
 def test_shell_classes_match_every_shell_assignment(q, graph, p):
     """One block per shell-class count vector against one block per shell
     assignment: energies and terms against each other, gradients of both
@@ -536,3 +536,27 @@ def test_shell_classes_match_every_shell_assignment(q, graph, p):
         _check_grad(g1[0, j].cpu().numpy(), gref)
         _check_grad(g2[0, j].cpu().numpy(), gref)
     assert a.device_status() == 0 and b.device_status() == 0
+
+
+def test_large_state_terms_with_shell_classes_match_oracle(q):
+    """Large-state cones whose shell classes have more than one member
+    (random cubic n=24 at p=3): per-term values against the FP64 oracle."""
+    n, edges = I.random_regular(24, 3, 1)
+    plan = q.Plan((n, edges), 3, orbits=False)
+    reps = plan.reps()
+    nb = plan.shell_blocks()
+    shell = reps["n_qubits"] - reps["n_inner"]
+    cand = [r for r in range(len(edges)) if reps["n_inner"][r] > 9 and nb[r] < 2 ** shell[r]
+            and reps["n_qubits"][r] <= 20]
+    assert cand, "no large-state cone with a merged shell class"
+    theta = I.draw_params(3, 2, 8)
+    _, t = plan.energy(_params(theta), terms=True)
+    t = t.cpu().numpy()
+    _, tg, tt = plan.energy_grad(_params(theta), terms=True)
+    tt = tt.cpu().numpy()
+    adj = O.adjacency(n, edges)
+    for r in cand[:3]:
+        for j in range(2):
+            ref = O.lightcone_term(n, edges, edges[reps["edge"][r]], theta[j], 3, adj)
+            assert abs(t[r, j] - ref) <= 2 * TERM_TOL
+            assert abs(tt[r, j] - ref) <= 2 * TERM_TOL
