@@ -319,27 +319,14 @@ cudaError_t launch_big_prep(const double *params, int64_t GP, int p, float2 *cs,
     return cudaGetLastError();
 }
 
+int occupancy_grid(const void *fn, int block, size_t smem);
+
 int big_grid(bool grad) {
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (grad)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, big_pass_kernel<true>, 128, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, big_pass_kernel<false>, 128, 0);
-    return sms * (per < 1 ? 1 : per);
+    return grad ? occupancy_grid((const void *)big_pass_kernel<true>, 128, 0)
+                : occupancy_grid((const void *)big_pass_kernel<false>, 128, 0);
 }
 
-static int mix_grid() {
-    static int grid = [] {
-        int dev = 0, sms = 0, per = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, big_mix_kernel, 128, 0);
-        return sms * (per < 1 ? 1 : per);
-    }();
-    return grid;
-}
+static int mix_grid() { return occupancy_grid((const void *)big_mix_kernel, 128, 0); }
 
 static bool mix_only(const BigPass &ps) {
     if (!ps.load_psi || !ps.store_psi || ps.load_lam || ps.store_lam) return false;

@@ -110,10 +110,7 @@ int ensure_uploaded(const qaoa_plan *plan) {
 // (never above the occupancy limit).
 int64_t tuned_grid(const qaoa_device_plan *d, int occupancy_grid) {
     if (d->blocks_per_sm <= 0) return occupancy_grid;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return std::min<int64_t>(occupancy_grid, int64_t(sms) * d->blocks_per_sm);
+    return std::min<int64_t>(occupancy_grid, int64_t(sm_count()) * d->blocks_per_sm);
 }
 
 // Large-state cones: per shape, waves of blocks that fit the scratch budget,

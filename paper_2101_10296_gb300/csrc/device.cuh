@@ -120,6 +120,7 @@ cudaError_t launch_reg_grad(const RegLaunch &a, bool wide, int grid, cudaStream_
 cudaError_t launch_cut_table(const DevCone *cone, uint8_t *out, int32_t n, int32_t *status, cudaStream_t s);
 // occupancy-sized persistent grids for a given dynamic shared memory size
 int reg_energy_grid(bool wide, size_t smem);
+int sm_count();  // multiprocessors of the current device (cached)
 int reg_grad_grid(bool wide, size_t smem, int p);
 constexpr int kRegBlock = 128;
 

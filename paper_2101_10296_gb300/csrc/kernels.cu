@@ -30,6 +30,10 @@
 // exp(-i gamma c), tan and the kappa powers are computed in FP64 and rounded
 // once; lane partial sums are reduced across the warp in FP32 and
 // accumulated across warps, cones and orbits in FP64 (atomicAdd).
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "cone_kernel.cuh"
 
 namespace qaoa {
@@ -92,13 +96,49 @@ __global__ void cut_table_kernel(const DevCone *__restrict__ C, uint8_t *__restr
 
 }  // namespace
 
+// Persistent grid size for (kernel, block, dynamic shared memory) on the
+// current device, computed once and cached (the runtime query is not free
+// and small evaluations are dominated by host overhead).
 int occupancy_grid(const void *fn, int block, size_t smem) {
-    int dev = 0, sms = 0, per = 0;
+    struct Key {
+        const void *fn;
+        int block, dev;
+        size_t smem;
+        bool operator<(const Key &o) const {
+            return std::tie(fn, block, dev, smem) < std::tie(o.fn, o.block, o.dev, o.smem);
+        }
+    };
+    static std::mutex mu;
+    static std::map<Key, int> cache;
+    int dev = 0;
     cudaGetDevice(&dev);
+    const Key key{fn, block, dev, smem};
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) return it->second;
+    }
+    int sms = 0, per = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, block, smem);
     if (per < 1) per = 1;
+    std::lock_guard<std::mutex> lk(mu);
+    cache[key] = sms * per;
     return sms * per;
+}
+
+int sm_count() {
+    static std::mutex mu;
+    static std::map<int, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(dev);
+    if (it != cache.end()) return it->second;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cache[dev] = sms;
+    return sms;
 }
 
 cudaError_t launch_prep(const PrepArgs &a, cudaStream_t s) {
