@@ -315,6 +315,21 @@ void qaoa_graph_free(qaoa_graph *graph);
 int qaoa_plan_timing(qaoa_plan *plan, int32_t enable);
 int qaoa_kernel_time(qaoa_plan *plan, double *ms, int64_t *launches, int64_t *all_launches);
 
+/*
+ * Failure injection for testing error handling; nothing here faults the GPU.
+ * The next `count` events of `kind` are made to fail on the host:
+ *   QAOA_FAULT_GENERATOR  a candidate automorphism of the orbit search gets
+ *                         two images exchanged before verification (which
+ *                         must then reject it; the orbits stay those of a
+ *                         verified subgroup)
+ *   QAOA_FAULT_DEVICE_ALLOC  a device allocation of an energy call reports
+ *                         out-of-memory (the call returns QAOA_E_OOM before
+ *                         launching anything)
+ * kind QAOA_FAULT_NONE clears every pending injection.  Process-wide.
+ */
+enum qaoa_fault { QAOA_FAULT_NONE = 0, QAOA_FAULT_GENERATOR = 1, QAOA_FAULT_DEVICE_ALLOC = 2 };
+int qaoa_inject_fault(int32_t kind, int32_t count);
+
 /* Last error message of the calling thread ("" if none). */
 const char *qaoa_last_error(void);
 

@@ -182,6 +182,10 @@ int run(const qaoa_plan *plan, int64_t n_points, const double *params, double *e
     const int32_t G = plan->n_graphs, p = plan->p;
     float2 *lut = nullptr, *mix = nullptr;
     float *kpow = nullptr;
+    if (take_fault(QAOA_FAULT_DEVICE_ALLOC)) {
+        set_error("cudaMallocAsync: out of memory (injected by qaoa_inject_fault)");
+        return QAOA_E_OOM;
+    }
     const size_t nlut = size_t(G) * n_points * p * d->cmax1;
     const size_t nmix = size_t(G) * n_points * p;
     cudaError_t e;

@@ -63,6 +63,10 @@ int extract_cone(const Graph &g, int64_t e, int32_t p, bool full_cone, bool shel
 
 void set_error(const std::string &msg);
 
+// Injected failures (qaoa_inject_fault): true if one of `kind` is pending,
+// consuming it.
+bool take_fault(int kind);
+
 }  // namespace qaoa
 
 struct qaoa_device_plan;  // defined in the CUDA translation unit

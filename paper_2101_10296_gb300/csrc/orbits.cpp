@@ -316,6 +316,23 @@ class AutSearch {
             for (int32_t x = 0; x < g_.n; ++x) perm[x] = x;
             for (int32_t q = 0; q < g_.n; ++q)
                 if (!iso_[leaf_[q]]) perm[leaf_[q]] = P.lab[q];
+            if (take_fault(QAOA_FAULT_GENERATOR)) {
+                // injected corruption: exchange the images of an edge's endpoints'
+                // first non-neighbour pair so that the candidate is not an automorphism
+                for (int64_t e = 0; e < g_.m; ++e) {
+                    const int32_t a = g_.eu[e];
+                    int32_t b = -1;
+                    for (int32_t y = 0; y < g_.n; ++y)
+                        if (y != a && find_edge(g_, a, y) < 0 && g_.degree(y) > 0) {
+                            b = y;
+                            break;
+                        }
+                    if (b >= 0) {
+                        std::swap(perm[a], perm[b]);
+                        break;
+                    }
+                }
+            }
             return verify(perm);
         }
         if (j + 1 >= depth_ || t != tgt_[j + 1] || P.len[t] != ref.len[t]) return false;

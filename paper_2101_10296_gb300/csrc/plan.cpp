@@ -16,6 +16,16 @@ static thread_local std::string g_last_error;
 
 void set_error(const std::string &msg) { g_last_error = msg; }
 
+static std::atomic<int32_t> g_faults[3];
+
+bool take_fault(int kind) {
+    if (kind < 1 || kind > 2) return false;
+    int32_t v = g_faults[kind].load();
+    while (v > 0)
+        if (g_faults[kind].compare_exchange_weak(v, v - 1)) return true;
+    return false;
+}
+
 // Reverse causal cone of edge e (Sec. 2.3): the operator Z_u Z_v conjugated
 // by the last layer's mixer stays on {u, v}; each phase layer adds the
 // qubits of every term meeting the current support, so after p layers the
@@ -400,5 +410,18 @@ extern "C" int qaoa_plan_shell(const qaoa_plan *plan, int64_t rep, int32_t *clas
             for (int32_t q : c.shell_classes[k]) class_of[q] = int32_t(k);
     }
     if (n_blocks) *n_blocks = c.n_blocks;
+    return QAOA_OK;
+}
+
+extern "C" int qaoa_inject_fault(int32_t kind, int32_t count) {
+    if (kind == QAOA_FAULT_NONE) {
+        for (auto &f : g_faults) f.store(0);
+        return QAOA_OK;
+    }
+    if (kind < 1 || kind > 2 || count < 0) {
+        set_error("unknown fault kind or negative count");
+        return QAOA_E_INVALID;
+    }
+    g_faults[kind].store(count);
     return QAOA_OK;
 }

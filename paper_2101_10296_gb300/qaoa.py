@@ -79,6 +79,7 @@ _SIGS = {
     "qaoa_graph_launch": (C.c_int, [_P, _P]),
     "qaoa_graph_free": (None, [_P]),
     "qaoa_kernel_time": (C.c_int, [_P, _F64P, _I64P, _I64P]),
+    "qaoa_inject_fault": (C.c_int, [C.c_int32, C.c_int32]),
     "qaoa_last_error": (C.c_char_p, []),
     "qaoa_version": (C.c_char_p, []),
 }
@@ -123,6 +124,14 @@ def edge_orbits(n, edges, budget=0):
     _check(lib().qaoa_edge_orbits(n, m, _ptr(e, C.c_int32), budget, _ptr(oid, C.c_int32), C.byref(norb),
                                   C.byref(ngen), C.byref(l10), C.byref(comp)))
     return oid, norb.value, ngen.value, l10.value, bool(comp.value)
+
+
+FAULT_NONE, FAULT_GENERATOR, FAULT_DEVICE_ALLOC = 0, 1, 2
+
+
+def inject_fault(kind, count=1):
+    """Make the next ``count`` events of ``kind`` fail on the host (testing only)."""
+    _check(lib().qaoa_inject_fault(kind, count))
 
 
 def _stream_handle(stream=None):

@@ -560,3 +560,19 @@ def test_large_state_terms_with_shell_classes_match_oracle(q):
             ref = O.lightcone_term(n, edges, edges[reps["edge"][r]], theta[j], 3, adj)
             assert abs(t[r, j] - ref) <= 2 * TERM_TOL
             assert abs(tt[r, j] - ref) <= 2 * TERM_TOL
+
+
+def test_injected_allocation_failure_is_reported_and_recoverable(q):
+    n, edges = I.petersen()
+    plan = q.Plan((n, edges), 2)
+    theta = _params(I.draw_params(2, 3, 0))
+    e0 = plan.energy(theta).cpu().numpy()
+    try:
+        q.inject_fault(q.FAULT_DEVICE_ALLOC, 1)
+        with pytest.raises(q.QAOAError) as ei:
+            plan.energy_grad(theta)
+        assert ei.value.code == q.QAOA_E_OOM
+    finally:
+        q.inject_fault(q.FAULT_NONE, 0)
+    e1, _ = plan.energy_grad(theta)
+    assert np.allclose(e1.cpu().numpy(), e0, rtol=E_REL_TOL, atol=0) and plan.device_status() == 0

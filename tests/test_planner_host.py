@@ -305,3 +305,35 @@ def test_shell_blocks_of_known_cones(qlib):
     assert max(set(nbs), key=nbs.count) == 81
     # hypercube Q_12 at p = 1: neighbours of u only and of v only -> 12 x 12 blocks
     assert qlib.Plan(I.hypercube(12), 1).shell(0)[1] == 144
+
+
+# ------------------------------------------------------- failure injection
+
+def test_corrupted_generators_are_rejected(qlib):
+    n, edges = I.petersen()
+    try:
+        qlib.inject_fault(qlib.FAULT_GENERATOR, 10 ** 6)  # corrupt every candidate
+        oid, norb, ngen, l10, comp = qlib.edge_orbits(n, edges)
+    finally:
+        qlib.inject_fault(qlib.FAULT_NONE, 0)
+    # no corrupted candidate passes verification: the group found is trivial
+    assert ngen == 0 and norb == len(edges) and np.array_equal(oid, np.arange(len(edges)))
+    oid2, norb2, ngen2, *_ = qlib.edge_orbits(n, edges)
+    assert norb2 == 1 and ngen2 > 0
+
+
+def test_some_corrupted_generators_leave_a_valid_subgroup(qlib):
+    n, edges = I.rook(5)
+    true_oid, *_ = qlib.edge_orbits(n, edges)
+    try:
+        qlib.inject_fault(qlib.FAULT_GENERATOR, 2)
+        oid, norb, ngen, _, comp = qlib.edge_orbits(n, edges)
+    finally:
+        qlib.inject_fault(qlib.FAULT_NONE, 0)
+    for r in np.unique(oid):
+        assert len(np.unique(true_oid[oid == r])) == 1
+
+
+def test_inject_fault_rejects_unknown_kinds(qlib):
+    with pytest.raises(qlib.QAOAError):
+        qlib.inject_fault(7, 1)
