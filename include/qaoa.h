@@ -56,9 +56,12 @@ enum qaoa_flags {
     QAOA_FULL_CONE = 2u,  /* simulate the whole 2^n cone state with the mixer on
                              every cone qubit in every layer (no pruning of the
                              gates that cancel); slower, used for cross-checks */
-    QAOA_SHELL_PLAIN = 4u /* evolve every assignment of the never-mixed shell
-                             qubits as its own block instead of one block per
-                             shell class count vector; slower, for cross-checks */
+    QAOA_SHELL_PLAIN = 4u, /* evolve every assignment of the never-mixed shell
+                              qubits as its own block instead of one block per
+                              shell class count vector; slower, for cross-checks */
+    QAOA_BIG_GENERAL = 8u  /* large-state cones always use the general pass
+                              schedule (psi and lambda both stored), never the
+                              core-tile schedule; slower, for cross-checks */
 };
 
 /* Largest cone handled: qubits per cone and local edges per cone. */

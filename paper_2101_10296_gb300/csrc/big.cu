@@ -12,30 +12,12 @@
 // exp(+i beta X) and exp(+i gamma C), which keep <lambda|X_q|psi> invariant
 // under the un-mixing of any qubit of the same layer.
 #include "big.cuh"
+#include "big_common.cuh"
 
 namespace qaoa {
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
 constexpr int NR = 1 << kBigRegBits;
-
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
-    return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
-}
-__device__ __forceinline__ float imconj(float2 a, float2 b) { return a.x * b.y - a.y * b.x; }
-// c me - i s other
-__device__ __forceinline__ float2 rot(float2 me, float2 o, float c, float s) {
-    return make_float2(fmaf(c, me.x, s * o.y), fmaf(c, me.y, -s * o.x));
-}
-
-__device__ __forceinline__ void add_gp(float v, double *base, int64_t idx) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(base + idx, double(v));
-}
 
 template <bool GRAD>
 __global__ void __launch_bounds__(128) big_pass_kernel(const __grid_constant__ BigLaunch L) {
@@ -52,14 +34,11 @@ __global__ void __launch_bounds__(128) big_pass_kernel(const __grid_constant__ B
     for (int64_t task = gw; task < ntask; task += nw) {
         const int64_t it = task / tiles;
         const int64_t tile = task - it * tiles;
-        const int64_t item = L.item0 + it;
-        const int64_t per_cone = L.P * L.Y;
-        const int ci = int(item / per_cone);
-        const int64_t rem = item - int64_t(ci) * per_cone;
-        const int64_t j = rem / L.Y;
-        const int64_t y = rem - j * L.Y;
+        int ci;
+        int64_t j, y;
+        decode_item(L, L.item0 + it, ci, j, y);
         const DevCone *__restrict__ C = L.cones + L.cone_ids[ci];
-        if (C->n != L.n || C->n_in != nin) {
+        if (C->n_in != nin) {
             if (lane == 0) atomicOr(L.status, 1);
             continue;
         }
@@ -102,7 +81,7 @@ __global__ void __launch_bounds__(128) big_pass_kernel(const __grid_constant__ B
             for (int i = 0; i < NR; ++i) r[i] = lp[int64_t(i) << b];
         }
         const float wgt = float(C->weight) * mult;  // orbit size x shell multiplicity
-        const float sig = __int_as_float((127 - L.n) << 23);  // 2^-n
+        const float sig = __int_as_float((127 - C->n) << 23);  // 2^-n
         for (int o = 0; o < ps.nops; ++o) {
             const BigOp op = ps.ops[o];
             const int l = op.layer;
@@ -254,10 +233,9 @@ __global__ void __launch_bounds__(128, 4) big_mix_kernel(const __grid_constant__
     for (int64_t task = gw; task < ntask; task += nw) {
         const int64_t it = task / tiles;
         const int64_t tile = task - it * tiles;
-        const int64_t item = L.item0 + it;
-        const int64_t per_cone = L.P * L.Y;
-        const int ci = int(item / per_cone);
-        const int64_t j = (item - int64_t(ci) * per_cone) / L.Y;
+        int ci;
+        int64_t j, y;
+        decode_item(L, L.item0 + it, ci, j, y);
         const DevCone *__restrict__ C = L.cones + L.cone_ids[ci];
         const float2 *__restrict__ cs = L.cs + (int64_t(C->graph) * L.P + j) * L.p;
         const int64_t lowmask = (int64_t(1) << (b - 5)) - 1;

@@ -1,0 +1,440 @@
+// Large-state cones, core-tile schedule.
+//
+// In a pruned cone, layer l mixes the qubits within distance p - l of the
+// edge (Sec. 2.3), so the outer inner qubits -- those at distance p - 1 --
+// are mixed by the first layer only.  When every later layer mixes only the
+// T = RB + 5 core qubits [0, T) of a warp tile, the state after the first
+// layer's mixer decouples into 2^(n_in - T) independent core tiles:
+//
+//   forward   outer passes build V_U exp(-i gamma_1 C)|+> (V_U: the first
+//             mixer on the outer qubits), five outer qubits per pass; the
+//             core pass loads one tile, applies the first mixer to the core
+//             qubits, runs layers 2..p in registers and reduces <Z_0 Z_1>.
+//   adjoint   the core pass continues with lambda = -1/2 Z_0 Z_1 psi, runs
+//             both states back through layers p..2 (the derivative terms of
+//             those layers), takes the first mixer's terms of the core
+//             qubits, un-mixes lambda alone on the core qubits and stores it
+//             in place of psi.  Outer passes un-mix lambda on the outer
+//             qubits; the last one evaluates the first layer's phase term
+//             and the outer qubits' mixer terms against the state before the
+//             first mixer, exp(-i gamma_1 C)|+>, which is known in closed
+//             form (amplitude = phase-table entry of C(z)).
+//
+// Both derivative identities rest on the first mixer commuting with every
+// X_q it contains: <lambda|X_q|psi> is the same before and after it.  Only
+// one state block per item is ever stored (the general schedule stores psi
+// and lambda), and psi is never written back after the core pass.
+//
+// Storage: address bits 0..4 = qubits RB..RB+4, bits 5..RB+4 = qubits
+// 0..RB-1, higher bits = the outer qubits themselves.  A core tile is one
+// warp: lane = qubits RB..RB+4, register i = qubits 0..RB-1, so the most
+// often mixed qubits 0, 1 are register butterflies and <Z_0 Z_1>'s sign is a
+// compile-time function of the register.  Every load and store moves 256
+// contiguous bytes per warp instruction.
+#include "big.cuh"
+#include "big_common.cuh"
+
+namespace qaoa {
+namespace {
+
+// exp(-i beta X) on register qubits [0, nbits) (nbits <= log2 NR).
+template <int NR>
+__device__ __forceinline__ void mix_regs(float2 (&x)[NR], int nbits, float c, float s) {
+#pragma unroll
+    for (int rb = 0; (1 << rb) < NR; ++rb) {
+        if (rb < nbits) {
+#pragma unroll
+            for (int i = 0; i < NR; ++i) {
+                if (i & (1 << rb)) continue;
+                const int i2 = i | (1 << rb);
+                const float2 a = x[i], bb = x[i2];
+                x[i] = rot(a, bb, c, s);
+                x[i2] = rot(bb, a, c, s);
+            }
+        }
+    }
+}
+
+// exp(-i beta X) on register bits [r0, r1) of a 32-register window.
+__device__ __forceinline__ void mix_window(float2 (&x)[32], int r0, int r1, float c, float s) {
+#pragma unroll
+    for (int rb = 0; rb < 5; ++rb) {
+        if (rb >= r0 && rb < r1) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                if (i & (1 << rb)) continue;
+                const int i2 = i | (1 << rb);
+                const float2 a = x[i], bb = x[i2];
+                x[i] = rot(a, bb, c, s);
+                x[i2] = rot(bb, a, c, s);
+            }
+        }
+    }
+}
+
+// exp(-i beta X) on lane bits [0, nb).
+template <int NR>
+__device__ __forceinline__ void mix_lanes(float2 (&x)[NR], int nb, float c, float s) {
+    for (int lb = 0; lb < nb; ++lb) {
+        const int m = 1 << lb;
+#pragma unroll
+        for (int i = 0; i < NR; ++i) {
+            float2 o;
+            o.x = __shfl_xor_sync(kFull, x[i].x, m);
+            o.y = __shfl_xor_sync(kFull, x[i].y, m);
+            x[i] = rot(x[i], o, c, s);
+        }
+    }
+}
+
+// Adjoint step of a mixer on register qubits [0, nbits): adds
+// Im<r|X_q|x> for each, then applies exp(+i beta X) to both states.
+template <int NR>
+__device__ __forceinline__ void unmix_regs_d(float2 (&x)[NR], float2 (&r)[NR], int nbits, float c, float s,
+                                             float &d) {
+#pragma unroll
+    for (int rb = 0; (1 << rb) < NR; ++rb) {
+        if (rb < nbits) {
+#pragma unroll
+            for (int i = 0; i < NR; ++i) {
+                if (i & (1 << rb)) continue;
+                const int i2 = i | (1 << rb);
+                const float2 a = x[i], bb = x[i2], ra = r[i], rbv = r[i2];
+                d += imconj(ra, bb) + imconj(rbv, a);
+                x[i] = rot(a, bb, c, -s);
+                x[i2] = rot(bb, a, c, -s);
+                r[i] = rot(ra, rbv, c, -s);
+                r[i2] = rot(rbv, ra, c, -s);
+            }
+        }
+    }
+}
+
+template <int NR>
+__device__ __forceinline__ void unmix_lanes_d(float2 (&x)[NR], float2 (&r)[NR], int nb, float c, float s, float &d) {
+    for (int lb = 0; lb < nb; ++lb) {
+        const int m = 1 << lb;
+#pragma unroll
+        for (int i = 0; i < NR; ++i) {
+            float2 xo, ro;
+            xo.x = __shfl_xor_sync(kFull, x[i].x, m);
+            xo.y = __shfl_xor_sync(kFull, x[i].y, m);
+            ro.x = __shfl_xor_sync(kFull, r[i].x, m);
+            ro.y = __shfl_xor_sync(kFull, r[i].y, m);
+            d += imconj(r[i], xo);
+            x[i] = rot(x[i], xo, c, -s);
+            r[i] = rot(r[i], ro, c, -s);
+        }
+    }
+}
+
+// Sum of Im<r|X_q|x> over every register and lane qubit, states unchanged.
+template <int NR>
+__device__ __forceinline__ float xterms_all(const float2 (&x)[NR], const float2 (&r)[NR]) {
+    float d = 0.f;
+#pragma unroll
+    for (int rb = 0; (1 << rb) < NR; ++rb) {
+#pragma unroll
+        for (int i = 0; i < NR; ++i) {
+            if (i & (1 << rb)) continue;
+            const int i2 = i | (1 << rb);
+            d += imconj(r[i], x[i2]) + imconj(r[i2], x[i]);
+        }
+    }
+#pragma unroll
+    for (int lb = 0; lb < 5; ++lb) {
+#pragma unroll
+        for (int i = 0; i < NR; ++i) {
+            float2 xo;
+            xo.x = __shfl_xor_sync(kFull, x[i].x, 1 << lb);
+            xo.y = __shfl_xor_sync(kFull, x[i].y, 1 << lb);
+            d += imconj(r[i], xo);
+        }
+    }
+    return d;
+}
+
+// <Z_0 Z_1> sign of register i (qubits 0 and 1 are register bits 0 and 1).
+__host__ __device__ constexpr float zz_sign(int i) { return ((i ^ (i >> 1)) & 1) ? -1.f : 1.f; }
+
+template <bool GRAD, int RB>
+__global__ void __launch_bounds__(128, GRAD ? 4 : 3) split_core_kernel(const __grid_constant__ BigLaunch L) {
+    constexpr int NR = 1 << RB;
+    constexpr int T = RB + 5;
+    constexpr int NW = NR / 4;  // packed cut counts, 4 registers per word
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    const int nin = L.n_in;
+    const int p = L.p;
+    const int64_t tiles = int64_t(1) << (nin - T);
+    const int64_t ntask = L.n_items * tiles;
+    const int64_t block_amps = int64_t(1) << nin;
+    for (int64_t task = gw; task < ntask; task += nw) {
+        const int64_t it = task / tiles;
+        const int64_t u = task - it * tiles;
+        int ci;
+        int64_t j, y;
+        decode_item(L, L.item0 + it, ci, j, y);
+        const DevCone *__restrict__ C = L.cones + L.cone_ids[ci];
+        if (C->n_in != nin) {
+            if (lane == 0) atomicOr(L.status, 1);
+            continue;
+        }
+        const int64_t gj = int64_t(C->graph) * L.P + j;
+        const float2 *__restrict__ lut = L.lut + gj * p * L.cmax1;
+        const float2 *__restrict__ cs = L.cs + gj * p;
+        // cut word of the tile's fixed bits: shell block, outer qubits, lane qubits
+        float mult = 1.f;
+        uint64_t base = shell_block(C, L.shell, uint32_t(y), mult);
+        for (int q = T; q < nin; ++q)
+            if ((u >> (q - T)) & 1) base ^= C->col[q];
+#pragma unroll
+        for (int lb = 0; lb < 5; ++lb)
+            if ((lane >> lb) & 1) base ^= C->col[RB + lb];
+        // cut value of every register, one byte each (a cone has < 256 edges)
+        uint32_t cnt[NW];
+        {
+            const uint64_t c0 = C->col[0], c1 = C->col[1];
+            const uint64_t lo[4] = {0ull, c0, c1, c0 ^ c1};
+#pragma unroll
+            for (int w = 0; w < NW; ++w) {
+                uint64_t h = base;
+#pragma unroll
+                for (int t = 0; t < RB - 2; ++t)
+                    if ((w >> t) & 1) h ^= C->col[2 + t];
+                uint32_t packed = 0;
+#pragma unroll
+                for (int a = 0; a < 4; ++a) packed |= uint32_t(__popcll(lo[a] ^ h)) << (8 * a);
+                cnt[w] = packed;
+            }
+        }
+        auto cut = [&](int i) -> int { return int((cnt[i >> 2] >> (8 * (i & 3))) & 0xffu); };
+        float2 *__restrict__ sp = L.psi + it * block_amps + (u << T) + lane;
+        float2 x[NR];
+        if (L.load) {
+#pragma unroll
+            for (int i = 0; i < NR; ++i) x[i] = sp[i << 5];
+        } else {
+#pragma unroll
+            for (int i = 0; i < NR; ++i) x[i] = __ldg(lut + cut(i));
+        }
+        const float sig = __int_as_float((127 - C->n) << 23);  // 2^-n
+        {  // first mixer on the core qubits
+            const float2 c_s = __ldg(cs);
+            mix_regs<NR>(x, RB, c_s.x, c_s.y);
+            mix_lanes<NR>(x, 5, c_s.x, c_s.y);
+        }
+        for (int l = 1; l < p; ++l) {
+            const float2 *__restrict__ lt = lut + l * L.cmax1;
+#pragma unroll
+            for (int i = 0; i < NR; ++i) x[i] = cmul(x[i], __ldg(lt + cut(i)));
+            const float2 c_s = __ldg(cs + l);
+            const int kl = C->k[l];
+            mix_regs<NR>(x, kl < RB ? kl : RB, c_s.x, c_s.y);
+            if (kl > RB) mix_lanes<NR>(x, kl - RB, c_s.x, c_s.y);
+        }
+        float acc = 0.f;
+#pragma unroll
+        for (int i = 0; i < NR; ++i) acc += zz_sign(i) * fmaf(x[i].x, x[i].x, x[i].y * x[i].y);
+        const float tv = acc * sig * mult;  // this tile's share of <Z_0 Z_1>
+        add_gp(-0.5f * float(C->weight) * tv, L.energy, gj);
+        if (L.terms) add_gp(tv, L.terms, C->rep * L.P + j);
+        if (GRAD) {
+            const float wgt2 = 2.f * float(C->weight) * mult * sig;
+            float2 r[NR];
+#pragma unroll
+            for (int i = 0; i < NR; ++i) {
+                const float h = -0.5f * zz_sign(i);
+                r[i] = make_float2(h * x[i].x, h * x[i].y);
+            }
+            for (int l = p - 1; l >= 1; --l) {
+                const float2 c_s = __ldg(cs + l);
+                const int kl = C->k[l];
+                float d = 0.f;
+                unmix_regs_d<NR>(x, r, kl < RB ? kl : RB, c_s.x, c_s.y, d);
+                if (kl > RB) unmix_lanes_d<NR>(x, r, kl - RB, c_s.x, c_s.y, d);
+                add_gp(wgt2 * d, L.grad, gj * 2 * p + p + l);
+                const float2 *__restrict__ lt = lut + l * L.cmax1;
+                float dg = 0.f;
+#pragma unroll
+                for (int i = 0; i < NR; ++i) {
+                    const int c = cut(i);
+                    dg = fmaf(float(c), imconj(r[i], x[i]), dg);
+                    const float2 ph = __ldg(lt + c);
+                    x[i] = cmulc(x[i], ph);
+                    r[i] = cmulc(r[i], ph);
+                }
+                add_gp(wgt2 * dg, L.grad, gj * 2 * p + l);
+            }
+            // first mixer: the core qubits' terms, then lambda alone un-mixed
+            const float2 c_s = __ldg(cs);
+            add_gp(wgt2 * xterms_all<NR>(x, r), L.grad, gj * 2 * p + p);
+            mix_regs<NR>(r, RB, c_s.x, -c_s.y);
+            mix_lanes<NR>(r, 5, c_s.x, -c_s.y);
+#pragma unroll
+            for (int i = 0; i < NR; ++i) sp[i << 5] = r[i];
+        }
+    }
+}
+
+// Qubit held by storage address bit a (see the layout above).
+__device__ __forceinline__ int qubit_of(int a, int rb) { return a < 5 ? rb + a : (a < rb + 5 ? a - 5 : a); }
+
+template <int MODE>
+__global__ void __launch_bounds__(128, MODE == kOuterGen ? 4 : 3) split_outer_kernel(const __grid_constant__ BigLaunch L) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    const int nin = L.n_in, b = L.b, RB = L.rb;
+    const int r0 = L.w0 - b, r1 = L.w1 - b;  // register bits of the outer qubits to mix
+    const int p = L.p;
+    const int64_t tiles = int64_t(1) << (nin - 10);
+    const int64_t ntask = L.n_items * tiles;
+    const int64_t block_amps = int64_t(1) << nin;
+    const int64_t lowmask = (int64_t(1) << (b - 5)) - 1;
+    for (int64_t task = gw; task < ntask; task += nw) {
+        const int64_t it = task / tiles;
+        const int64_t tile = task - it * tiles;
+        int ci;
+        int64_t j, y;
+        decode_item(L, L.item0 + it, ci, j, y);
+        const DevCone *__restrict__ C = L.cones + L.cone_ids[ci];
+        if (C->n_in != nin) {
+            if (lane == 0) atomicOr(L.status, 1);
+            continue;
+        }
+        const int64_t gj = int64_t(C->graph) * L.P + j;
+        const float2 c_s = __ldg(L.cs + gj * p);
+        // address of (lane, register i) = xb | (i << b) | lane
+        const int64_t xb = ((tile & lowmask) << 5) | ((tile >> (b - 5)) << (b + 5));
+        float2 *__restrict__ sp = L.psi + it * block_amps + xb + lane;
+        float2 x[32];
+        if (MODE != kOuterGen) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) x[i] = sp[int64_t(i) << b];
+        }
+        if (MODE == kOuterMix) {
+            mix_window(x, r0, r1, c_s.x, float(L.sign) * c_s.y);
+        } else {
+            const float2 *__restrict__ lut = L.lut + gj * p * L.cmax1;  // first layer's phase table
+            float mult = 1.f;
+            uint64_t base = shell_block(C, L.shell, uint32_t(y), mult);
+#pragma unroll
+            for (int lb = 0; lb < 5; ++lb)
+                if ((lane >> lb) & 1) base ^= C->col[RB + lb];
+            for (int a = 5; a < nin; ++a)
+                if ((a < b || a >= b + 5) && ((xb >> a) & 1)) base ^= C->col[qubit_of(a, RB)];
+            uint64_t lo[4], hi[8];
+            {
+                const uint64_t c0 = C->col[qubit_of(b, RB)], c1 = C->col[qubit_of(b + 1, RB)];
+                const uint64_t c2 = C->col[qubit_of(b + 2, RB)], c3 = C->col[qubit_of(b + 3, RB)];
+                const uint64_t c4 = C->col[qubit_of(b + 4, RB)];
+                lo[0] = 0;
+                lo[1] = c0;
+                lo[2] = c1;
+                lo[3] = c0 ^ c1;
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    hi[k] = base ^ ((k & 1) ? c2 : 0ull) ^ ((k & 2) ? c3 : 0ull) ^ ((k & 4) ? c4 : 0ull);
+            }
+            if (MODE == kOuterGen) {
+#pragma unroll
+                for (int i = 0; i < 32; ++i) x[i] = __ldg(lut + __popcll(lo[i & 3] ^ hi[i >> 2]));
+                mix_window(x, r0, r1, c_s.x, c_s.y);
+            } else {  // kOuterFirst: x holds lambda
+                mix_window(x, r0, r1, c_s.x, -c_s.y);
+                float dg = 0.f, db = 0.f;
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const int c = __popcll(lo[i & 3] ^ hi[i >> 2]);
+                    const float2 ph = __ldg(lut + c);  // state before the first mixer, times 2^(n/2)
+                    dg = fmaf(float(c), imconj(x[i], ph), dg);
+#pragma unroll
+                    for (int rb = 0; rb < 5; ++rb)
+                        if (rb >= r0 && rb < r1) db += imconj(x[i ^ (1 << rb)], ph);
+                }
+                for (int q = L.x0; q < L.x1; ++q) {  // outer qubits outside the window
+                    const uint64_t cq = C->col[q];
+#pragma unroll
+                    for (int i = 0; i < 32; ++i)
+                        db += imconj(x[i], __ldg(lut + __popcll(lo[i & 3] ^ hi[i >> 2] ^ cq)));
+                }
+                const float wgt2 = 2.f * float(C->weight) * mult * __int_as_float((127 - C->n) << 23);
+                add_gp(wgt2 * dg, L.grad, gj * 2 * p);
+                add_gp(wgt2 * db, L.grad, gj * 2 * p + p);
+            }
+        }
+        if (MODE != kOuterFirst) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) sp[int64_t(i) << b] = x[i];
+        }
+    }
+}
+
+}  // namespace
+
+int occupancy_grid(const void *fn, int block, size_t smem);
+
+bool split_ok(int n_in, int p, const int32_t *k, bool grad) {
+    const int T = (grad ? kSplitRbGrad : kSplitRbEnergy) + 5;
+    if (n_in < 10 || n_in < T || n_in > QAOA_MAX_CONE_QUBITS || k[0] != n_in) return false;
+    if (grad && n_in == T) return false;
+    for (int l = 1; l < p; ++l)
+        if (k[l] > T) return false;
+    return true;
+}
+
+cudaError_t launch_split_wave(BigLaunch B, bool grad, int64_t &launches, cudaStream_t s) {
+    const int RB = grad ? kSplitRbGrad : kSplitRbEnergy, T = RB + 5;
+    const int nin = B.n_in;
+    B.rb = RB;
+    std::vector<std::pair<int, int>> win;  // outer qubit windows, five qubits each
+    for (int w0 = T; w0 < nin; w0 += 5) win.emplace_back(w0, std::min(w0 + 5, nin));
+    auto grid_for = [](const void *fn, int64_t tasks) {
+        const int64_t need = std::max<int64_t>(1, (tasks + 3) / 4);
+        return int(std::min<int64_t>(occupancy_grid(fn, 128, 0), need));
+    };
+    auto outer = [&](int mode, size_t w, int sign) -> cudaError_t {
+        B.mode = mode;
+        B.w0 = win[w].first;
+        B.w1 = win[w].second;
+        B.b = std::min(B.w0, nin - 5);
+        B.x0 = win[w].second;
+        B.x1 = nin;
+        B.sign = sign;
+        const int64_t tasks = B.n_items << (nin - 10);
+        if (mode == kOuterGen) {
+            const void *fn = (const void *)split_outer_kernel<kOuterGen>;
+            split_outer_kernel<kOuterGen><<<grid_for(fn, tasks), 128, 0, s>>>(B);
+        } else if (mode == kOuterMix) {
+            const void *fn = (const void *)split_outer_kernel<kOuterMix>;
+            split_outer_kernel<kOuterMix><<<grid_for(fn, tasks), 128, 0, s>>>(B);
+        } else {
+            const void *fn = (const void *)split_outer_kernel<kOuterFirst>;
+            split_outer_kernel<kOuterFirst><<<grid_for(fn, tasks), 128, 0, s>>>(B);
+        }
+        ++launches;
+        return cudaGetLastError();
+    };
+    if (grad && win.empty()) return cudaErrorInvalidValue;  // excluded by split_ok
+    cudaError_t e = cudaSuccess;
+    for (size_t w = 0; w < win.size() && e == cudaSuccess; ++w) e = outer(w == 0 ? kOuterGen : kOuterMix, w, 1);
+    if (e != cudaSuccess) return e;
+    B.load = win.empty() ? 0 : 1;
+    const int64_t core_tasks = B.n_items << (nin - T);
+    if (grad) {
+        const void *fn = (const void *)split_core_kernel<true, kSplitRbGrad>;
+        split_core_kernel<true, kSplitRbGrad><<<grid_for(fn, core_tasks), 128, 0, s>>>(B);
+    } else {
+        const void *fn = (const void *)split_core_kernel<false, kSplitRbEnergy>;
+        split_core_kernel<false, kSplitRbEnergy><<<grid_for(fn, core_tasks), 128, 0, s>>>(B);
+    }
+    ++launches;
+    if ((e = cudaGetLastError()) != cudaSuccess || !grad) return e;
+    for (size_t w = win.size(); w-- > 1 && e == cudaSuccess;) e = outer(kOuterMix, w, -1);
+    if (e != cudaSuccess) return e;
+    return outer(kOuterFirst, 0, -1);
+}
+
+}  // namespace qaoa

@@ -128,9 +128,10 @@ cudaError_t run_big(const qaoa_device_plan *d, const qaoa_plan *plan, int64_t P,
     const int grid = big_grid(g);
     for (const BigShape &bs : d->big) {
         if (e != cudaSuccess) break;
-        const int64_t block_bytes = (int64_t(1) << bs.n_in) * int64_t(sizeof(float2)) * (g ? 2 : 1);
-        const int64_t Y = bs.n_blocks;
-        const int64_t items = int64_t(bs.cones.size()) * P * Y;
+        const bool split = g ? bs.split_g : bs.split_e;
+        // the general adjoint keeps psi and lambda; everything else one block per item
+        const int64_t block_bytes = (int64_t(1) << bs.n_in) * int64_t(sizeof(float2)) * (g && !split ? 2 : 1);
+        const int64_t items = bs.ystart.back() * P;
         const int64_t wave = std::max<int64_t>(1, std::min<int64_t>(items, int64_t(d->big_budget) / block_bytes));
         float2 *scratch = nullptr;
         e = cudaMallocAsync(&scratch, size_t(wave) * block_bytes, s);
@@ -138,16 +139,16 @@ cudaError_t run_big(const qaoa_device_plan *d, const qaoa_plan *plan, int64_t P,
         BigLaunch B{};
         B.cones = d->cones;
         B.cone_ids = bs.d_cones;
-        B.n = bs.n;
+        B.ystart = bs.d_ystart;
+        B.n_shape = int32_t(bs.cones.size());
         B.n_in = bs.n_in;
-        B.Y = Y;
         B.P = P;
         B.p = p;
         B.cmax1 = d->cmax1;
         B.lut = lut;
         B.cs = cs;
         B.psi = scratch;
-        B.lam = g ? scratch + size_t(wave) * (size_t(1) << bs.n_in) : nullptr;
+        B.lam = g && !split ? scratch + size_t(wave) * (size_t(1) << bs.n_in) : nullptr;
         B.shell = d->shell;
         B.energy = energy;
         B.grad = grad;
@@ -157,6 +158,10 @@ cudaError_t run_big(const qaoa_device_plan *d, const qaoa_plan *plan, int64_t P,
         for (int64_t i0 = 0; i0 < items && e == cudaSuccess; i0 += wave) {
             B.item0 = i0;
             B.n_items = std::min(wave, items - i0);
+            if (split) {
+                e = launch_split_wave(B, g, dm->all_launches, s);
+                continue;
+            }
             for (const BigPass &ps : passes) {
                 B.pass = ps;
                 e = launch_big_pass(B, g, grid, s);
@@ -282,7 +287,10 @@ extern "C" void qaoa_device_release(qaoa_plan *plan) {
     cudaFree(d->cones);
     free_work(d->reg_e);
     free_work(d->reg_g);
-    for (auto &bs : d->big) cudaFree(bs.d_cones);
+    for (auto &bs : d->big) {
+        cudaFree(bs.d_cones);
+        cudaFree(bs.d_ystart);
+    }
     cudaFree(d->half_edges);
     cudaFree(d->status);
     cudaFree(d->shell);
@@ -357,18 +365,21 @@ extern "C" int qaoa_plan_upload(qaoa_plan *plan) {
         std::vector<int32_t> kv(c.k, c.k + plan->p);
         BigShape *shape = nullptr;
         for (auto &bs : d->big)
-            if (bs.n == c.n && bs.n_in == c.n_in && bs.k == kv && bs.n_blocks == c.n_blocks) shape = &bs;
+            if (bs.n_in == c.n_in && bs.k == kv) shape = &bs;
         if (!shape) {
             d->big.emplace_back();
             shape = &d->big.back();
-            shape->n = c.n;
             shape->n_in = c.n_in;
-            shape->n_blocks = c.n_blocks;
             shape->k = kv;
+            shape->ystart.push_back(0);
+            const bool general = (plan->flags & QAOA_BIG_GENERAL) != 0;
+            shape->split_e = !general && split_ok(c.n_in, plan->p, kv.data(), false);
+            shape->split_g = !general && split_ok(c.n_in, plan->p, kv.data(), true);
             shape->fwd = big_forward_passes(c.n_in, plan->p, kv.data());
             shape->grad = big_grad_passes(c.n_in, plan->p, kv.data());
         }
         shape->cones.push_back(int32_t(i));
+        shape->ystart.push_back(shape->ystart.back() + c.n_blocks);
     }
     cudaGetDevice(&d->device);
     d->n_cones = int64_t(hc.size());
@@ -387,10 +398,13 @@ extern "C" int qaoa_plan_upload(qaoa_plan *plan) {
     }
     for (auto &bs : d->big) {
         if (rc != QAOA_OK) break;
-        if ((e = cudaMalloc(&bs.d_cones, bs.cones.size() * sizeof(int32_t))) != cudaSuccess)
+        if ((e = cudaMalloc(&bs.d_cones, bs.cones.size() * sizeof(int32_t))) != cudaSuccess ||
+            (e = cudaMalloc(&bs.d_ystart, bs.ystart.size() * sizeof(int64_t))) != cudaSuccess) {
             rc = cuda_fail(e, "cudaMalloc");
-        else
+        } else {
             cudaMemcpy(bs.d_cones, bs.cones.data(), bs.cones.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+            cudaMemcpy(bs.d_ystart, bs.ystart.data(), bs.ystart.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+        }
     }
     if (rc == QAOA_OK) {
         if (shell_tab.empty()) shell_tab.push_back(0);

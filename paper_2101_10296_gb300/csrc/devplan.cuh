@@ -16,14 +16,17 @@ struct DevWork {
     int32_t n = 0;
 };
 
-// Cones of one shape (n, n_in, k_1..k_p) on the large-state path.
+// Cones of one shape (n_in, k_1..k_p) on the large-state path.  Items of a
+// call are numbered cone by cone (P * n_blocks each).
 struct BigShape {
-    int32_t n = 0, n_in = 0;
-    int64_t n_blocks = 1;  // shell blocks per (cone, point)
+    int32_t n_in = 0;
     std::vector<int32_t> k;
-    std::vector<int32_t> cones;  // plan indices
+    std::vector<int32_t> cones;   // plan indices
+    std::vector<int64_t> ystart;  // [cones + 1] prefix of the cones' shell-block counts
     int32_t *d_cones = nullptr;
-    std::vector<qaoa::BigPass> fwd, grad;
+    int64_t *d_ystart = nullptr;
+    bool split_e = false, split_g = false;  // core-tile schedule usable (energy, adjoint)
+    std::vector<qaoa::BigPass> fwd, grad;   // general schedule
 };
 
 struct qaoa_device_plan {

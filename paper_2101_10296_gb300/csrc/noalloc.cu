@@ -151,18 +151,18 @@ extern "C" int qaoa_energy_noalloc(const qaoa_plan *plan, int64_t n_points, cons
     if (e == cudaSuccess && !d->big.empty()) {
         e = launch_big_prep(params_dev, int64_t(GP), p, cs, s);
         const int grid = big_grid(false);
+        int64_t launches = 0;
         for (const BigShape &bs : d->big) {
             if (e != cudaSuccess) break;
             const size_t block_bytes = (size_t(1) << bs.n_in) * sizeof(float2);
-            const int64_t Y = bs.n_blocks;
-            const int64_t items = int64_t(bs.cones.size()) * n_points * Y;
+            const int64_t items = bs.ystart.back() * n_points;
             const int64_t wave = std::max<int64_t>(1, std::min<int64_t>(items, int64_t(block_room / block_bytes)));
             BigLaunch B{};
             B.cones = d->cones;
             B.cone_ids = bs.d_cones;
-            B.n = bs.n;
+            B.ystart = bs.d_ystart;
+            B.n_shape = int32_t(bs.cones.size());
             B.n_in = bs.n_in;
-            B.Y = Y;
             B.P = n_points;
             B.p = p;
             B.cmax1 = d->cmax1;
@@ -178,6 +178,10 @@ extern "C" int qaoa_energy_noalloc(const qaoa_plan *plan, int64_t n_points, cons
             for (int64_t i0 = 0; i0 < items && e == cudaSuccess; i0 += wave) {
                 B.item0 = i0;
                 B.n_items = std::min(wave, items - i0);
+                if (bs.split_e) {
+                    e = launch_split_wave(B, false, launches, s);
+                    continue;
+                }
                 for (const BigPass &ps : bs.fwd) {
                     B.pass = ps;
                     e = launch_big_pass(B, false, grid, s);

@@ -198,7 +198,7 @@ extern "C" int qaoa_plan_graphs(int32_t n_graphs, const int32_t *n_vertices, con
         set_error("p must be in [1, QAOA_MAX_P]");
         return QAOA_E_INVALID;
     }
-    if (flags & ~uint32_t(QAOA_ORBITS | QAOA_FULL_CONE | QAOA_SHELL_PLAIN)) {
+    if (flags & ~uint32_t(QAOA_ORBITS | QAOA_FULL_CONE | QAOA_SHELL_PLAIN | QAOA_BIG_GENERAL)) {
         set_error("unknown flag bits");
         return QAOA_E_INVALID;
     }

@@ -26,6 +26,7 @@ ORBITS_OFF = 0
 ORBITS = 1
 FULL_CONE = 2
 SHELL_PLAIN = 4
+BIG_GENERAL = 8
 
 
 class QAOAError(RuntimeError):
@@ -144,7 +145,7 @@ class Plan:
     """A planned batch of graphs (orbits + cones), owning its device copy."""
 
     def __init__(self, graphs, p, orbits=True, full_cone=False, max_cone_qubits=0, search_budget=0,
-                 shell_plain=False):
+                 shell_plain=False, big_general=False):
         if isinstance(graphs, tuple):
             graphs = [graphs]
         nv = _i32([g[0] for g in graphs])
@@ -157,6 +158,7 @@ class Plan:
         edges = _i32(np.concatenate(rows) if rows else np.zeros((0, 2)))
         offs = np.asarray(offs, dtype=np.int64)
         flags = (ORBITS if orbits else ORBITS_OFF) | (FULL_CONE if full_cone else 0) | (SHELL_PLAIN if shell_plain else 0)
+        flags |= BIG_GENERAL if big_general else 0
         h = C.c_void_p()
         _check(lib().qaoa_plan_graphs(len(graphs), _ptr(nv, C.c_int32), _ptr(offs, C.c_int64),
                                       _ptr(edges, C.c_int32) if edges.size else None, p, flags,

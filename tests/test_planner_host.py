@@ -269,6 +269,22 @@ def test_bad_call_arguments(qlib):
     assert qlib.lib().qaoa_energy(None, 1, None, None, None, None) == qlib.QAOA_E_INVALID
 
 
+def test_plan_flags(qlib):
+    """Every documented flag is accepted (the large-state schedule switch
+    changes nothing on the host), an unknown bit is refused."""
+    import ctypes as C
+    n, edges = I.random_regular(24, 3, 1)
+    a = qlib.Plan((n, edges), 3)
+    b = qlib.Plan((n, edges), 3, big_general=True)
+    for key in ("n_qubits", "n_inner", "weight"):
+        assert np.array_equal(a.reps()[key], b.reps()[key])
+    assert np.array_equal(a.shell_blocks(), b.shell_blocks())
+    e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32))
+    h = C.c_void_p()
+    rc = qlib.lib().qaoa_plan_graph(n, len(edges), qlib._ptr(e, C.c_int32), 3, 16, 0, 0, C.byref(h))
+    assert rc == qlib.QAOA_E_INVALID
+
+
 # ------------------------------------------------------------ shell classes
 
 @pytest.mark.parametrize("graph,p", [
