@@ -189,11 +189,12 @@ __global__ void __launch_bounds__(128) big_pass_kernel(const __grid_constant__ B
                 case kOpUnphase: {  // q0 = 1: also undo the phase
                     if (GRAD) {
                         const float2 *__restrict__ lt = lut + l * L.cmax1;
+                        const float c0 = 0.5f * float(C->m);  // Im<r|x> = 0: C - c0 in place of C
                         float d = 0.f;
 #pragma unroll
                         for (int i = 0; i < NR; ++i) {
                             const int c = __popcll(lo[i & 3] ^ hi[i >> 2]);
-                            d = fmaf(float(c), imconj(r[i], x[i]), d);
+                            d = fmaf(float(c) - c0, imconj(r[i], x[i]), d);
                             if (op.q0) {
                                 const float2 ph = __ldg(lt + c);
                                 x[i] = cmulc(x[i], ph);

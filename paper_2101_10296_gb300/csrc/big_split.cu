@@ -128,12 +128,14 @@ __device__ __forceinline__ void unmix_lanes_d(float2 (&x)[NR], float2 (&r)[NR], 
     }
 }
 
-// Sum of Im<r|X_q|x> over every register and lane qubit, states unchanged.
+// Sum of Im<r|X_q|x> over every register and lane qubit (only qubits 0 and 1
+// unless `all`), states unchanged.
 template <int NR>
-__device__ __forceinline__ float xterms_all(const float2 (&x)[NR], const float2 (&r)[NR]) {
+__device__ __forceinline__ float xterms(const float2 (&x)[NR], const float2 (&r)[NR], bool all) {
     float d = 0.f;
 #pragma unroll
     for (int rb = 0; (1 << rb) < NR; ++rb) {
+        if (!all && rb >= 2) continue;
 #pragma unroll
         for (int i = 0; i < NR; ++i) {
             if (i & (1 << rb)) continue;
@@ -141,6 +143,7 @@ __device__ __forceinline__ float xterms_all(const float2 (&x)[NR], const float2 
             d += imconj(r[i], x[i2]) + imconj(r[i2], x[i]);
         }
     }
+    if (!all) return d;
 #pragma unroll
     for (int lb = 0; lb < 5; ++lb) {
 #pragma unroll
@@ -157,8 +160,12 @@ __device__ __forceinline__ float xterms_all(const float2 (&x)[NR], const float2 
 // <Z_0 Z_1> sign of register i (qubits 0 and 1 are register bits 0 and 1).
 __host__ __device__ constexpr float zz_sign(int i) { return ((i ^ (i >> 1)) & 1) ? -1.f : 1.f; }
 
+#ifndef QAOA_SPLIT_GRAD_BLOCKS
+#define QAOA_SPLIT_GRAD_BLOCKS 4  // resident CTAs per SM of the adjoint core kernel
+#endif
+
 template <bool GRAD, int RB>
-__global__ void __launch_bounds__(128, GRAD ? 4 : 3) split_core_kernel(const __grid_constant__ BigLaunch L) {
+__global__ void __launch_bounds__(128, GRAD ? QAOA_SPLIT_GRAD_BLOCKS : 3) split_core_kernel(const __grid_constant__ BigLaunch L) {
     constexpr int NR = 1 << RB;
     constexpr int T = RB + 5;
     constexpr int NW = NR / 4;  // packed cut counts, 4 registers per word
@@ -248,6 +255,11 @@ __global__ void __launch_bounds__(128, GRAD ? 4 : 3) split_core_kernel(const __g
                 const float h = -0.5f * zz_sign(i);
                 r[i] = make_float2(h * x[i].x, h * x[i].y);
             }
+            // In d/d gamma_l, C may be replaced by C - c0: Im<lambda|psi> =
+            // <psi_end|O|psi_end> is zero within every core tile, and c0 = m/2
+            // (the mean cut value) removes most of the cancellation in the
+            // FP32 sums.
+            const float c0 = 0.5f * float(C->m);
             for (int l = p - 1; l >= 1; --l) {
                 const float2 c_s = __ldg(cs + l);
                 const int kl = C->k[l];
@@ -256,11 +268,15 @@ __global__ void __launch_bounds__(128, GRAD ? 4 : 3) split_core_kernel(const __g
                 if (kl > RB) unmix_lanes_d<NR>(x, r, kl - RB, c_s.x, c_s.y, d);
                 add_gp(wgt2 * d, L.grad, gj * 2 * p + p + l);
                 const float2 *__restrict__ lt = lut + l * L.cmax1;
+                // keep the shifted cut values from being hoisted out of the layer
+                // loop into sixteen live registers
+#pragma unroll
+                for (int w = 0; w < NW; ++w) asm volatile("" : "+r"(cnt[w]));
                 float dg = 0.f;
 #pragma unroll
                 for (int i = 0; i < NR; ++i) {
                     const int c = cut(i);
-                    dg = fmaf(float(c), imconj(r[i], x[i]), dg);
+                    dg = fmaf(float(c) - c0, imconj(r[i], x[i]), dg);
                     const float2 ph = __ldg(lt + c);
                     x[i] = cmulc(x[i], ph);
                     r[i] = cmulc(r[i], ph);
@@ -269,7 +285,10 @@ __global__ void __launch_bounds__(128, GRAD ? 4 : 3) split_core_kernel(const __g
             }
             // first mixer: the core qubits' terms, then lambda alone un-mixed
             const float2 c_s = __ldg(cs);
-            add_gp(wgt2 * xterms_all<NR>(x, r), L.grad, gj * 2 * p + p);
+            // At p = 1 the first layer is the last: lambda = O psi with
+            // O = -1/2 Z_0 Z_1, and <psi|O X_q|psi> is real for every q other
+            // than 0 and 1 (X_q and O commute), so only those two contribute.
+            add_gp(wgt2 * xterms<NR>(x, r, p > 1), L.grad, gj * 2 * p + p);
             mix_regs<NR>(r, RB, c_s.x, -c_s.y);
             mix_lanes<NR>(r, 5, c_s.x, -c_s.y);
 #pragma unroll
@@ -344,17 +363,23 @@ __global__ void __launch_bounds__(128, MODE == kOuterGen ? 4 : 3) split_outer_ke
                 mix_window(x, r0, r1, c_s.x, c_s.y);
             } else {  // kOuterFirst: x holds lambda
                 mix_window(x, r0, r1, c_s.x, -c_s.y);
+                // the outer qubits' mixer terms vanish at p = 1, where the first
+                // layer is the last (only qubits 0 and 1 contribute there)
+                const bool outer_terms = p > 1;
+                const float c0 = 0.5f * float(C->m);  // Im<lambda|psi> = 0: C - c0 in place of C
                 float dg = 0.f, db = 0.f;
 #pragma unroll
                 for (int i = 0; i < 32; ++i) {
                     const int c = __popcll(lo[i & 3] ^ hi[i >> 2]);
                     const float2 ph = __ldg(lut + c);  // state before the first mixer, times 2^(n/2)
-                    dg = fmaf(float(c), imconj(x[i], ph), dg);
+                    dg = fmaf(float(c) - c0, imconj(x[i], ph), dg);
+                    if (outer_terms) {
 #pragma unroll
-                    for (int rb = 0; rb < 5; ++rb)
-                        if (rb >= r0 && rb < r1) db += imconj(x[i ^ (1 << rb)], ph);
+                        for (int rb = 0; rb < 5; ++rb)
+                            if (rb >= r0 && rb < r1) db += imconj(x[i ^ (1 << rb)], ph);
+                    }
                 }
-                for (int q = L.x0; q < L.x1; ++q) {  // outer qubits outside the window
+                for (int q = L.x0; q < (outer_terms ? L.x1 : L.x0); ++q) {  // outer qubits outside the window
                     const uint64_t cq = C->col[q];
 #pragma unroll
                     for (int i = 0; i < 32; ++i)
@@ -362,7 +387,7 @@ __global__ void __launch_bounds__(128, MODE == kOuterGen ? 4 : 3) split_outer_ke
                 }
                 const float wgt2 = 2.f * float(C->weight) * mult * __int_as_float((127 - C->n) << 23);
                 add_gp(wgt2 * dg, L.grad, gj * 2 * p);
-                add_gp(wgt2 * db, L.grad, gj * 2 * p + p);
+                if (outer_terms) add_gp(wgt2 * db, L.grad, gj * 2 * p + p);
             }
         }
         if (MODE != kOuterFirst) {

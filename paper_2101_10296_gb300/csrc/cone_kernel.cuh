@@ -350,6 +350,11 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? kGradMinBlocks : kEnergyMinB
                 }
                 const float gw2 = active ? 2.f * wgt : 0.f;
                 const float sig_end = sig;
+                // Im<lambda|psi> = <psi_end|O|psi_end> is real at every point of
+                // the sweep (and within every shell block), so C may be replaced
+                // by C - c0 in d/d gamma: c0 = m/2 removes the mean cut value and
+                // with it most of the cancellation in the FP32 sums.
+                const float c0 = 0.5f * float(C->m);
 #pragma unroll(PC > 0 ? PC : 1)
                 for (int l = p - 1; l >= 0; --l) {
                     const float2 mx = __ldg(mix + l);
@@ -421,7 +426,7 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? kGradMinBlocks : kEnergyMinB
                     const float2 *lt = lut + l * L.cmax1;
                     if (l > 0) {
                         cw.visit([&](int i, int cv) {
-                            dg4[i >> 2] = fmaf(float(cv), imconj(r[i], x[i]), dg4[i >> 2]);
+                            dg4[i >> 2] = fmaf(float(cv) - c0, imconj(r[i], x[i]), dg4[i >> 2]);
                             const float2 ph = lt[cv];
                             x[i] = cmulc(x[i], ph);
                             r[i] = cmulc(r[i], ph);
@@ -432,7 +437,7 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? kGradMinBlocks : kEnergyMinB
                         // butterflies, and sigma * Lambda = sigma at the end of the forward
                         // sweep: use the table and that sigma.
                         cw.visit([&](int i, int cv) {
-                            dg4[i >> 2] = fmaf(float(cv), imconj(r[i], lt[cv]), dg4[i >> 2]);
+                            dg4[i >> 2] = fmaf(float(cv) - c0, imconj(r[i], lt[cv]), dg4[i >> 2]);
                         });
                     }
                     float dgs = 0.f;
