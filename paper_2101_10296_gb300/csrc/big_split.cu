@@ -31,6 +31,9 @@
 // often mixed qubits 0, 1 are register butterflies and <Z_0 Z_1>'s sign is a
 // compile-time function of the register.  Every load and store moves 256
 // contiguous bytes per warp instruction.
+#include <mutex>
+#include <set>
+
 #include "big.cuh"
 #include "big_common.cuh"
 
@@ -397,6 +400,197 @@ __global__ void __launch_bounds__(128, MODE == kOuterGen ? 4 : 3) split_outer_ke
     }
 }
 
+// ------------------------------------------------------------ chunk passes
+// An outer pass over more than five outer qubits stages a chunk of the block
+// in shared memory: 2^13 amplitudes made of the lowest lo = 13 - w address
+// bits (contiguous runs of at least 64 bytes) and a window of w <=
+// kChunkMaxW outer qubits.  The window is mixed five qubits at a time by
+// register butterflies over amplitudes gathered from shared memory, so one
+// HBM round trip covers all of it.
+constexpr int kChunkBits = 13;
+constexpr int kChunkMaxW = 10;
+constexpr int kChunkThreads = 256;
+
+// Bank swizzle: bit 3 of the shared-memory index (which 64-byte half of a
+// 128-byte row) is flipped by the parity of the bits above it, so the four
+// 64-byte runs that a warp touches fall two in each half.
+__device__ __forceinline__ int swz(int s) { return s ^ ((__popc(s >> 4) & 1) << 3); }
+
+// slot with gn zero bits inserted at bit position pos
+__device__ __forceinline__ int spread_slot(int slot, int pos, int gn) {
+    return (slot & ((1 << pos) - 1)) | ((slot >> pos) << (pos + gn));
+}
+
+// First-layer cut words of a chunk slot: `base` for the slot's fixed bits,
+// lo/hi over the G register qubits w0 .. w0+G-1.
+template <int G>
+__device__ __forceinline__ void slot_words(const DevCone *__restrict__ C, uint64_t base, int w0, uint64_t (&lo)[4],
+                                           uint64_t (&hi)[8]) {
+    uint64_t cr[5];
+#pragma unroll
+    for (int b = 0; b < 5; ++b) cr[b] = b < G ? C->col[w0 + b] : 0ull;
+    lo[0] = 0;
+    lo[1] = cr[0];
+    lo[2] = cr[1];
+    lo[3] = cr[0] ^ cr[1];
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        hi[k] = base ^ ((k & 1) ? cr[2] : 0ull) ^ ((k & 2) ? cr[3] : 0ull) ^ ((k & 4) ? cr[4] : 0ull);
+}
+
+// One round of a chunk pass: every slot gathers the 2^G amplitudes that
+// differ in chunk bits [pos, pos+G), applies the mixer to those G qubits and
+// writes them back.  GEN in its first round generates the amplitudes instead.
+template <int G, bool GEN>
+__device__ __forceinline__ void chunk_round(float2 *__restrict__ sm, int n_el, int pos, float c, float sn,
+                                            const DevCone *__restrict__ C, uint64_t cw, int lo_bits, int RB, int w0,
+                                            const float2 *__restrict__ lut) {
+    constexpr int NR = 1 << G;
+    for (int slot = threadIdx.x; slot < (n_el >> G); slot += kChunkThreads) {
+        const int sb = spread_slot(slot, pos, G);
+        float2 x[NR];
+        if (GEN) {
+            uint64_t base = cw;
+            for (int b = 0; b < lo_bits; ++b)  // the window bits of sb are zero in the first round
+                if ((sb >> b) & 1) base ^= C->col[qubit_of(b, RB)];
+            for (int b = lo_bits + G; b < kChunkBits; ++b)
+                if ((sb >> b) & 1) base ^= C->col[w0 + b - lo_bits];
+            uint64_t lo[4], hi[8];
+            slot_words<G>(C, base, w0, lo, hi);
+#pragma unroll
+            for (int i = 0; i < NR; ++i) x[i] = __ldg(lut + __popcll(lo[i & 3] ^ hi[i >> 2]));
+        } else {
+#pragma unroll
+            for (int i = 0; i < NR; ++i) x[i] = sm[swz(sb | (i << pos))];
+        }
+        mix_regs<NR>(x, G, c, sn);
+#pragma unroll
+        for (int i = 0; i < NR; ++i) sm[swz(sb | (i << pos))] = x[i];
+    }
+}
+
+template <bool GEN>
+__device__ __forceinline__ void chunk_round_any(int G, float2 *sm, int n_el, int pos, float c, float sn,
+                                                const DevCone *C, uint64_t cw, int lo_bits, int RB, int w0,
+                                                const float2 *lut) {
+    switch (G) {
+        case 1: chunk_round<1, GEN>(sm, n_el, pos, c, sn, C, cw, lo_bits, RB, w0, lut); break;
+        case 2: chunk_round<2, GEN>(sm, n_el, pos, c, sn, C, cw, lo_bits, RB, w0, lut); break;
+        case 3: chunk_round<3, GEN>(sm, n_el, pos, c, sn, C, cw, lo_bits, RB, w0, lut); break;
+        case 4: chunk_round<4, GEN>(sm, n_el, pos, c, sn, C, cw, lo_bits, RB, w0, lut); break;
+        default: chunk_round<5, GEN>(sm, n_el, pos, c, sn, C, cw, lo_bits, RB, w0, lut); break;
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kChunkThreads, 2) split_chunk_kernel(const __grid_constant__ BigLaunch L) {
+    extern __shared__ float4 sm4[];
+    float2 *sm = reinterpret_cast<float2 *>(sm4);
+    const int tid = threadIdx.x;
+    const int nin = L.n_in, RB = L.rb, w0 = L.w0, w = L.w1 - L.w0;
+    const int lo_bits = kChunkBits - w;  // lowest address bits of the chunk (w0 >= lo_bits)
+    const int n_el = 1 << kChunkBits;
+    const int p = L.p;
+    const int64_t chunks = int64_t(1) << (nin - kChunkBits);
+    const int64_t ntask = L.n_items * chunks;
+    const int64_t block_amps = int64_t(1) << nin;
+    const int64_t lowmask = (int64_t(1) << (w0 - lo_bits)) - 1;
+    const int runmask = (1 << lo_bits) - 1;
+    for (int64_t task = blockIdx.x; task < ntask; task += gridDim.x) {
+        const int64_t it = task / chunks;
+        const int64_t ch = task - it * chunks;
+        int ci;
+        int64_t j, y;
+        decode_item(L, L.item0 + it, ci, j, y);
+        const DevCone *__restrict__ C = L.cones + L.cone_ids[ci];
+        if (C->n_in != nin) {  // uniform over the CTA
+            if (tid == 0) atomicOr(L.status, 1);
+            continue;
+        }
+        const int64_t gj = int64_t(C->graph) * L.P + j;
+        const float2 c_s = __ldg(L.cs + gj * p);
+        const float sn = MODE == kOuterGen ? c_s.y : (MODE == kOuterMix ? float(L.sign) * c_s.y : -c_s.y);
+        // element e of the chunk <-> address xb + (e & runmask) + ((e >> lo_bits) << w0);
+        // pairs of elements (2e', 2e'+1) are adjacent in both places and move as one float4
+        const int64_t xb = ((ch & lowmask) << lo_bits) | ((ch >> (w0 - lo_bits)) << (w0 + w));
+        float2 *__restrict__ gp = L.psi + it * block_amps + xb;
+        if (MODE != kOuterGen) {
+            for (int e2 = tid; e2 < (n_el >> 1); e2 += kChunkThreads) {
+                const int e = e2 << 1;
+                sm4[swz(e) >> 1] = *reinterpret_cast<const float4 *>(gp + (e & runmask) + (int64_t(e >> lo_bits) << w0));
+            }
+        }
+        // cut word of the chunk's fixed bits (shell block and address bits outside the chunk)
+        float mult = 1.f;
+        uint64_t cw = 0;
+        const float2 *__restrict__ lut = L.lut + gj * p * L.cmax1;  // first layer's phase table
+        if (MODE != kOuterMix) {
+            cw = shell_block(C, L.shell, uint32_t(y), mult);
+            for (int a = lo_bits; a < nin; ++a)
+                if ((a < w0 || a >= w0 + w) && ((xb >> a) & 1)) cw ^= C->col[qubit_of(a, RB)];
+        }
+        __syncthreads();
+        for (int g0 = 0; g0 < w; g0 += 5) {
+            const int gn = min(5, w - g0);  // this round's qubits: chunk bits lo_bits + g0 ..
+            if (MODE == kOuterGen && g0 == 0)
+                chunk_round_any<true>(gn, sm, n_el, lo_bits, c_s.x, sn, C, cw, lo_bits, RB, w0, lut);
+            else
+                chunk_round_any<false>(gn, sm, n_el, lo_bits + g0, c_s.x, sn, C, cw, lo_bits, RB, w0, lut);
+            __syncthreads();
+        }
+        if (MODE == kOuterFirst) {
+            // lambda is now fully un-mixed: the first layer's phase term and the
+            // outer qubits' mixer terms against exp(-i gamma_1 C)|+>
+            const bool outer_terms = p > 1;
+            const float c0 = 0.5f * float(C->m);  // Im<lambda|psi> = 0: C - c0 in place of C
+            const int gn = min(5, w);
+            const int nreg = 1 << gn;
+            float dg = 0.f, db = 0.f;
+            for (int slot = tid; slot < (n_el >> gn); slot += kChunkThreads) {
+                const int sb = spread_slot(slot, lo_bits, gn);
+                float2 x[32];
+#pragma unroll
+                for (int i = 0; i < 32; ++i) x[i] = i < nreg ? sm[swz(sb | (i << lo_bits))] : make_float2(0.f, 0.f);
+                uint64_t base = cw;
+                for (int b = 0; b < lo_bits; ++b)
+                    if ((sb >> b) & 1) base ^= C->col[qubit_of(b, RB)];
+                for (int b = lo_bits + gn; b < kChunkBits; ++b)
+                    if ((sb >> b) & 1) base ^= C->col[w0 + b - lo_bits];
+                uint64_t lo[4], hi[8];
+                slot_words<5>(C, base, w0, lo, hi);  // w > 5 here: five window qubits in registers
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const int c = __popcll(lo[i & 3] ^ hi[i >> 2]);
+                    const float2 ph = __ldg(lut + c);
+                    dg = fmaf(float(c) - c0, imconj(x[i], ph), dg);
+                    if (outer_terms) {
+#pragma unroll
+                        for (int rb = 0; rb < 5; ++rb) db += imconj(x[i ^ (1 << rb)], ph);
+                    }
+                }
+                if (outer_terms) {
+                    // the other outer qubits: the rest of the window, then beyond it
+                    for (int q = w0 + 5; q < L.x1; ++q) {
+                        const uint64_t cq = C->col[q];
+#pragma unroll
+                        for (int i = 0; i < 32; ++i)
+                            db += imconj(x[i], __ldg(lut + __popcll(lo[i & 3] ^ hi[i >> 2] ^ cq)));
+                    }
+                }
+            }
+            const float wgt2 = 2.f * float(C->weight) * mult * __int_as_float((127 - C->n) << 23);
+            add_gp(wgt2 * dg, L.grad, gj * 2 * p);
+            if (outer_terms) add_gp(wgt2 * db, L.grad, gj * 2 * p + p);
+        } else {
+            for (int e2 = tid; e2 < (n_el >> 1); e2 += kChunkThreads) {
+                const int e = e2 << 1;
+                *reinterpret_cast<float4 *>(gp + (e & runmask) + (int64_t(e >> lo_bits) << w0)) = sm4[swz(e) >> 1];
+            }
+        }
+        __syncthreads();  // the next task reuses the shared chunk
+    }
+}
+
 }  // namespace
 
 int occupancy_grid(const void *fn, int block, size_t smem);
@@ -410,34 +604,76 @@ bool split_ok(int n_in, int p, const int32_t *k, bool grad) {
     return true;
 }
 
+// Chunk kernels need more than the default 48 KB of dynamic shared memory:
+// raised once per kernel and device.
+static cudaError_t allow_chunk_smem(const void *fn, int mode) {
+    static std::mutex mu;
+    static std::set<std::pair<int, int>> done;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.count({dev, mode})) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(sizeof(float2) << kChunkBits));
+    if (e == cudaSuccess) done.insert({dev, mode});
+    return e;
+}
+
 cudaError_t launch_split_wave(BigLaunch B, bool grad, int64_t &launches, cudaStream_t s) {
     const int RB = grad ? kSplitRbGrad : kSplitRbEnergy, T = RB + 5;
     const int nin = B.n_in;
     B.rb = RB;
-    std::vector<std::pair<int, int>> win;  // outer qubit windows, five qubits each
-    for (int w0 = T; w0 < nin; w0 += 5) win.emplace_back(w0, std::min(w0 + 5, nin));
+    // Outer qubit windows: shared-memory chunks of up to kChunkMaxW qubits
+    // while more than five remain, then one register window of at most five.
+    struct Win {
+        int w0, w1;
+        bool chunk;
+    };
+    std::vector<Win> win;
+    for (int w0 = T; w0 < nin;) {
+        const int left = nin - w0;
+        const int n = left > 5 ? std::min(left, kChunkMaxW) : left;
+        win.push_back({w0, w0 + n, left > 5});
+        w0 += n;
+    }
     auto grid_for = [](const void *fn, int64_t tasks) {
         const int64_t need = std::max<int64_t>(1, (tasks + 3) / 4);
         return int(std::min<int64_t>(occupancy_grid(fn, 128, 0), need));
     };
     auto outer = [&](int mode, size_t w, int sign) -> cudaError_t {
         B.mode = mode;
-        B.w0 = win[w].first;
-        B.w1 = win[w].second;
+        B.w0 = win[w].w0;
+        B.w1 = win[w].w1;
         B.b = std::min(B.w0, nin - 5);
-        B.x0 = win[w].second;
+        B.x0 = win[w].w1;
         B.x1 = nin;
         B.sign = sign;
-        const int64_t tasks = B.n_items << (nin - 10);
-        if (mode == kOuterGen) {
-            const void *fn = (const void *)split_outer_kernel<kOuterGen>;
-            split_outer_kernel<kOuterGen><<<grid_for(fn, tasks), 128, 0, s>>>(B);
-        } else if (mode == kOuterMix) {
-            const void *fn = (const void *)split_outer_kernel<kOuterMix>;
-            split_outer_kernel<kOuterMix><<<grid_for(fn, tasks), 128, 0, s>>>(B);
+        if (win[w].chunk) {
+            const size_t smem = size_t(sizeof(float2)) << kChunkBits;
+            const int64_t tasks = B.n_items << (nin - kChunkBits);
+            const void *fn = mode == kOuterGen   ? (const void *)split_chunk_kernel<kOuterGen>
+                             : mode == kOuterMix ? (const void *)split_chunk_kernel<kOuterMix>
+                                                 : (const void *)split_chunk_kernel<kOuterFirst>;
+            if (cudaError_t e = allow_chunk_smem(fn, mode); e != cudaSuccess) return e;
+            const int grid = int(std::min<int64_t>(occupancy_grid(fn, kChunkThreads, smem), std::max<int64_t>(tasks, 1)));
+            if (mode == kOuterGen)
+                split_chunk_kernel<kOuterGen><<<grid, kChunkThreads, smem, s>>>(B);
+            else if (mode == kOuterMix)
+                split_chunk_kernel<kOuterMix><<<grid, kChunkThreads, smem, s>>>(B);
+            else
+                split_chunk_kernel<kOuterFirst><<<grid, kChunkThreads, smem, s>>>(B);
         } else {
-            const void *fn = (const void *)split_outer_kernel<kOuterFirst>;
-            split_outer_kernel<kOuterFirst><<<grid_for(fn, tasks), 128, 0, s>>>(B);
+            const int64_t tasks = B.n_items << (nin - 10);
+            if (mode == kOuterGen) {
+                const void *fn = (const void *)split_outer_kernel<kOuterGen>;
+                split_outer_kernel<kOuterGen><<<grid_for(fn, tasks), 128, 0, s>>>(B);
+            } else if (mode == kOuterMix) {
+                const void *fn = (const void *)split_outer_kernel<kOuterMix>;
+                split_outer_kernel<kOuterMix><<<grid_for(fn, tasks), 128, 0, s>>>(B);
+            } else {
+                const void *fn = (const void *)split_outer_kernel<kOuterFirst>;
+                split_outer_kernel<kOuterFirst><<<grid_for(fn, tasks), 128, 0, s>>>(B);
+            }
         }
         ++launches;
         return cudaGetLastError();

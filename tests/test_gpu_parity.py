@@ -372,6 +372,33 @@ def test_core_tile_schedule_matches_general_schedule(q, graph, p, kw):
     assert a.device_status() == 0 and b.device_status() == 0
 
 
+def test_shared_memory_chunk_windows_match_oracle(q):
+    """K_{8,8} at p = 2: one 16-qubit cone whose inner part is the whole graph
+    (k = (16, 2)), so seven outer qubits (adjoint) and six (energy) run through
+    the shared-memory chunk passes.  Energy, terms and gradient against the
+    FP64 oracle, and against the general schedule."""
+    n, edges = I.complete_bipartite(8, 8)
+    p = 2
+    theta = I.draw_params(p, 3, 31)
+    plan = q.Plan((n, edges), p)
+    reps = plan.reps()
+    assert reps["n_inner"][0] == 16 and list(reps["mix_qubits"][0]) == [16, 2]
+    e, t = plan.energy(_params(theta), terms=True)
+    eg, g = plan.energy_grad(_params(theta))
+    eb, gb = q.Plan((n, edges), p, big_general=True).energy_grad(_params(theta))
+    oid = plan.orbits(0)[0]
+    adj = O.adjacency(n, edges)
+    for j in range(3):
+        eref, gref = O.orbit_grad_adjoint(n, edges, theta[j], p, oid, adj)
+        ref_t = O.lightcone_term(n, edges, edges[reps["edge"][0]], theta[j], p, adj)
+        assert abs(t.cpu().numpy()[0, j] - ref_t) <= TERM_TOL
+        for x in (e, eg, eb):
+            assert abs(x[0, j].item() - eref) <= E_REL_TOL * abs(eref)
+        _check_grad(g[0, j].cpu().numpy(), gref)
+        _check_grad(gb[0, j].cpu().numpy(), gref)
+    assert plan.device_status() == 0
+
+
 # ------------------------------------------ batching: CUDA graphs, tuning
 
 def _mixed_plan(q):
