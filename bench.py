@@ -133,9 +133,13 @@ def hbm_path_measurement(device, flush, stream):
     ms /= max(launches, 1)
     block = 8 * 2 ** 24
     alg = 2 * block * P
-    # core-tile schedule, energy: the 14 outer qubits in windows of 5 -> one
-    # generating pass (write), two mixing passes (read + write), the core pass (read)
-    windows = -(-(24 - 10) // 5)
+    # core-tile schedule, energy: the 14 outer qubits in one shared-memory chunk
+    # window of 10 and one register window of 4 -> a generating pass (write), a
+    # mixing pass (read + write) and the core pass (read)
+    windows, left = 0, 24 - 10
+    while left > 0:
+        left -= min(left, 10) if left > 5 else left
+        windows += 1
     sched = 2 * windows * block * P
     peak, basis = hbm_peak_gbs()
     return {

@@ -21,8 +21,9 @@ def test_noalloc_energy_matches_qaoa_energy_twice(qlib):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     # register-resident cones (the 30-cycle) and large-state cones (C_30(1,2): 11
-    # inner qubits, a random cubic graph on 16 vertices: 13)
-    graphs = [I.cycle(30), I.circulant(30, [1, 2]), I.random_regular(16, 3, 3)]
+    # inner qubits, a random cubic graph on 16 vertices: 13, K_{8,8}: 16, six of
+    # them outer qubits mixed in a shared-memory chunk pass)
+    graphs = [I.cycle(30), I.circulant(30, [1, 2]), I.random_regular(16, 3, 3), I.complete_bipartite(8, 8)]
     p = 3
     plan = qlib.Plan(graphs, p, orbits=False)
     plan.upload()
