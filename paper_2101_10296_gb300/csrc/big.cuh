@@ -80,6 +80,9 @@ int big_grid(bool grad);
 // Core-tile schedule: whether a shape can use it, the scratch it needs per
 // item (one block; the general adjoint needs two), and one wave's launches.
 bool split_ok(int n_in, int p, const int32_t *k, bool grad);
+// Per-device kernel attributes (shared memory of the chunk passes), set at
+// upload so that no attribute call falls inside a stream capture.
+cudaError_t split_prepare();
 cudaError_t launch_split_wave(BigLaunch B, bool grad, int64_t &launches, cudaStream_t s);
 
 }  // namespace qaoa

@@ -619,6 +619,13 @@ static cudaError_t allow_chunk_smem(const void *fn, int mode) {
     return e;
 }
 
+cudaError_t split_prepare() {
+    cudaError_t e = allow_chunk_smem((const void *)split_chunk_kernel<kOuterGen>, kOuterGen);
+    if (e == cudaSuccess) e = allow_chunk_smem((const void *)split_chunk_kernel<kOuterMix>, kOuterMix);
+    if (e == cudaSuccess) e = allow_chunk_smem((const void *)split_chunk_kernel<kOuterFirst>, kOuterFirst);
+    return e;
+}
+
 cudaError_t launch_split_wave(BigLaunch B, bool grad, int64_t &launches, cudaStream_t s) {
     const int RB = grad ? kSplitRbGrad : kSplitRbEnergy, T = RB + 5;
     const int nin = B.n_in;

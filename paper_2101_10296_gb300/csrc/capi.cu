@@ -429,6 +429,7 @@ extern "C" int qaoa_plan_upload(qaoa_plan *plan) {
         else if ((e = cudaMemset(d->status, 0, sizeof(int32_t))) != cudaSuccess)
             rc = cuda_fail(e, "cudaMemset");
     }
+    if (rc == QAOA_OK && !d->big.empty() && (e = split_prepare()) != cudaSuccess) rc = cuda_fail(e, "kernel attributes");
     if (rc == QAOA_OK && (e = cudaDeviceSynchronize()) != cudaSuccess) rc = cuda_fail(e, "upload");
     if (rc != QAOA_OK) qaoa_device_release(plan);
     return rc;

@@ -399,6 +399,34 @@ def test_shared_memory_chunk_windows_match_oracle(q):
     assert plan.device_status() == 0
 
 
+def test_chunk_passes_in_many_waves_and_cuda_graph(q):
+    """K_{8,8} at p = 2 with 16 points: the chunk passes split into waves of
+    two items (1 MiB of scratch) give the results of one wave, and a captured
+    CUDA graph replays them."""
+    n, edges = I.complete_bipartite(8, 8)
+    plan = q.Plan((n, edges), 2, orbits=False)
+    th = _params(I.draw_params(2, 16, 41))
+    e0, g0 = plan.energy_grad(th)
+    _, t0 = plan.energy(th, terms=True)
+    plan.set_tuning(big_scratch_bytes=1 << 20)
+    e1, g1 = plan.energy_grad(th)
+    _, t1 = plan.energy(th, terms=True)
+    assert np.allclose(e1.cpu().numpy(), e0.cpu().numpy(), rtol=E_REL_TOL, atol=0)
+    assert np.max(np.abs(t1.cpu().numpy() - t0.cpu().numpy())) <= TERM_TOL
+    for j in range(16):
+        _check_grad(g1[0, j].cpu().numpy(), g0[0, j].cpu().numpy(), scale=2.0)
+    plan.set_tuning()
+    fresh = q.Plan((n, edges), 2, orbits=False)  # captured before any direct call
+    graph = fresh.graph(th, grad=True)
+    e2, g2 = graph.run(th)
+    torch.cuda.synchronize()
+    assert np.allclose(e2.cpu().numpy(), e0.cpu().numpy(), rtol=E_REL_TOL, atol=0)
+    for j in range(16):
+        _check_grad(g2[0, j].cpu().numpy(), g0[0, j].cpu().numpy(), scale=2.0)
+    graph.close()
+    assert plan.device_status() == 0 and fresh.device_status() == 0
+
+
 # ------------------------------------------ batching: CUDA graphs, tuning
 
 def _mixed_plan(q):
