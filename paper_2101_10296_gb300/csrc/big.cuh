@@ -57,6 +57,8 @@ struct BigLaunch {
     int64_t item0, n_items;   // items (cone, point, shell block) of this wave
     const float2 *lut;        // [G][P][p][cmax1]
     const float2 *cs;         // [G][P][p] (cos beta, sin beta)
+    const float2 *mix;        // [G][P][p] (tau, flip) and
+    const float *kpow;        // [G][P][p][kKpow] kappa^(2k): the register kernels' mixer tables
     float2 *psi, *lam;        // scratch: n_items blocks of 2^n_in
     double *energy, *grad, *terms;
     int32_t *status;

@@ -40,6 +40,88 @@
 namespace qaoa {
 namespace {
 
+// The first layer's mixer in factored form, without bit flips:
+// exp(-i beta X) = kappa D with D = I - i a X (a = tan beta, kappa = cos beta)
+// when |tan beta| <= 1, else D = a I - i X (a = cot beta, kappa = sin beta);
+// its inverse up to the same factor, D' = exp(+i beta X) / kappa, is I + i a X
+// or a I + i X.  Two FMAs per output amplitude in both cases (the exact
+// rotation takes four).  Only the first layer uses it: every state of the
+// schedule then carries one known factor, kappa^(n_in) per amplitude of psi,
+// and every derivative term is taken either before any of the first mixer
+// is undone or after all of it, so (D'D = 1 / kappa^2 per qubit) nothing else
+// changes.
+template <bool B, bool INV>
+__device__ __forceinline__ float2 fmix(float2 me, float2 o, float a) {
+    if (!B) return INV ? make_float2(fmaf(-a, o.y, me.x), fmaf(a, o.x, me.y))
+                       : make_float2(fmaf(a, o.y, me.x), fmaf(-a, o.x, me.y));
+    return INV ? make_float2(fmaf(a, me.x, -o.y), fmaf(a, me.y, o.x))
+               : make_float2(fmaf(a, me.x, o.y), fmaf(a, me.y, -o.x));
+}
+
+// D (or D') on register bits [r0, r1).
+template <int NR, bool B, bool INV>
+__device__ __forceinline__ void fmix_regs(float2 (&x)[NR], int r0, int r1, float a) {
+#pragma unroll
+    for (int rb = 0; (1 << rb) < NR; ++rb) {
+        if (rb >= r0 && rb < r1) {
+#pragma unroll
+            for (int i = 0; i < NR; ++i) {
+                if (i & (1 << rb)) continue;
+                const int i2 = i | (1 << rb);
+                const float2 u = x[i], v = x[i2];
+                x[i] = fmix<B, INV>(u, v, a);
+                x[i2] = fmix<B, INV>(v, u, a);
+            }
+        }
+    }
+}
+
+// D (or D') on lane bits [0, nb).
+template <int NR, bool B, bool INV>
+__device__ __forceinline__ void fmix_lanes(float2 (&x)[NR], int nb, float a) {
+    for (int lb = 0; lb < nb; ++lb) {
+        const int m = 1 << lb;
+#pragma unroll
+        for (int i = 0; i < NR; ++i) {
+            float2 o;
+            o.x = __shfl_xor_sync(kFull, x[i].x, m);
+            o.y = __shfl_xor_sync(kFull, x[i].y, m);
+            x[i] = fmix<B, INV>(x[i], o, a);
+        }
+    }
+}
+
+template <int NR, bool INV>
+__device__ __forceinline__ void first_mix_regs(float2 (&x)[NR], int r0, int r1, float a, bool b) {
+    if (b)
+        fmix_regs<NR, true, INV>(x, r0, r1, a);
+    else
+        fmix_regs<NR, false, INV>(x, r0, r1, a);
+}
+
+template <int NR, bool INV>
+__device__ __forceinline__ void first_mix_lanes(float2 (&x)[NR], int nb, float a, bool b) {
+    if (b)
+        fmix_lanes<NR, true, INV>(x, nb, a);
+    else
+        fmix_lanes<NR, false, INV>(x, nb, a);
+}
+
+// The first layer's a, form (b: the a I - i X form) and kappa^(2 n_in) of one
+// (graph, point), from the register kernels' mixer tables.
+struct FirstMix {
+    float a, k2n;
+    bool b;
+};
+__device__ __forceinline__ FirstMix first_mix(const BigLaunch &L, int64_t gj, int n_in) {
+    const float2 m = __ldg(L.mix + gj * L.p);  // (tau, flip) of the factored form with bit flips
+    FirstMix f;
+    f.b = m.y != 0.f;
+    f.a = f.b ? -m.x : m.x;  // flip form: tau = -cot beta
+    f.k2n = __ldg(L.kpow + gj * L.p * kKpow + n_in);
+    return f;
+}
+
 // exp(-i beta X) on register qubits [0, nbits) (nbits <= log2 NR).
 template <int NR>
 __device__ __forceinline__ void mix_regs(float2 (&x)[NR], int nbits, float c, float s) {
@@ -48,23 +130,6 @@ __device__ __forceinline__ void mix_regs(float2 (&x)[NR], int nbits, float c, fl
         if (rb < nbits) {
 #pragma unroll
             for (int i = 0; i < NR; ++i) {
-                if (i & (1 << rb)) continue;
-                const int i2 = i | (1 << rb);
-                const float2 a = x[i], bb = x[i2];
-                x[i] = rot(a, bb, c, s);
-                x[i2] = rot(bb, a, c, s);
-            }
-        }
-    }
-}
-
-// exp(-i beta X) on register bits [r0, r1) of a 32-register window.
-__device__ __forceinline__ void mix_window(float2 (&x)[32], int r0, int r1, float c, float s) {
-#pragma unroll
-    for (int rb = 0; rb < 5; ++rb) {
-        if (rb >= r0 && rb < r1) {
-#pragma unroll
-            for (int i = 0; i < 32; ++i) {
                 if (i & (1 << rb)) continue;
                 const int i2 = i | (1 << rb);
                 const float2 a = x[i], bb = x[i2];
@@ -229,12 +294,12 @@ __global__ void __launch_bounds__(128, GRAD ? QAOA_SPLIT_GRAD_BLOCKS : 3) split_
 #pragma unroll
             for (int i = 0; i < NR; ++i) x[i] = __ldg(lut + cut(i));
         }
-        const float sig = __int_as_float((127 - C->n) << 23);  // 2^-n
-        {  // first mixer on the core qubits
-            const float2 c_s = __ldg(cs);
-            mix_regs<NR>(x, RB, c_s.x, c_s.y);
-            mix_lanes<NR>(x, 5, c_s.x, c_s.y);
-        }
+        const FirstMix f1 = first_mix(L, gj, nin);
+        // |psi|^2 = 2^-n kappa_1^(2 n_in) |x|^2 (the first mixer's factored form)
+        const float sig = __int_as_float((127 - C->n) << 23) * f1.k2n;
+        // first mixer on the core qubits
+        first_mix_regs<NR, false>(x, 0, RB, f1.a, f1.b);
+        first_mix_lanes<NR, false>(x, 5, f1.a, f1.b);
         for (int l = 1; l < p; ++l) {
             const float2 *__restrict__ lt = lut + l * L.cmax1;
 #pragma unroll
@@ -287,13 +352,12 @@ __global__ void __launch_bounds__(128, GRAD ? QAOA_SPLIT_GRAD_BLOCKS : 3) split_
                 add_gp(wgt2 * dg, L.grad, gj * 2 * p + l);
             }
             // first mixer: the core qubits' terms, then lambda alone un-mixed
-            const float2 c_s = __ldg(cs);
             // At p = 1 the first layer is the last: lambda = O psi with
             // O = -1/2 Z_0 Z_1, and <psi|O X_q|psi> is real for every q other
             // than 0 and 1 (X_q and O commute), so only those two contribute.
             add_gp(wgt2 * xterms<NR>(x, r, p > 1), L.grad, gj * 2 * p + p);
-            mix_regs<NR>(r, RB, c_s.x, -c_s.y);
-            mix_lanes<NR>(r, 5, c_s.x, -c_s.y);
+            first_mix_regs<NR, true>(r, 0, RB, f1.a, f1.b);
+            first_mix_lanes<NR, true>(r, 5, f1.a, f1.b);
 #pragma unroll
             for (int i = 0; i < NR; ++i) sp[i << 5] = r[i];
         }
@@ -327,7 +391,7 @@ __global__ void __launch_bounds__(128, MODE == kOuterGen ? 4 : 3) split_outer_ke
             continue;
         }
         const int64_t gj = int64_t(C->graph) * L.P + j;
-        const float2 c_s = __ldg(L.cs + gj * p);
+        const FirstMix f1 = first_mix(L, gj, nin);
         // address of (lane, register i) = xb | (i << b) | lane
         const int64_t xb = ((tile & lowmask) << 5) | ((tile >> (b - 5)) << (b + 5));
         float2 *__restrict__ sp = L.psi + it * block_amps + xb + lane;
@@ -337,7 +401,10 @@ __global__ void __launch_bounds__(128, MODE == kOuterGen ? 4 : 3) split_outer_ke
             for (int i = 0; i < 32; ++i) x[i] = sp[int64_t(i) << b];
         }
         if (MODE == kOuterMix) {
-            mix_window(x, r0, r1, c_s.x, float(L.sign) * c_s.y);
+            if (L.sign > 0)
+                first_mix_regs<32, false>(x, r0, r1, f1.a, f1.b);
+            else
+                first_mix_regs<32, true>(x, r0, r1, f1.a, f1.b);
         } else {
             const float2 *__restrict__ lut = L.lut + gj * p * L.cmax1;  // first layer's phase table
             float mult = 1.f;
@@ -363,9 +430,9 @@ __global__ void __launch_bounds__(128, MODE == kOuterGen ? 4 : 3) split_outer_ke
             if (MODE == kOuterGen) {
 #pragma unroll
                 for (int i = 0; i < 32; ++i) x[i] = __ldg(lut + __popcll(lo[i & 3] ^ hi[i >> 2]));
-                mix_window(x, r0, r1, c_s.x, c_s.y);
+                first_mix_regs<32, false>(x, r0, r1, f1.a, f1.b);
             } else {  // kOuterFirst: x holds lambda
-                mix_window(x, r0, r1, c_s.x, -c_s.y);
+                first_mix_regs<32, true>(x, r0, r1, f1.a, f1.b);
                 // the outer qubits' mixer terms vanish at p = 1, where the first
                 // layer is the last (only qubits 0 and 1 contribute there)
                 const bool outer_terms = p > 1;
@@ -388,7 +455,8 @@ __global__ void __launch_bounds__(128, MODE == kOuterGen ? 4 : 3) split_outer_ke
                     for (int i = 0; i < 32; ++i)
                         db += imconj(x[i], __ldg(lut + __popcll(lo[i & 3] ^ hi[i >> 2] ^ cq)));
                 }
-                const float wgt2 = 2.f * float(C->weight) * mult * __int_as_float((127 - C->n) << 23);
+                // lambda = 2^(-n/2) kappa_1^(2 n_in) x once the first mixer is undone
+                const float wgt2 = 2.f * float(C->weight) * mult * __int_as_float((127 - C->n) << 23) * f1.k2n;
                 add_gp(wgt2 * dg, L.grad, gj * 2 * p);
                 if (outer_terms) add_gp(wgt2 * db, L.grad, gj * 2 * p + p);
             }
@@ -442,7 +510,7 @@ __device__ __forceinline__ void slot_words(const DevCone *__restrict__ C, uint64
 // differ in chunk bits [pos, pos+G), applies the mixer to those G qubits and
 // writes them back.  GEN in its first round generates the amplitudes instead.
 template <int G, bool GEN>
-__device__ __forceinline__ void chunk_round(float2 *__restrict__ sm, int n_el, int pos, float c, float sn,
+__device__ __forceinline__ void chunk_round(float2 *__restrict__ sm, int n_el, int pos, FirstMix f, bool inv,
                                             const DevCone *__restrict__ C, uint64_t cw, int lo_bits, int RB, int w0,
                                             const float2 *__restrict__ lut) {
     constexpr int NR = 1 << G;
@@ -463,22 +531,25 @@ __device__ __forceinline__ void chunk_round(float2 *__restrict__ sm, int n_el, i
 #pragma unroll
             for (int i = 0; i < NR; ++i) x[i] = sm[swz(sb | (i << pos))];
         }
-        mix_regs<NR>(x, G, c, sn);
+        if (inv)
+            first_mix_regs<NR, true>(x, 0, G, f.a, f.b);
+        else
+            first_mix_regs<NR, false>(x, 0, G, f.a, f.b);
 #pragma unroll
         for (int i = 0; i < NR; ++i) sm[swz(sb | (i << pos))] = x[i];
     }
 }
 
 template <bool GEN>
-__device__ __forceinline__ void chunk_round_any(int G, float2 *sm, int n_el, int pos, float c, float sn,
+__device__ __forceinline__ void chunk_round_any(int G, float2 *sm, int n_el, int pos, FirstMix f, bool inv,
                                                 const DevCone *C, uint64_t cw, int lo_bits, int RB, int w0,
                                                 const float2 *lut) {
     switch (G) {
-        case 1: chunk_round<1, GEN>(sm, n_el, pos, c, sn, C, cw, lo_bits, RB, w0, lut); break;
-        case 2: chunk_round<2, GEN>(sm, n_el, pos, c, sn, C, cw, lo_bits, RB, w0, lut); break;
-        case 3: chunk_round<3, GEN>(sm, n_el, pos, c, sn, C, cw, lo_bits, RB, w0, lut); break;
-        case 4: chunk_round<4, GEN>(sm, n_el, pos, c, sn, C, cw, lo_bits, RB, w0, lut); break;
-        default: chunk_round<5, GEN>(sm, n_el, pos, c, sn, C, cw, lo_bits, RB, w0, lut); break;
+        case 1: chunk_round<1, GEN>(sm, n_el, pos, f, inv, C, cw, lo_bits, RB, w0, lut); break;
+        case 2: chunk_round<2, GEN>(sm, n_el, pos, f, inv, C, cw, lo_bits, RB, w0, lut); break;
+        case 3: chunk_round<3, GEN>(sm, n_el, pos, f, inv, C, cw, lo_bits, RB, w0, lut); break;
+        case 4: chunk_round<4, GEN>(sm, n_el, pos, f, inv, C, cw, lo_bits, RB, w0, lut); break;
+        default: chunk_round<5, GEN>(sm, n_el, pos, f, inv, C, cw, lo_bits, RB, w0, lut); break;
     }
 }
 
@@ -508,8 +579,8 @@ __global__ void __launch_bounds__(kChunkThreads, 2) split_chunk_kernel(const __g
             continue;
         }
         const int64_t gj = int64_t(C->graph) * L.P + j;
-        const float2 c_s = __ldg(L.cs + gj * p);
-        const float sn = MODE == kOuterGen ? c_s.y : (MODE == kOuterMix ? float(L.sign) * c_s.y : -c_s.y);
+        const FirstMix f1 = first_mix(L, gj, nin);
+        const bool inv = MODE == kOuterFirst || (MODE == kOuterMix && L.sign < 0);
         // element e of the chunk <-> address xb + (e & runmask) + ((e >> lo_bits) << w0);
         // pairs of elements (2e', 2e'+1) are adjacent in both places and move as one float4
         const int64_t xb = ((ch & lowmask) << lo_bits) | ((ch >> (w0 - lo_bits)) << (w0 + w));
@@ -533,9 +604,9 @@ __global__ void __launch_bounds__(kChunkThreads, 2) split_chunk_kernel(const __g
         for (int g0 = 0; g0 < w; g0 += 5) {
             const int gn = min(5, w - g0);  // this round's qubits: chunk bits lo_bits + g0 ..
             if (MODE == kOuterGen && g0 == 0)
-                chunk_round_any<true>(gn, sm, n_el, lo_bits, c_s.x, sn, C, cw, lo_bits, RB, w0, lut);
+                chunk_round_any<true>(gn, sm, n_el, lo_bits, f1, false, C, cw, lo_bits, RB, w0, lut);
             else
-                chunk_round_any<false>(gn, sm, n_el, lo_bits + g0, c_s.x, sn, C, cw, lo_bits, RB, w0, lut);
+                chunk_round_any<false>(gn, sm, n_el, lo_bits + g0, f1, inv, C, cw, lo_bits, RB, w0, lut);
             __syncthreads();
         }
         if (MODE == kOuterFirst) {
@@ -578,7 +649,8 @@ __global__ void __launch_bounds__(kChunkThreads, 2) split_chunk_kernel(const __g
                     }
                 }
             }
-            const float wgt2 = 2.f * float(C->weight) * mult * __int_as_float((127 - C->n) << 23);
+            // lambda = 2^(-n/2) kappa_1^(2 n_in) x once the first mixer is undone
+            const float wgt2 = 2.f * float(C->weight) * mult * __int_as_float((127 - C->n) << 23) * f1.k2n;
             add_gp(wgt2 * dg, L.grad, gj * 2 * p);
             if (outer_terms) add_gp(wgt2 * db, L.grad, gj * 2 * p + p);
         } else {

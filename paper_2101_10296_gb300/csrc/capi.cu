@@ -116,7 +116,8 @@ int64_t tuned_grid(const qaoa_device_plan *d, int occupancy_grid) {
 // Large-state cones: per shape, waves of blocks that fit the scratch budget,
 // each wave streamed through the shape's pass list.
 cudaError_t run_big(const qaoa_device_plan *d, const qaoa_plan *plan, int64_t P, const double *params,
-                    const float2 *lut, double *energy, double *grad, double *terms, cudaStream_t s) {
+                    const float2 *lut, const float2 *mix, const float *kpow, double *energy, double *grad,
+                    double *terms, cudaStream_t s) {
     qaoa_device_plan *dm = const_cast<qaoa_device_plan *>(d);
     const int p = plan->p;
     float2 *cs = nullptr;
@@ -147,6 +148,8 @@ cudaError_t run_big(const qaoa_device_plan *d, const qaoa_plan *plan, int64_t P,
         B.cmax1 = d->cmax1;
         B.lut = lut;
         B.cs = cs;
+        B.mix = mix;
+        B.kpow = kpow;
         B.psi = scratch;
         B.lam = g && !split ? scratch + size_t(wave) * (size_t(1) << bs.n_in) : nullptr;
         B.shell = d->shell;
@@ -263,7 +266,7 @@ int run(const qaoa_plan *plan, int64_t n_points, const double *params, double *e
             }
         }
         if (L.work.warps > 0) dm->all_launches += 1;
-        if (e == cudaSuccess && !d->big.empty()) e = run_big(d, plan, n_points, params, lut, energy, grad, terms, s);
+        if (e == cudaSuccess && !d->big.empty()) e = run_big(d, plan, n_points, params, lut, mix, kpow, energy, grad, terms, s);
     }
     if (ev0) {
         cudaEventRecord(ev1, s);

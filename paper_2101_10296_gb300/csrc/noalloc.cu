@@ -168,6 +168,8 @@ extern "C" int qaoa_energy_noalloc(const qaoa_plan *plan, int64_t n_points, cons
             B.cmax1 = d->cmax1;
             B.lut = lut;
             B.cs = cs;
+            B.mix = mix;
+            B.kpow = kpow;
             B.psi = reinterpret_cast<float2 *>(blocks);
             B.shell = d->shell;
             B.lam = nullptr;
