@@ -392,6 +392,15 @@ def run_ours(args, rank, world, local_rank):
     plain = qaoa.Plan(graphs, p, orbits=False)
     plain.upload()
     plain_ms = timed(lambda: plain.energy_grad(params))
+    # local-symmetry reduction: one cone per isomorphism class of cones
+    t_cc = time.perf_counter()
+    ccplan = qaoa.Plan(graphs, p, cone_classes=True)
+    t_cc = time.perf_counter() - t_cc
+    ccplan.upload()
+    cc_ms = timed(lambda: ccplan.energy_grad(params))
+    cc_e, _ = ccplan.energy_grad(params)
+    ref_e, _ = plan.energy_grad(params)
+    cc_err = float((cc_e - ref_e).abs().max() / ref_e.abs().max())
 
     # roofline of the dominant kernel (the adjoint cone kernel)
     flops = algorithmic_flops(reps, p, grad=True) * P
@@ -445,6 +454,9 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clocks,
         "energy_only_evals_per_s": world * evals / (energy_ms / 1e3),
         "plain_all_edge_evals_per_s": world * evals / (plain_ms / 1e3),
+        "cone_classes": {"n_classes": int(ccplan.info()["n_reps"]), "plan_s": t_cc,
+                         "energy_grad_evals_per_s": world * evals / (cc_ms / 1e3),
+                         "max_rel_energy_diff_vs_orbit_path": cc_err},
         "amp_updates_per_s": world * amp_updates / (ms_per_step / 1e3),
         "evolved_amp_updates_per_s": world * evolved / (ms_per_step / 1e3),
         "plan_s": t_plan,
@@ -572,6 +584,10 @@ def run_suite(args):
         ms_g = timed(lambda: plan.energy_grad(params))
         ms_e = timed(lambda: plan.energy(params))
         ms_pg = timed(lambda: plain.energy_grad(params))
+        ccplan = qaoa.Plan(graphs, p, cone_classes=True)
+        ccplan.upload()
+        ms_cc = timed(lambda: ccplan.energy_grad(params))
+        e_cc = ccplan.energy(params).cpu().numpy()
         e_gpu, terms = plan.energy(params, terms=True)
         e_gpu = e_gpu.cpu().numpy()
         terms = terms.cpu().numpy()
@@ -611,6 +627,9 @@ def run_suite(args):
             "large_state_cones": int(info["n_big"]), "plan_s": t_plan, "t_orbits_s": info["t_orbits_s"],
             "energy_grad_evals_per_s": evals / (ms_g / 1e3), "energy_evals_per_s": evals / (ms_e / 1e3),
             "plain_energy_grad_evals_per_s": evals / (ms_pg / 1e3),
+            "cone_class_reps": int(ccplan.info()["n_reps"]),
+            "cone_class_energy_grad_evals_per_s": evals / (ms_cc / 1e3),
+            "cone_class_max_rel_energy_diff": float(np.max(np.abs(e_cc - e_gpu) / np.abs(e_gpu))),
             "amp_updates_per_s": amps / (ms_g / 1e3), "fp32_tflops_alg": flops / (ms_g / 1e3) / 1e12,
             "max_term_err_vs_fp64": dterm, "max_rel_energy_err_vs_closed_form": drel,
             "cpu_oracle_evals_per_s": (1.0 / cpu_eval_s) if cpu_eval_s == cpu_eval_s and cpu_eval_s > 0 else None,

@@ -59,9 +59,17 @@ enum qaoa_flags {
     QAOA_SHELL_PLAIN = 4u, /* evolve every assignment of the never-mixed shell
                               qubits as its own block instead of one block per
                               shell class count vector; slower, for cross-checks */
-    QAOA_BIG_GENERAL = 8u  /* large-state cones always use the general pass
+    QAOA_BIG_GENERAL = 8u, /* large-state cones always use the general pass
                               schedule (psi and lambda both stored), never the
                               core-tile schedule; slower, for cross-checks */
+    QAOA_CONE_CLASSES = 16u /* simulate one cone per isomorphism class of the
+                               graph's cones (root edge fixed setwise), weighted
+                               by the class's total orbit size: edges with
+                               isomorphic cones have equal terms (the argument
+                               of Sec. 3 applied to cone isomorphisms, the
+                               local symmetries of Sec. 6); a coarser partition
+                               than the Aut(G) orbits, found by a verified
+                               search (qaoa_plan_cone_classes) */
 };
 
 /* Largest cone handled: qubits per cone and local edges per cone. */
@@ -144,6 +152,16 @@ int qaoa_plan_info(const qaoa_plan *plan, qaoa_plan_info_t *info);
  */
 int qaoa_plan_orbits(const qaoa_plan *plan, int32_t graph, int32_t *orbit_id,
                      int64_t *n_orbits, double *log10_aut, int32_t *complete);
+
+/* Cone classes of graph `graph` (0-based): class_id[e] (host, n_edges of the
+ * graph, may be NULL) = the smallest edge index of edge e's class, and
+ * *n_classes (may be NULL) = the number of classes = the graph's rows in the
+ * plan.  Without QAOA_CONE_CLASSES the classes are the orbits.  Every class
+ * only joins edges whose cones were proven isomorphic (search with the
+ * root edge fixed setwise, leaves checked edge by edge), so all its edges
+ * have the same term.  Host only.  Returns QAOA_E_INVALID on a bad plan or
+ * graph index. */
+int qaoa_plan_cone_classes(const qaoa_plan *plan, int32_t graph, int32_t *class_id, int64_t *n_classes);
 
 /*
  * Representatives, in plan order (the row order of terms_dev).  Each array

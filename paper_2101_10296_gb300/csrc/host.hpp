@@ -61,6 +61,12 @@ struct Cone {
 int extract_cone(const Graph &g, int64_t e, int32_t p, bool full_cone, bool shell_plain, int32_t max_qubits,
                  std::vector<int32_t> &dist_scratch, Cone &c, std::string &err);
 
+// Cone classes (cone_classes.cpp): whether two cones are isomorphic with the
+// root edge fixed setwise (then their terms are equal), and the classes of a
+// list of cones: class_of[i] = index of the first cone of i's class.
+bool cones_isomorphic(const Cone &a, const Cone &b, int p);
+void cone_classes(const std::vector<const Cone *> &cones, int p, std::vector<int32_t> &class_of);
+
 void set_error(const std::string &msg);
 
 // Injected failures (qaoa_inject_fault): true if one of `kind` is pending,
@@ -79,6 +85,10 @@ struct qaoa_plan {
     std::vector<int64_t> n_edges;
     std::vector<qaoa::OrbitResult> orbits;
     std::vector<qaoa::Cone> cones;  // plan order (rows of terms)
+    // per graph and edge: the smallest edge of its cone class (QAOA_CONE_CLASSES),
+    // else of its orbit; and the number of classes
+    std::vector<std::vector<int32_t>> cone_class;
+    std::vector<int64_t> n_classes;
     double t_orbits = 0.0, t_cones = 0.0;
     qaoa_device_plan *dev = nullptr;
 };

@@ -7,6 +7,8 @@
 #include <cstring>
 #include <new>
 #include <thread>
+#include <unordered_map>
+#include <vector>
 
 #include "host.hpp"
 
@@ -198,7 +200,7 @@ extern "C" int qaoa_plan_graphs(int32_t n_graphs, const int32_t *n_vertices, con
         set_error("p must be in [1, QAOA_MAX_P]");
         return QAOA_E_INVALID;
     }
-    if (flags & ~uint32_t(QAOA_ORBITS | QAOA_FULL_CONE | QAOA_SHELL_PLAIN | QAOA_BIG_GENERAL)) {
+    if (flags & ~uint32_t(QAOA_ORBITS | QAOA_FULL_CONE | QAOA_SHELL_PLAIN | QAOA_BIG_GENERAL | QAOA_CONE_CLASSES)) {
         set_error("unknown flag bits");
         return QAOA_E_INVALID;
     }
@@ -292,6 +294,48 @@ extern "C" int qaoa_plan_graphs(int32_t n_graphs, const int32_t *n_vertices, con
                 return rc;
             }
         }
+        // cone classes: per graph, one cone per isomorphism class of its cones,
+        // weighted by the class's total orbit size
+        pl->cone_class.resize(n_graphs);
+        pl->n_classes.assign(n_graphs, 0);
+        std::vector<int64_t> first(n_graphs + 1, 0);  // graph g's cones: [first[g], first[g+1])
+        for (const Cone &c : pl->cones) first[c.graph + 1]++;
+        for (int32_t g = 0; g < n_graphs; ++g) first[g + 1] += first[g];
+        std::vector<std::vector<int32_t>> class_of(n_graphs);
+        if (flags & QAOA_CONE_CLASSES) {
+            parallel_for(n_graphs, [&](int64_t g, int) {
+                std::vector<const Cone *> list;
+                for (int64_t i = first[g]; i < first[g + 1]; ++i) list.push_back(&pl->cones[i]);
+                cone_classes(list, p, class_of[g]);
+            });
+        }
+        std::vector<Cone> kept;
+        std::vector<int64_t> rep_edge_of_cone(pl->cones.size());
+        for (int32_t g = 0; g < n_graphs; ++g) {
+            for (int64_t i = first[g]; i < first[g + 1]; ++i) {
+                const int64_t r = (flags & QAOA_CONE_CLASSES) ? first[g] + class_of[g][i - first[g]] : i;
+                rep_edge_of_cone[i] = pl->cones[r].edge;
+            }
+            std::unordered_map<int64_t, size_t> slot;  // class representative's edge -> kept index
+            for (int64_t i = first[g]; i < first[g + 1]; ++i) {
+                auto it = slot.find(rep_edge_of_cone[i]);
+                if (it == slot.end()) {
+                    slot.emplace(rep_edge_of_cone[i], kept.size());
+                    kept.push_back(pl->cones[i]);
+                } else {
+                    kept[it->second].weight += pl->cones[i].weight;
+                }
+            }
+            pl->n_classes[g] = int64_t(slot.size());
+            // edge -> its orbit's representative cone -> that cone's class representative
+            std::unordered_map<int64_t, int64_t> cone_of_edge;
+            for (int64_t i = first[g]; i < first[g + 1]; ++i) cone_of_edge[pl->cones[i].edge] = i;
+            const auto &oid = pl->orbits[g].orbit_id;
+            pl->cone_class[g].resize(oid.size());
+            for (size_t e = 0; e < oid.size(); ++e)
+                pl->cone_class[g][e] = int32_t(rep_edge_of_cone[cone_of_edge[oid[e]]]);
+        }
+        pl->cones.swap(kept);
         auto t2 = std::chrono::steady_clock::now();
         pl->t_orbits = std::chrono::duration<double>(t1 - t0).count();
         pl->t_cones = std::chrono::duration<double>(t2 - t1).count();
@@ -318,6 +362,17 @@ extern "C" void qaoa_plan_free(qaoa_plan *plan) {
     if (!plan) return;
     qaoa_device_release(plan);
     delete plan;
+}
+
+extern "C" int qaoa_plan_cone_classes(const qaoa_plan *plan, int32_t graph, int32_t *class_id, int64_t *n_classes) {
+    if (!plan || graph < 0 || graph >= plan->n_graphs) {
+        set_error("bad plan or graph index");
+        return QAOA_E_INVALID;
+    }
+    const auto &cc = plan->cone_class[graph];
+    if (class_id) std::copy(cc.begin(), cc.end(), class_id);
+    if (n_classes) *n_classes = plan->n_classes[graph];
+    return QAOA_OK;
 }
 
 extern "C" int qaoa_plan_orbits(const qaoa_plan *plan, int32_t graph, int32_t *orbit_id, int64_t *n_orbits,

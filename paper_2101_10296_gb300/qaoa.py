@@ -27,6 +27,7 @@ ORBITS = 1
 FULL_CONE = 2
 SHELL_PLAIN = 4
 BIG_GENERAL = 8
+CONE_CLASSES = 16
 
 
 class QAOAError(RuntimeError):
@@ -63,6 +64,7 @@ _SIGS = {
     "qaoa_plan_free": (None, [_P]),
     "qaoa_plan_info": (C.c_int, [_P, C.POINTER(PlanInfo)]),
     "qaoa_plan_orbits": (C.c_int, [_P, C.c_int32, _I32P, _I64P, _F64P, _I32P]),
+    "qaoa_plan_cone_classes": (C.c_int, [_P, C.c_int32, _I32P, _I64P]),
     "qaoa_plan_reps": (C.c_int, [_P, _I32P, _I64P, _I32P, _I32P, _I32P, _I32P, _I32P]),
     "qaoa_plan_cone": (C.c_int, [_P, C.c_int64, _I32P, _I32P, _I32P]),
     "qaoa_plan_shell": (C.c_int, [_P, C.c_int64, _I32P, _I64P]),
@@ -145,7 +147,7 @@ class Plan:
     """A planned batch of graphs (orbits + cones), owning its device copy."""
 
     def __init__(self, graphs, p, orbits=True, full_cone=False, max_cone_qubits=0, search_budget=0,
-                 shell_plain=False, big_general=False):
+                 shell_plain=False, big_general=False, cone_classes=False):
         if isinstance(graphs, tuple):
             graphs = [graphs]
         nv = _i32([g[0] for g in graphs])
@@ -158,7 +160,7 @@ class Plan:
         edges = _i32(np.concatenate(rows) if rows else np.zeros((0, 2)))
         offs = np.asarray(offs, dtype=np.int64)
         flags = (ORBITS if orbits else ORBITS_OFF) | (FULL_CONE if full_cone else 0) | (SHELL_PLAIN if shell_plain else 0)
-        flags |= BIG_GENERAL if big_general else 0
+        flags |= (BIG_GENERAL if big_general else 0) | (CONE_CLASSES if cone_classes else 0)
         h = C.c_void_p()
         _check(lib().qaoa_plan_graphs(len(graphs), _ptr(nv, C.c_int32), _ptr(offs, C.c_int64),
                                       _ptr(edges, C.c_int32) if edges.size else None, p, flags,
@@ -192,6 +194,13 @@ class Plan:
         _check(lib().qaoa_plan_orbits(self._h, graph, _ptr(oid, C.c_int32), C.byref(norb), C.byref(l10),
                                       C.byref(comp)))
         return oid, norb.value, l10.value, bool(comp.value)
+
+    def cone_classes(self, graph=0):
+        """(class id per edge = smallest edge of its cone class, number of classes)."""
+        cid = np.zeros(self.n_edges[graph], dtype=np.int32)
+        ncls = C.c_int64()
+        _check(lib().qaoa_plan_cone_classes(self._h, graph, _ptr(cid, C.c_int32), C.byref(ncls)))
+        return cid, ncls.value
 
     def reps(self):
         r = self.info()["n_reps"]

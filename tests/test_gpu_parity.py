@@ -427,6 +427,50 @@ def test_chunk_passes_in_many_waves_and_cuda_graph(q):
     assert plan.device_status() == 0 and fresh.device_status() == 0
 
 
+@pytest.mark.parametrize("graphs,p", [([I.random_regular(200, 3, s) for s in (1, 2)], 2),
+                                      ([I.erdos_renyi(150, 4 / 149, 3), I.circulant(40, [1, 3])], 1),
+                                      ([I.random_regular(24, 3, s) for s in (1, 2)], 3)])
+def test_cone_classes_match_orbit_reduction(q, graphs, p):
+    """One cone per isomorphism class of cones gives the energies, gradients and
+    class representatives' terms of the orbit-reduced plan."""
+    P = 5
+    th = _params(np.stack([I.draw_params(p, P, 50 + k) for k in range(len(graphs))]))
+    a = q.Plan(graphs, p)
+    b = q.Plan(graphs, p, cone_classes=True)
+    assert b.info()["n_reps"] < a.info()["n_reps"]
+    ea, ga = a.energy_grad(th)
+    eb, gb = b.energy_grad(th)
+    assert np.allclose(eb.cpu().numpy(), ea.cpu().numpy(), rtol=E_REL_TOL, atol=0)
+    for k in range(len(graphs)):
+        for j in range(P):
+            _check_grad(gb[k, j].cpu().numpy(), ga[k, j].cpu().numpy(), scale=2.0)
+    _, ta = a.energy(th, terms=True)
+    _, tb = b.energy(th, terms=True)
+    ra, rb = a.reps(), b.reps()
+    row_a = {(int(g), int(e)): i for i, (g, e) in enumerate(zip(ra["graph"], ra["edge"]))}
+    for i, (g, e) in enumerate(zip(rb["graph"], rb["edge"])):
+        assert np.max(np.abs(tb[i].cpu().numpy() - ta[row_a[(int(g), int(e))]].cpu().numpy())) <= TERM_TOL
+    assert b.device_status() == 0
+
+
+def test_cone_classes_match_the_fp64_oracle(q):
+    """Random cubic n = 24 at p = 2 with cone classes: energy and gradient against
+    the FP64 oracle summed over every edge (no reduction on the oracle side)."""
+    n, edges = I.random_regular(24, 3, 5)
+    p = 2
+    plan = q.Plan((n, edges), p, cone_classes=True)
+    assert plan.info()["n_reps"] < len(edges)
+    theta = I.draw_params(p, 3, 61)
+    e, g = plan.energy_grad(_params(theta))
+    adj = O.adjacency(n, edges)
+    every_edge = np.arange(len(edges))
+    for j in range(3):
+        eref, gref = O.orbit_grad_adjoint(n, edges, theta[j], p, every_edge, adj)
+        assert abs(e[0, j].item() - eref) <= E_REL_TOL * abs(eref)
+        _check_grad(g[0, j].cpu().numpy(), gref)
+    assert plan.device_status() == 0
+
+
 # ------------------------------------------ batching: CUDA graphs, tuning
 
 def _mixed_plan(q):

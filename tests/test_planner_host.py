@@ -281,8 +281,90 @@ def test_plan_flags(qlib):
     assert np.array_equal(a.shell_blocks(), b.shell_blocks())
     e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32))
     h = C.c_void_p()
-    rc = qlib.lib().qaoa_plan_graph(n, len(edges), qlib._ptr(e, C.c_int32), 3, 16, 0, 0, C.byref(h))
+    rc = qlib.lib().qaoa_plan_graph(n, len(edges), qlib._ptr(e, C.c_int32), 3, 32, 0, 0, C.byref(h))
     assert rc == qlib.QAOA_E_INVALID
+
+
+# ------------------------------------------------------------ cone classes
+
+def _cone_nx(plan, rep):
+    nx = pytest.importorskip("networkx")
+    verts, dist, ce = plan.cone(rep)
+    g = nx.Graph()
+    for i, d in enumerate(dist):
+        g.add_node(i, dist=int(d))
+    g.add_edges_from(map(tuple, ce))
+    return g
+
+
+@pytest.mark.parametrize("graph,p", [(I.random_regular(30, 3, 2), 2), (I.erdos_renyi(40, 0.15, 5), 1),
+                                     (I.random_regular(24, 3, 1), 3), (I.circulant(30, [1, 4]), 2),
+                                     (I.petersen(), 2)])
+def test_cone_classes_are_the_isomorphism_classes(qlib, graph, p):
+    """Edges share a cone class exactly when their cones are isomorphic with
+    the root edge fixed setwise: networkx's matcher (distance from the edge
+    as the node label, so the root edge maps onto itself) gives the same
+    partition of the edges."""
+    nx = pytest.importorskip("networkx")
+    from networkx.algorithms.isomorphism import GraphMatcher, categorical_node_match
+    n, edges = graph
+    plain = qlib.Plan((n, edges), p, orbits=False)  # one cone per edge, in edge order
+    cc = qlib.Plan((n, edges), p, orbits=False, cone_classes=True)
+    cid, ncls = cc.cone_classes(0)
+    cones = [_cone_nx(plain, e) for e in range(len(edges))]
+    match = categorical_node_match("dist", -1)
+    ref = [-1] * len(edges)
+    reps = []
+    for e, g in enumerate(cones):
+        for r in reps:
+            if GraphMatcher(g, cones[r], node_match=match).is_isomorphic():
+                ref[e] = r
+                break
+        if ref[e] < 0:
+            ref[e] = e
+            reps.append(e)
+    assert list(cid) == ref
+    assert ncls == len(reps) == cc.info()["n_reps"]
+    assert int(cc.reps()["weight"].sum()) == len(edges)
+
+
+def test_cone_classes_refine_orbits_and_keep_weights(qlib):
+    """With orbit reduction on, every Aut(G) orbit lies in one cone class, the
+    class weights sum to |E|, and a class's row carries its smallest edge."""
+    for graph, p in ((I.circulant(40, [1, 3]), 2), (I.random_regular(200, 3, 4), 2), (I.torus(6, 6), 2)):
+        n, edges = graph
+        plan = qlib.Plan((n, edges), p, cone_classes=True)
+        oid, _, _, _ = plan.orbits(0)
+        cid, ncls = plan.cone_classes(0)
+        for e in range(len(edges)):
+            assert cid[oid[e]] == cid[e] and cid[e] <= e
+        reps = plan.reps()
+        assert ncls == len(reps["edge"]) and int(reps["weight"].sum()) == len(edges)
+        assert sorted(reps["edge"]) == sorted(set(cid))
+        # without the flag the classes are the orbits
+        o = qlib.Plan((n, edges), p)
+        assert np.array_equal(o.cone_classes(0)[0], o.orbits(0)[0])
+
+
+def test_cone_classes_have_equal_oracle_terms(qlib):
+    """The FP64 oracle gives every edge of a class the same term (Theorem 1's
+    argument applied to cone isomorphisms), while different classes differ."""
+    n, edges = I.random_regular(60, 3, 7)
+    p = 2
+    plan = qlib.Plan((n, edges), p, orbits=False, cone_classes=True)
+    cid, ncls = plan.cone_classes(0)
+    assert ncls < len(edges)
+    adj = O.adjacency(n, edges)
+    theta = I.draw_params(p, 1, 3)[0]
+    classes = {}
+    for e, c in enumerate(cid):
+        classes.setdefault(int(c), []).append(e)
+    vals = {}
+    for c, members in sorted(classes.items(), key=lambda kv: -len(kv[1]))[:4]:
+        terms = [O.lightcone_term(n, edges, edges[e], theta, p, adj) for e in members[:3]]
+        assert max(terms) - min(terms) <= 1e-12
+        vals[c] = terms[0]
+    assert len(set(round(v, 9) for v in vals.values())) == len(vals)
 
 
 # ------------------------------------------------------------ shell classes
