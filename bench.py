@@ -401,6 +401,14 @@ def run_ours(args, rank, world, local_rank):
     cc_e, _ = ccplan.energy_grad(params)
     ref_e, _ = plan.energy_grad(params)
     cc_err = float((cc_e - ref_e).abs().max() / ref_e.abs().max())
+    # the training driver on this workload: Adam on -E from the same 64 starts per graph
+    from paper_2101_10296_gb300 import train as qtrain
+    tr_steps = 50
+    tr = qtrain.train(graphs, p, points=P, steps=tr_steps, lr=0.03, seed=1, plan=plan, device=device)
+    training = {"steps": tr_steps, "points_per_graph": P, "seconds": tr["seconds"],
+                "energy_grad_evals_per_s": world * tr["evals"] / tr["seconds"],
+                "best_energy_per_edge": float(np.mean(tr["energy"] / np.array([len(e) for _, e in graphs]))),
+                "note": "Adam (torch.optim) on the autograd energy, best point tracked on the host every step"}
 
     # roofline of the dominant kernel (the adjoint cone kernel)
     flops = algorithmic_flops(reps, p, grad=True) * P
@@ -454,6 +462,7 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clocks,
         "energy_only_evals_per_s": world * evals / (energy_ms / 1e3),
         "plain_all_edge_evals_per_s": world * evals / (plain_ms / 1e3),
+        "training": training,
         "cone_classes": {"n_classes": int(ccplan.info()["n_reps"]), "plan_s": t_cc,
                          "energy_grad_evals_per_s": world * evals / (cc_ms / 1e3),
                          "max_rel_energy_diff_vs_orbit_path": cc_err},

@@ -471,6 +471,34 @@ def test_cone_classes_match_the_fp64_oracle(q):
     assert plan.device_status() == 0
 
 
+def test_training_reaches_the_p1_optimum(q):
+    """The training driver (Adam through the autograd energy, 8 starts) reaches
+    the p = 1 optimum of a random cubic graph, found independently by
+    maximising the FP64 closed form (grid, then Nelder-Mead); the cone-class
+    plan trains to the same energy."""
+    from scipy.optimize import minimize
+
+    from paper_2101_10296_gb300 import train
+    n, edges = I.random_regular(16, 3, 9)
+    adj = O.adjacency(n, edges)
+
+    def energy(x):
+        return sum(O.closed_form_p1_term(n, edges, e, x[0], x[1], adj) for e in edges)
+
+    grid = [(energy((g, b)), g, b) for g in np.linspace(0, np.pi, 61) for b in np.linspace(0, np.pi / 2, 31)]
+    _, g0, b0 = max(grid)
+    res = minimize(lambda x: -energy(x), [g0, b0], method="Nelder-Mead",
+                   options={"xatol": 1e-10, "fatol": 1e-12, "maxiter": 4000})
+    e_star = -res.fun
+    out = train.train((n, edges), 1, points=8, steps=300, lr=0.03, seed=5, target=e_star - 1e-3)
+    # above the optimum only by the FP32 energy error (E_REL_TOL)
+    assert e_star - 1e-4 <= out["energy"][0] <= e_star * (1 + E_REL_TOL)
+    assert out["steps_to_target"][0] is not None and out["seconds_to_target"][0] > 0
+    assert np.all(np.diff(out["history"][:, 0]) >= 0)
+    out_cc = train.train((n, edges), 1, points=8, steps=300, lr=0.03, seed=5, cone_classes=True)
+    assert abs(out_cc["energy"][0] - out["energy"][0]) <= 1e-5
+
+
 # ------------------------------------------ batching: CUDA graphs, tuning
 
 def _mixed_plan(q):
