@@ -116,6 +116,26 @@ int qaoa_plan_graphs(int32_t n_graphs, const int32_t *n_vertices,
                      int32_t p, uint32_t flags, int32_t max_cone_qubits,
                      int64_t search_budget, qaoa_plan **out);
 
+/*
+ * Weighted (edge-coloured) form of qaoa_plan_graphs: weights (host
+ * int32[total edges], same order as edges; NULL = all 1) gives each edge an
+ * integer weight w_e with 1 <= |w_e| <= QAOA_MAX_CONE_EDGES.  The objective
+ * becomes the weighted cut C(z) = sum_e w_e [z_u != z_v] and
+ * E = sum_e w_e (1 - <Z_u Z_v>) / 2; the Ising objective
+ * f(z) = sum J_ij z_i z_j of Sec. 4 is this with w = -J (up to a constant
+ * and gamma -> 2 gamma).  Orbits are those of the automorphisms that map
+ * every edge to an edge of the same weight (Sec. 4: edge colours), shell and
+ * cone classes respect weights too.  An edge of weight w takes |w| bits of a
+ * cone's 64-bit cut word, so a cone's total |w| is capped at
+ * QAOA_MAX_CONE_EDGES (QAOA_E_CONE_TOO_LARGE).  QAOA_E_INVALID for a zero or
+ * out-of-range weight; otherwise as qaoa_plan_graphs.
+ */
+int qaoa_plan_graphs_weighted(int32_t n_graphs, const int32_t *n_vertices,
+                              const int64_t *edge_offsets, const int32_t *edges,
+                              const int32_t *weights, int32_t p, uint32_t flags,
+                              int32_t max_cone_qubits, int64_t search_budget,
+                              qaoa_plan **out);
+
 /* Single-graph form of qaoa_plan_graphs (edges: host int32[n_edges][2]). */
 int qaoa_plan_graph(int32_t n_vertices, int64_t n_edges, const int32_t *edges,
                     int32_t p, uint32_t flags, int32_t max_cone_qubits,
@@ -165,7 +185,8 @@ int qaoa_plan_cone_classes(const qaoa_plan *plan, int32_t graph, int32_t *class_
 
 /*
  * Representatives, in plan order (the row order of terms_dev).  Each array
- * is host memory of length n_reps and may be NULL.  weight = orbit size.
+ * is host memory of length n_reps and may be NULL.  weight = orbit size
+ * (total over the class with QAOA_CONE_CLASSES) times the edge's weight.
  * mix_qubits (host int32[n_reps][p], may be NULL): qubits mixed in each
  * layer -- the local qubits within distance p-l of the edge for layer l
  * (all n_qubits with QAOA_FULL_CONE).
@@ -182,6 +203,11 @@ int qaoa_plan_reps(const qaoa_plan *plan, int32_t *graph, int64_t *edge,
  */
 int qaoa_plan_cone(const qaoa_plan *plan, int64_t rep, int32_t *verts,
                    int32_t *dist, int32_t *cone_edges);
+
+/* Weights of one representative's cone edges (host int32[n_cone_edges], the
+ * order of qaoa_plan_cone; all 1 for an unweighted plan).  QAOA_E_INVALID on
+ * a bad plan, index or NULL pointer. */
+int qaoa_plan_cone_weights(const qaoa_plan *plan, int64_t rep, int32_t *weights);
 
 /*
  * Shell classes of one representative's cone.  The shell qubits (distance p,
@@ -219,7 +245,8 @@ int qaoa_plan_upload(qaoa_plan *plan);
  * Hamiltonian is diagonal with value C(z) = number of cone edges (a, b) with
  * z_a != z_b; bit q of z is local qubit q).  out_dev: device uint8[2^n]
  * with n = the cone's qubit count; computed by the same device routine the
- * energy kernels use.  Bit-exact.
+ * energy kernels use.  Bit-exact.  For a weighted plan the table holds
+ * C(z) + (sum of |w| over the cone's negative edges), which is >= 0.
  */
 int qaoa_cut_table(const qaoa_plan *plan, int64_t rep, uint8_t *out_dev,
                    qaoa_stream_t stream);

@@ -20,6 +20,10 @@ complex128 NumPy (arXiv:2101.10296):
   every cone qubit in every layer (no pruning).
 * Symmetry (Sec. 3, Theorem 1 and the orbit-weighted sum that follows it):
   E = sum_m |orbit_m| * 1/2 (1 - <Z Z>_{rep_m}).
+* Weighted objective (Sec. 4, the Ising objective with coloured edges):
+  with an integer weight w_e per edge (``weights``; None = all 1),
+  C(z) = sum_e w_e [z_u != z_v] and E = sum_e w_e 1/2 (1 - <Z_u Z_v>);
+  symmetries must map every edge to an edge of the same weight.
 
 Bit convention: bit q of the basis index z is the value of qubit (vertex) q.
 Readings where the paper is silent: the mixer is exp(-i beta X) with no 1/2
@@ -42,12 +46,15 @@ import numpy as np
 
 # ---------------------------------------------------------------- basics
 
-def cut_table(n, edges):
-    """C(z) for z in [0, 2^n): the number of edges (a, b) with z_a != z_b."""
+def cut_table(n, edges, weights=None):
+    """C(z) for z in [0, 2^n): the number (total weight) of edges (a, b) with
+    z_a != z_b."""
     z = np.arange(1 << n, dtype=np.int64)
     c = np.zeros(1 << n, dtype=np.int64)
-    for a, b in np.asarray(edges, dtype=np.int64).reshape(-1, 2):
-        c += ((z >> a) ^ (z >> b)) & 1
+    edges = np.asarray(edges, dtype=np.int64).reshape(-1, 2)
+    w = np.ones(len(edges), dtype=np.int64) if weights is None else np.asarray(weights, dtype=np.int64)
+    for (a, b), we in zip(edges, w):
+        c += we * (((z >> a) ^ (z >> b)) & 1)
     return c
 
 
@@ -80,9 +87,9 @@ def apply_mixer(psi, n, beta, qubits=None):
     return psi
 
 
-def qaoa_state(n, edges, gammas, betas):
+def qaoa_state(n, edges, gammas, betas, weights=None):
     """|beta, gamma>_p on n qubits for the graph ``edges`` (Sec. 2.2)."""
-    cut = cut_table(n, edges)
+    cut = cut_table(n, edges, weights)
     psi = plus_state(n)
     for g, b in zip(gammas, betas):
         psi = apply_phase(psi, cut, g)
@@ -104,11 +111,11 @@ def split_params(theta, p):
 
 # ------------------------------------------------ O1: whole-graph state
 
-def full_energy(n, edges, theta, p):
+def full_energy(n, edges, theta, p, weights=None):
     """E_p = <psi| C |psi> on the whole graph (n <= ~22)."""
     g, b = split_params(theta, p)
-    psi = qaoa_state(n, edges, g, b)
-    return float(np.sum(np.abs(psi) ** 2 * cut_table(n, edges)))
+    psi = qaoa_state(n, edges, g, b, weights)
+    return float(np.sum(np.abs(psi) ** 2 * cut_table(n, edges, weights)))
 
 
 def full_edge_terms(n, edges, theta, p):
@@ -167,19 +174,29 @@ def lightcone(n, edges, edge, p, adj=None):
     return verts, [dist[w] for w in verts], np.array(ledges, dtype=np.int64).reshape(-1, 2)
 
 
-def lightcone_term(n, edges, edge, theta, p, adj=None):
+def cone_weights(edges, weights, verts, ledges):
+    """Weights of a cone's local edges (None for an unweighted graph)."""
+    if weights is None:
+        return None
+    w = {(int(min(a, b)), int(max(a, b))): int(x) for (a, b), x in zip(np.asarray(edges).reshape(-1, 2), weights)}
+    return np.array([w[(min(verts[a], verts[b]), max(verts[a], verts[b]))] for a, b in ledges], dtype=np.int64)
+
+
+def lightcone_term(n, edges, edge, theta, p, adj=None, weights=None):
     """<Z_u Z_v> of one edge, simulated on its cone's induced subgraph."""
     verts, _, ledges = lightcone(n, edges, edge, p, adj)
     g, b = split_params(theta, p)
-    psi = qaoa_state(len(verts), ledges, g, b)
+    psi = qaoa_state(len(verts), ledges, g, b, cone_weights(edges, weights, verts, ledges))
     return zz_expectation(psi, 0, 1)
 
 
-def lightcone_energy(n, edges, theta, p, adj=None):
-    """E_p = sum over every edge of 1/2 (1 - <Z_u Z_v>_cone) (no symmetry)."""
+def lightcone_energy(n, edges, theta, p, adj=None, weights=None):
+    """E_p = sum over every edge of w_e 1/2 (1 - <Z_u Z_v>_cone) (no symmetry)."""
     if adj is None:
         adj = adjacency(n, edges)
-    return float(sum(0.5 * (1.0 - lightcone_term(n, edges, e, theta, p, adj)) for e in edges))
+    w = np.ones(len(edges)) if weights is None else np.asarray(weights, dtype=np.float64)
+    return float(sum(we * 0.5 * (1.0 - lightcone_term(n, edges, e, theta, p, adj, weights))
+                     for e, we in zip(edges, w)))
 
 
 def orbit_energy(n, edges, theta, p, orbit_id, adj=None):
@@ -221,17 +238,19 @@ def closed_form_p1_term(n, edges, edge, gamma, beta, adj=None):
 
 # ------------------------------------------------ O4: brute-force orbits
 
-def brute_automorphisms(n, edges):
+def brute_automorphisms(n, edges, weights=None):
     """Every automorphism of the graph, by backtracking over vertex images.
 
-    An automorphism is a vertex permutation preserving adjacency (Sec. 2.6).
+    An automorphism is a vertex permutation preserving adjacency (Sec. 2.6),
+    and with weights the weight of every edge (Sec. 4: edge colours).
     Vertices are mapped in the order 0..n-1; a partial map is extended only if
     degree and adjacency to every already-mapped vertex are preserved.
     """
-    adjm = np.zeros((n, n), dtype=bool)
-    for a, b in np.asarray(edges, dtype=np.int64).reshape(-1, 2):
-        adjm[a, b] = adjm[b, a] = True
-    deg = adjm.sum(axis=1)
+    adjm = np.zeros((n, n), dtype=np.int64)  # edge weight, 0 = no edge
+    w = np.ones(len(np.asarray(edges).reshape(-1, 2))) if weights is None else weights
+    for (a, b), we in zip(np.asarray(edges, dtype=np.int64).reshape(-1, 2), w):
+        adjm[a, b] = adjm[b, a] = int(we)
+    deg = (adjm != 0).sum(axis=1)
     out = []
     img = [-1] * n
     used = [False] * n
@@ -259,8 +278,9 @@ def brute_automorphisms(n, edges):
     return out
 
 
-def brute_edge_orbits(n, edges):
-    """Edge orbits under the full automorphism group.
+def brute_edge_orbits(n, edges, weights=None):
+    """Edge orbits under the full automorphism group (weight-preserving when
+    weights are given).
 
     Returns ``orbit_id[m]`` with orbits numbered by their smallest edge index
     (edge order as given).
@@ -269,7 +289,7 @@ def brute_edge_orbits(n, edges):
     index = {(int(a), int(b)): i for i, (a, b) in enumerate(edges)}
     m = len(edges)
     orbit = [-1] * m
-    autos = brute_automorphisms(n, edges)
+    autos = brute_automorphisms(n, edges, weights)
     nxt = 0
     for i in range(m):
         if orbit[i] >= 0:
@@ -285,11 +305,11 @@ def brute_edge_orbits(n, edges):
 
 # ---------------------------------------------------- O5: gradients
 
-def energy_lightcone_theta(n, edges, theta, p, adj=None):
-    return lightcone_energy(n, edges, theta, p, adj)
+def energy_lightcone_theta(n, edges, theta, p, adj=None, weights=None):
+    return lightcone_energy(n, edges, theta, p, adj, weights)
 
 
-def grad_fd(n, edges, theta, p, h=1e-4, adj=None):
+def grad_fd(n, edges, theta, p, h=1e-4, adj=None, weights=None):
     """Central finite differences of the cone-sum energy, FP64, step h."""
     if adj is None:
         adj = adjacency(n, edges)
@@ -300,11 +320,11 @@ def grad_fd(n, edges, theta, p, h=1e-4, adj=None):
         tm = theta.copy()
         tp[k] += h
         tm[k] -= h
-        g[k] = (lightcone_energy(n, edges, tp, p, adj) - lightcone_energy(n, edges, tm, p, adj)) / (2 * h)
+        g[k] = (lightcone_energy(n, edges, tp, p, adj, weights) - lightcone_energy(n, edges, tm, p, adj, weights)) / (2 * h)
     return g
 
 
-def term_grad_adjoint(nq, ledges, theta, p):
+def term_grad_adjoint(nq, ledges, theta, p, lweights=None):
     """d/dtheta of 1/2 (1 - <Z_0 Z_1>) on one cone, by the adjoint method.
 
     Forward: phi_l = U_P(g_l) psi_{l-1}, psi_l = U_B(b_l) phi_l.  With the
@@ -315,7 +335,7 @@ def term_grad_adjoint(nq, ledges, theta, p):
     back through the inverse gate.
     """
     gam, bet = split_params(theta, p)
-    cut = cut_table(nq, ledges)
+    cut = cut_table(nq, ledges, lweights)
     psi = plus_state(nq)
     for g_, b_ in zip(gam, bet):
         psi = apply_phase(psi, cut, g_)
@@ -338,22 +358,24 @@ def term_grad_adjoint(nq, ledges, theta, p):
     return value, grad
 
 
-def grad_adjoint(n, edges, theta, p, adj=None):
-    """(E, dE/dtheta) summed over every edge's cone, FP64 adjoint."""
+def grad_adjoint(n, edges, theta, p, adj=None, weights=None):
+    """(E, dE/dtheta) summed over every edge's cone (times its weight), FP64 adjoint."""
     if adj is None:
         adj = adjacency(n, edges)
+    w = np.ones(len(edges)) if weights is None else np.asarray(weights, dtype=np.float64)
     e_tot = 0.0
     g_tot = np.zeros(2 * p)
-    for e in edges:
+    for e, we in zip(edges, w):
         verts, _, ledges = lightcone(n, edges, e, p, adj)
-        val, gr = term_grad_adjoint(len(verts), ledges, theta, p)
-        e_tot += val
-        g_tot += gr
+        val, gr = term_grad_adjoint(len(verts), ledges, theta, p, cone_weights(edges, weights, verts, ledges))
+        e_tot += we * val
+        g_tot += we * gr
     return e_tot, g_tot
 
 
-def orbit_grad_adjoint(n, edges, theta, p, orbit_id, adj=None):
-    """(E, dE/dtheta) from one cone per orbit weighted by the orbit size."""
+def orbit_grad_adjoint(n, edges, theta, p, orbit_id, adj=None, weights=None):
+    """(E, dE/dtheta) from one cone per orbit weighted by the orbit size (and
+    the representative's edge weight)."""
     if adj is None:
         adj = adjacency(n, edges)
     orbit_id = np.asarray(orbit_id)
@@ -361,8 +383,10 @@ def orbit_grad_adjoint(n, edges, theta, p, orbit_id, adj=None):
     g_tot = np.zeros(2 * p)
     for m in np.unique(orbit_id):
         members = np.nonzero(orbit_id == m)[0]
-        verts, _, ledges = lightcone(n, edges, edges[members[0]], p, adj)
-        val, gr = term_grad_adjoint(len(verts), ledges, theta, p)
-        e_tot += members.size * val
-        g_tot += members.size * gr
+        rep = members[0]
+        we = 1.0 if weights is None else float(weights[rep])
+        verts, _, ledges = lightcone(n, edges, edges[rep], p, adj)
+        val, gr = term_grad_adjoint(len(verts), ledges, theta, p, cone_weights(edges, weights, verts, ledges))
+        e_tot += members.size * we * val
+        g_tot += members.size * we * gr
     return e_tot, g_tot

@@ -324,19 +324,38 @@ extern "C" int qaoa_plan_upload(qaoa_plan *plan) {
         d.graph = c.graph;
         d.n = c.n;
         d.n_in = c.n_in;
-        d.m = int32_t(c.ea.size());
         for (int l = 0; l < QAOA_MAX_P; ++l) d.k[l] = c.k[l];
         d.weight = double(c.weight);
         d.rep = int64_t(i);
+        // cut word bits: an edge of weight w owns |w| bits; the bits of negative
+        // edges are XORed in as a constant (neg), since -b = (b xor 1) - 1 for a
+        // cut bit b and the constant only adds a global phase
+        int32_t bit = 0;
         for (size_t e = 0; e < c.ea.size(); ++e) {
-            d.col[c.ea[e]] |= 1ull << e;
-            d.col[c.eb[e]] |= 1ull << e;
+            const int32_t w = c.ew[e], aw = w < 0 ? -w : w;
+            const uint64_t mask = (aw >= 64 ? ~0ull : ((1ull << aw) - 1)) << bit;
+            d.col[c.ea[e]] |= mask;
+            d.col[c.eb[e]] |= mask;
+            if (w < 0) d.neg |= mask;
+            bit += aw;
         }
+        d.m = bit;
         for (int l = 0; l < QAOA_MAX_P; ++l)
             for (int q = 0; q < c.k[l]; ++q) d.pw[l] ^= d.col[q];
         d.n_blocks = c.n_blocks;
         d.n_cls = int32_t(c.shell_classes.size());
         d.cls_off = int32_t(shell_tab.size());
+        if (d.neg) {
+            // the negative edges' constant enters every cut word once, through a
+            // class of no qubits in front of the shell classes (one block, weight 1)
+            const float one = 1.f;
+            uint32_t one_bits;
+            std::memcpy(&one_bits, &one, sizeof one_bits);
+            shell_tab.push_back(0);
+            shell_tab.push_back(d.neg);
+            shell_tab.push_back(one_bits);
+            d.n_cls += 1;
+        }
         for (const auto &cls : c.shell_classes) {
             const size_t sz = cls.size();
             shell_tab.push_back(sz);
@@ -420,7 +439,7 @@ extern "C" int qaoa_plan_upload(qaoa_plan *plan) {
     if (rc == QAOA_OK) rc = build_work(hc, reg_idx, kRegBitsGrad, d->reg_g);
     if (rc == QAOA_OK) {
         std::vector<double> half(size_t(plan->n_graphs));
-        for (int32_t g = 0; g < plan->n_graphs; ++g) half[g] = 0.5 * double(plan->n_edges[g]);
+        for (int32_t g = 0; g < plan->n_graphs; ++g) half[g] = 0.5 * double(plan->weight_sum[g]);
         if ((e = cudaMalloc(&d->half_edges, half.size() * sizeof(double))) != cudaSuccess)
             rc = cuda_fail(e, "cudaMalloc");
         else

@@ -34,6 +34,7 @@ struct ConeGraph {
     int m = 0;
     uint32_t adj[kMaxN] = {0};
     int32_t dist[kMaxN] = {0};
+    int8_t w[kMaxN][kMaxN] = {{0}};  // edge weights (colours)
 };
 
 ConeGraph cone_graph(const Cone &c) {
@@ -44,6 +45,7 @@ ConeGraph cone_graph(const Cone &c) {
     for (size_t e = 0; e < c.ea.size(); ++e) {
         g.adj[c.ea[e]] |= 1u << c.eb[e];
         g.adj[c.eb[e]] |= 1u << c.ea[e];
+        g.w[c.ea[e]][c.eb[e]] = g.w[c.eb[e]][c.ea[e]] = int8_t(c.ew[e]);
     }
     return g;
 }
@@ -69,7 +71,10 @@ void refine_round(const ConeGraph &g, uint64_t *col) {
     uint64_t nxt[kMaxN];
     for (int v = 0; v < g.n; ++v) {
         uint64_t s = 0;
-        for (uint32_t a = g.adj[v]; a; a &= a - 1) s += mix64(col[__builtin_ctz(a)]);
+        for (uint32_t a = g.adj[v]; a; a &= a - 1) {
+            const int u = __builtin_ctz(a);
+            s += mix64(col[u] ^ (uint64_t(uint8_t(g.w[v][u])) << 56));
+        }
         nxt[v] = mix64(col[v] * 0x2545f4914f6cdd1dull ^ s);
     }
     std::copy(nxt, nxt + g.n, col);
@@ -131,7 +136,11 @@ bool iso_search(const ConeGraph &A, const ConeGraph &B, uint64_t *ca, uint64_t *
         }
         for (int a = 0; a < A.n; ++a) {
             uint32_t img = 0;
-            for (uint32_t s = A.adj[a]; s; s &= s - 1) img |= 1u << phi[__builtin_ctz(s)];
+            for (uint32_t s = A.adj[a]; s; s &= s - 1) {
+                const int u = __builtin_ctz(s);
+                if (B.w[phi[a]][phi[u]] != A.w[a][u]) return false;
+                img |= 1u << phi[u];
+            }
             if (img != B.adj[phi[a]]) return false;
         }
         return true;

@@ -66,7 +66,7 @@ struct CutWords {
         lo[1] = c0;
         lo[2] = c1;
         lo[3] = c0 ^ c1;
-        MT base = 0;
+        MT base = MT(C->neg);  // negative-weight edges (see DevCone)
         for (int q = R; q < n; ++q)
             if ((t >> (q - R)) & 1) base ^= MT(C->col[q]);
         MT cm[R - 2];

@@ -20,7 +20,7 @@ struct alignas(16) DevCone {
     int32_t graph;   // graph index g
     int32_t n;       // qubits
     int32_t n_in;    // inner qubits: the only ones any mixer touches
-    int32_t m;       // cone edges
+    int32_t m;       // cut-word bits: cone edges, an edge of weight w counting |w|
     int32_t k[QAOA_MAX_P];  // layer l mixes qubits [0, k[l])
     double weight;   // orbit size
     int64_t rep;     // row of this cone in terms[]
@@ -29,6 +29,7 @@ struct alignas(16) DevCone {
     int32_t cls_off;   // this cone's entries in the shell table
     uint64_t col[QAOA_MAX_CONE_QUBITS];
     uint64_t pw[QAOA_MAX_P];  // M of the qubits layer l mixes, [0, k[l])
+    uint64_t neg;             // bits of negative-weight edges (already in the shell table's words)
 };
 
 // Shell table, per cone from cls_off, per class c of size s: word 0 = s,

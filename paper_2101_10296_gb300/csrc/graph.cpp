@@ -6,7 +6,7 @@
 
 namespace qaoa {
 
-int build_graph(int32_t n, int64_t m, const int32_t *edges, Graph &g, std::string &err) {
+int build_graph(int32_t n, int64_t m, const int32_t *edges, const int32_t *weights, Graph &g, std::string &err) {
     if (n < 0 || m < 0 || (m > 0 && edges == nullptr)) {
         err = "invalid graph sizes or NULL edge array";
         return QAOA_E_INVALID;
@@ -15,6 +15,20 @@ int build_graph(int32_t n, int64_t m, const int32_t *edges, Graph &g, std::strin
     g.m = m;
     g.eu.resize(m);
     g.ev.resize(m);
+    g.ew.assign(size_t(m), 1);
+    if (weights) {
+        for (int64_t e = 0; e < m; ++e) {
+            const int32_t w = weights[e];
+            if (w == 0 || w > QAOA_MAX_CONE_EDGES || w < -QAOA_MAX_CONE_EDGES) {
+                char buf[128];
+                snprintf(buf, sizeof buf, "edge %lld has weight %d (need 1 <= |w| <= %d)", (long long)e, w,
+                         QAOA_MAX_CONE_EDGES);
+                err = buf;
+                return QAOA_E_INVALID;
+            }
+            g.ew[e] = w;
+        }
+    }
     std::vector<int64_t> deg(size_t(n) + 1, 0);
     for (int64_t e = 0; e < m; ++e) {
         int32_t a = edges[2 * e], b = edges[2 * e + 1];

@@ -19,11 +19,13 @@ struct Graph {
     std::vector<int32_t> adj;
     std::vector<int64_t> eid;
     std::vector<int32_t> eu, ev;
+    std::vector<int32_t> ew;  // edge weights (colours), input order; all 1 for MaxCut
     int32_t degree(int32_t v) const { return int32_t(off[v + 1] - off[v]); }
 };
 
-// Validates and builds; returns QAOA_OK or QAOA_E_INVALID with `err` set.
-int build_graph(int32_t n, int64_t m, const int32_t *edges, Graph &g, std::string &err);
+// Validates and builds; weights may be NULL (all 1).  Returns QAOA_OK or
+// QAOA_E_INVALID with `err` set.
+int build_graph(int32_t n, int64_t m, const int32_t *edges, const int32_t *weights, Graph &g, std::string &err);
 int64_t find_edge(const Graph &g, int32_t a, int32_t b);
 
 struct OrbitResult {
@@ -49,6 +51,7 @@ struct Cone {
     int32_t k[QAOA_MAX_P] = {0};  // layer l mixes local qubits [0, k[l])
     std::vector<int32_t> verts, dist;
     std::vector<int32_t> ea, eb;  // local edges (a < b), sorted
+    std::vector<int32_t> ew;      // their weights
     // Shell (never-mixed) qubits grouped by their set of inner neighbours;
     // one block per vector of per-class counts of shell qubits set to 1.
     std::vector<std::vector<int32_t>> shell_classes;
@@ -83,6 +86,8 @@ struct qaoa_plan {
     int32_t n_graphs = 0;
     std::vector<int32_t> n_vertices;
     std::vector<int64_t> n_edges;
+    std::vector<int64_t> weight_sum;  // per graph: sum of edge weights (|E| for MaxCut)
+    bool weighted = false;
     std::vector<qaoa::OrbitResult> orbits;
     std::vector<qaoa::Cone> cones;  // plan order (rows of terms)
     // per graph and edge: the smallest edge of its cone class (QAOA_CONE_CLASSES),

@@ -72,6 +72,13 @@ class Refiner {
    public:
     explicit Refiner(const Graph &g) : g_(g), cnt_(size_t(g.n), 0), inq_(size_t(g.n), 0) {}
 
+    // A neighbour across an edge of weight w counts as ecode(w): 1 for the
+    // unweighted case, a distinct hash per weight otherwise, so the split
+    // respects edge colours (Sec. 4: colours = equal weights).
+    static uint64_t ecode(int32_t w) {
+        return w == 1 ? 1ull : hmix(0x5bd1e9955bd1e995ull, uint64_t(uint32_t(w))) | (1ull << 40);
+    }
+
     // Refines P to the coarsest equitable partition finer than P, starting
     // from the splitter cells in `queue` (consumed).  Each split is one event
     // hash; with `record` the events are appended, with `expect` they are
@@ -91,21 +98,21 @@ class Refiner {
                 int32_t x = P.lab[i];
                 for (int64_t k = g_.off[x]; k < g_.off[x + 1]; ++k) {
                     int32_t y = g_.adj[k];
-                    if (cnt_[y]++ == 0) touched_.push_back(y);
+                    if (cnt_[y] == 0) touched_.push_back(y);
+                    cnt_[y] += ecode(g_.ew[g_.eid[k]]);
                 }
             }
             keys_.clear();
-            for (int32_t y : touched_)
-                keys_.push_back({(uint64_t(uint32_t(P.cell[y])) << 32) | uint32_t(cnt_[y]), y});
+            for (int32_t y : touched_) keys_.push_back({{P.cell[y], cnt_[y]}, y});
             std::sort(keys_.begin(), keys_.end());
             size_t a = 0;
             while (a < keys_.size() && ok) {
-                int32_t X = int32_t(keys_[a].first >> 32);
+                int32_t X = keys_[a].first.first;
                 size_t b = a;
-                while (b < keys_.size() && int32_t(keys_[b].first >> 32) == X) ++b;
+                while (b < keys_.size() && keys_[b].first.first == X) ++b;
                 int32_t L = P.len[X];
                 int32_t t = int32_t(b - a);
-                bool split = (t < L) || (uint32_t(keys_[a].first) != uint32_t(keys_[b - 1].first));
+                bool split = (t < L) || (keys_[a].first.second != keys_[b - 1].first.second);
                 if (split && L > 1) {
                     uint64_t h = hmix(hmix(hmix(hmix(0, uint64_t(S)), uint64_t(slen)), uint64_t(X)),
                                       uint64_t(L));
@@ -125,8 +132,8 @@ class Refiner {
                     if (t < L) frag_.push_back({X, L - t, 0u});
                     for (size_t k = a; k < b;) {
                         size_t r = k;
-                        while (r < b && uint32_t(keys_[r].first) == uint32_t(keys_[k].first)) ++r;
-                        frag_.push_back({back + int32_t(k - a), int32_t(r - k), uint32_t(keys_[k].first)});
+                        while (r < b && keys_[r].first.second == keys_[k].first.second) ++r;
+                        frag_.push_back({back + int32_t(k - a), int32_t(r - k), keys_[k].first.second});
                         k = r;
                     }
                     bool was_in = inq_[X] != 0;
@@ -166,13 +173,13 @@ class Refiner {
    private:
     struct Frag {
         int32_t start, size;
-        uint32_t count;
+        uint64_t count;
     };
     const Graph &g_;
-    std::vector<int32_t> cnt_;
+    std::vector<uint64_t> cnt_;
     std::vector<char> inq_;
     std::vector<int32_t> touched_;
-    std::vector<std::pair<uint64_t, int32_t>> keys_;
+    std::vector<std::pair<std::pair<int32_t, uint64_t>, int32_t>> keys_;  // ((cell, count), vertex)
     std::vector<Frag> frag_;
 };
 
@@ -293,8 +300,10 @@ class AutSearch {
     }
 
     bool verify(const std::vector<int32_t> &perm) const {
-        for (int64_t e = 0; e < g_.m; ++e)
-            if (find_edge(g_, perm[g_.eu[e]], perm[g_.ev[e]]) < 0) return false;
+        for (int64_t e = 0; e < g_.m; ++e) {
+            const int64_t f = find_edge(g_, perm[g_.eu[e]], perm[g_.ev[e]]);
+            if (f < 0 || g_.ew[f] != g_.ew[e]) return false;
+        }
         return true;
     }
 

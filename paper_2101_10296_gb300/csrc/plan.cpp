@@ -82,7 +82,7 @@ int extract_cone(const Graph &g, int64_t e, int32_t p, bool full_cone, bool shel
         });
         return int32_t(it - ball.begin());
     };
-    std::vector<std::pair<int32_t, int32_t>> le;
+    std::vector<std::pair<std::pair<int32_t, int32_t>, int32_t>> le;  // ((a, b), weight)
     for (size_t i = 0; i < ball.size(); ++i) {
         int32_t x = ball[i];
         if (dist[x] > p - 1) continue;
@@ -91,23 +91,32 @@ int extract_cone(const Graph &g, int64_t e, int32_t p, bool full_cone, bool shel
             if (dist[y] < 0) continue;
             if (dist[y] <= p - 1 && y < x) continue;  // inner-inner edge: add once
             int32_t a = int32_t(i), b = local(y);
-            le.emplace_back(std::min(a, b), std::max(a, b));
+            le.push_back({{std::min(a, b), std::max(a, b)}, g.ew[g.eid[k]]});
         }
     }
     std::sort(le.begin(), le.end());
     restore();
-    if (le.size() > size_t(QAOA_MAX_CONE_EDGES)) {
+    // an edge of weight w takes |w| bits of the 64-bit cut word
+    size_t bits = 0;
+    for (const auto &x : le) bits += size_t(x.second < 0 ? -x.second : x.second);
+    if (bits > size_t(QAOA_MAX_CONE_EDGES)) {
         char buf[160];
-        snprintf(buf, sizeof buf, "cone of edge %lld has %zu edges > cap %d", (long long)e, le.size(),
-                 QAOA_MAX_CONE_EDGES);
+        if (bits == le.size())
+            snprintf(buf, sizeof buf, "cone of edge %lld has %zu edges > cap %d", (long long)e, le.size(),
+                     QAOA_MAX_CONE_EDGES);
+        else
+            snprintf(buf, sizeof buf, "cone of edge %lld has %zu edges of total |weight| %zu > cap %d",
+                     (long long)e, le.size(), bits, QAOA_MAX_CONE_EDGES);
         err = buf;
         return QAOA_E_CONE_TOO_LARGE;
     }
     c.ea.resize(le.size());
     c.eb.resize(le.size());
+    c.ew.resize(le.size());
     for (size_t i = 0; i < le.size(); ++i) {
-        c.ea[i] = le[i].first;
-        c.eb[i] = le[i].second;
+        c.ea[i] = le[i].first.first;
+        c.eb[i] = le[i].first.second;
+        c.ew[i] = le[i].second;
     }
     int32_t n_in = 0;
     for (int32_t d : c.dist) n_in += (d <= p - 1);
@@ -121,18 +130,20 @@ int extract_cone(const Graph &g, int64_t e, int32_t p, bool full_cone, bool shel
     }
     // Shell classes.  A shell qubit (distance p) is never mixed and meets the
     // phases only through its cone edges, all of which go to inner qubits; two
-    // shell qubits with the same inner neighbours can be exchanged without
-    // changing any cut value, so an inner block's evolution depends on the
-    // shell assignment only through how many qubits of each class are 1.
+    // shell qubits with the same inner neighbours (and edge weights) can be
+    // exchanged without changing any cut value, so an inner block's evolution
+    // depends on the shell assignment only through how many qubits of each
+    // class are 1.
     c.shell_classes.clear();
     c.n_blocks = 1;
     if (c.n_in < c.n) {
-        std::vector<uint64_t> nb(size_t(c.n), 0);
+        std::vector<std::vector<std::pair<int32_t, int32_t>>> nb(size_t(c.n));  // (inner neighbour, weight)
         for (size_t i = 0; i < c.ea.size(); ++i) {
             const int32_t a = c.ea[i], b = c.eb[i];
-            if (a >= c.n_in && b < c.n_in) nb[a] |= 1ull << b;
-            if (b >= c.n_in && a < c.n_in) nb[b] |= 1ull << a;
+            if (a >= c.n_in && b < c.n_in) nb[a].emplace_back(b, c.ew[i]);
+            if (b >= c.n_in && a < c.n_in) nb[b].emplace_back(a, c.ew[i]);
         }
+        for (auto &x : nb) std::sort(x.begin(), x.end());
         for (int32_t q = c.n_in; q < c.n; ++q) {
             bool placed = false;
             if (!shell_plain) {
@@ -186,6 +197,13 @@ extern "C" const char *qaoa_version(void) { return "qaoa-gb300 0.1 (sm_103a)"; }
 extern "C" int qaoa_plan_graphs(int32_t n_graphs, const int32_t *n_vertices, const int64_t *edge_offsets,
                                 const int32_t *edges, int32_t p, uint32_t flags, int32_t max_cone_qubits,
                                 int64_t search_budget, qaoa_plan **out) {
+    return qaoa_plan_graphs_weighted(n_graphs, n_vertices, edge_offsets, edges, nullptr, p, flags, max_cone_qubits,
+                                     search_budget, out);
+}
+
+extern "C" int qaoa_plan_graphs_weighted(int32_t n_graphs, const int32_t *n_vertices, const int64_t *edge_offsets,
+                                         const int32_t *edges, const int32_t *weights, int32_t p, uint32_t flags,
+                                         int32_t max_cone_qubits, int64_t search_budget, qaoa_plan **out) {
     g_last_error.clear();
     if (!out) {
         set_error("out is NULL");
@@ -234,17 +252,24 @@ extern "C" int qaoa_plan_graphs(int32_t n_graphs, const int32_t *n_vertices, con
         pl->n_graphs = n_graphs;
         pl->n_vertices.assign(n_vertices, n_vertices + n_graphs);
         pl->n_edges.resize(n_graphs);
+        pl->weight_sum.resize(n_graphs);
         std::vector<Graph> graphs(n_graphs);
         for (int32_t g = 0; g < n_graphs; ++g) {
             std::string err;
             int64_t m = edge_offsets[g + 1] - edge_offsets[g];
-            int rc = build_graph(n_vertices[g], m, edges + 2 * edge_offsets[g], graphs[g], err);
+            int rc = build_graph(n_vertices[g], m, edges + 2 * edge_offsets[g],
+                                 weights ? weights + edge_offsets[g] : nullptr, graphs[g], err);
             if (rc != QAOA_OK) {
                 set_error("graph " + std::to_string(g) + ": " + err);
                 delete pl;
                 return rc;
             }
             pl->n_edges[g] = m;
+            pl->weight_sum[g] = 0;
+            for (int32_t w : graphs[g].ew) {
+                pl->weight_sum[g] += w;
+                pl->weighted |= w != 1;
+            }
         }
         auto t0 = std::chrono::steady_clock::now();
         pl->orbits.resize(n_graphs);
@@ -276,7 +301,7 @@ extern "C" int qaoa_plan_graphs(int32_t n_graphs, const int32_t *n_vertices, con
             Cone &c = pl->cones[i];
             c.graph = g;
             c.edge = reps[i].second;
-            c.weight = size_of[g][reps[i].second];
+            c.weight = size_of[g][reps[i].second] * graphs[g].ew[reps[i].second];  // orbit size x edge weight
             rcs[i] = extract_cone(graphs[g], c.edge, p, (flags & QAOA_FULL_CONE) != 0,
                                   (flags & QAOA_SHELL_PLAIN) != 0, max_cone_qubits, dist, c, errs[t]);
         });
@@ -427,13 +452,23 @@ extern "C" int qaoa_plan_cone(const qaoa_plan *plan, int64_t rep, int32_t *verts
     return QAOA_OK;
 }
 
+extern "C" int qaoa_plan_cone_weights(const qaoa_plan *plan, int64_t rep, int32_t *weights) {
+    if (!plan || rep < 0 || rep >= int64_t(plan->cones.size()) || !weights) {
+        set_error("bad plan, representative index or NULL weights");
+        return QAOA_E_INVALID;
+    }
+    const Cone &c = plan->cones[size_t(rep)];
+    std::copy(c.ew.begin(), c.ew.end(), weights);
+    return QAOA_OK;
+}
+
 extern "C" int qaoa_edge_orbits(int32_t n_vertices, int64_t n_edges, const int32_t *edges, int64_t search_budget,
                                 int32_t *orbit_id, int64_t *n_orbits, int64_t *n_generators, double *log10_aut,
                                 int32_t *complete) {
     g_last_error.clear();
     Graph g;
     std::string err;
-    int rc = build_graph(n_vertices, n_edges, edges, g, err);
+    int rc = build_graph(n_vertices, n_edges, edges, nullptr, g, err);
     if (rc != QAOA_OK) {
         set_error(err);
         return rc;

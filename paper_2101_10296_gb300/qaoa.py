@@ -65,6 +65,9 @@ _SIGS = {
     "qaoa_plan_info": (C.c_int, [_P, C.POINTER(PlanInfo)]),
     "qaoa_plan_orbits": (C.c_int, [_P, C.c_int32, _I32P, _I64P, _F64P, _I32P]),
     "qaoa_plan_cone_classes": (C.c_int, [_P, C.c_int32, _I32P, _I64P]),
+    "qaoa_plan_graphs_weighted": (C.c_int, [C.c_int32, _I32P, _I64P, _I32P, _I32P, C.c_int32, C.c_uint32,
+                                            C.c_int32, C.c_int64, C.POINTER(_P)]),
+    "qaoa_plan_cone_weights": (C.c_int, [_P, C.c_int64, _I32P]),
     "qaoa_plan_reps": (C.c_int, [_P, _I32P, _I64P, _I32P, _I32P, _I32P, _I32P, _I32P]),
     "qaoa_plan_cone": (C.c_int, [_P, C.c_int64, _I32P, _I32P, _I32P]),
     "qaoa_plan_shell": (C.c_int, [_P, C.c_int64, _I32P, _I64P]),
@@ -147,9 +150,14 @@ class Plan:
     """A planned batch of graphs (orbits + cones), owning its device copy."""
 
     def __init__(self, graphs, p, orbits=True, full_cone=False, max_cone_qubits=0, search_budget=0,
-                 shell_plain=False, big_general=False, cone_classes=False):
+                 shell_plain=False, big_general=False, cone_classes=False, weights=None):
+        """graphs: (n, edges) or a list of them; weights: None (MaxCut) or one
+        integer array per graph (edge weights / colours, see
+        qaoa_plan_graphs_weighted)."""
         if isinstance(graphs, tuple):
             graphs = [graphs]
+            if weights is not None and np.ndim(weights[0]) == 0:
+                weights = [weights]
         nv = _i32([g[0] for g in graphs])
         offs = [0]
         rows = []
@@ -162,9 +170,18 @@ class Plan:
         flags = (ORBITS if orbits else ORBITS_OFF) | (FULL_CONE if full_cone else 0) | (SHELL_PLAIN if shell_plain else 0)
         flags |= (BIG_GENERAL if big_general else 0) | (CONE_CLASSES if cone_classes else 0)
         h = C.c_void_p()
-        _check(lib().qaoa_plan_graphs(len(graphs), _ptr(nv, C.c_int32), _ptr(offs, C.c_int64),
-                                      _ptr(edges, C.c_int32) if edges.size else None, p, flags,
-                                      max_cone_qubits, search_budget, C.byref(h)))
+        if weights is None:
+            _check(lib().qaoa_plan_graphs(len(graphs), _ptr(nv, C.c_int32), _ptr(offs, C.c_int64),
+                                          _ptr(edges, C.c_int32) if edges.size else None, p, flags,
+                                          max_cone_qubits, search_budget, C.byref(h)))
+        else:
+            w = _i32(np.concatenate([np.asarray(x).reshape(-1) for x in weights]) if len(weights) else [])
+            if w.size != edges.shape[0]:
+                raise ValueError("one weight per edge is needed")
+            _check(lib().qaoa_plan_graphs_weighted(len(graphs), _ptr(nv, C.c_int32), _ptr(offs, C.c_int64),
+                                                   _ptr(edges, C.c_int32) if edges.size else None,
+                                                   _ptr(w, C.c_int32) if w.size else None, p, flags,
+                                                   max_cone_qubits, search_budget, C.byref(h)))
         self._h = h
         self.p = p
         self.n_graphs = len(graphs)
@@ -225,6 +242,13 @@ class Plan:
         _check(lib().qaoa_plan_cone(self._h, rep, _ptr(verts, C.c_int32), _ptr(dist, C.c_int32),
                                     _ptr(ce, C.c_int32)))
         return verts, dist, ce[:ne]
+
+    def cone_weights(self, rep):
+        """Weights of the cone's edges (order of :meth:`cone`)."""
+        ne = int(self.reps()["n_cone_edges"][rep])
+        w = np.zeros(max(ne, 1), dtype=np.int32)
+        _check(lib().qaoa_plan_cone_weights(self._h, rep, _ptr(w, C.c_int32)))
+        return w[:ne]
 
     def shell(self, rep):
         """(class index per cone qubit, -1 for inner; number of shell blocks)."""

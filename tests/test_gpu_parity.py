@@ -499,6 +499,58 @@ def test_training_reaches_the_p1_optimum(q):
     assert abs(out_cc["energy"][0] - out["energy"][0]) <= 1e-5
 
 
+def _alternating(edges):
+    return np.array([(-1) ** int(min(a, b)) if abs(int(a) - int(b)) == 1 else -1 for a, b in edges])
+
+
+@pytest.mark.parametrize("graph,p,values", [(I.random_regular(16, 3, 3), 2, (1, -1)),
+                                            (I.cycle(12), 2, None),
+                                            (I.complete(8), 1, (1, -1)),
+                                            (I.erdos_renyi(14, 0.3, 2), 1, (1, -1, 2)),
+                                            (I.random_regular(16, 3, 3), 3, (1, -1)),
+                                            (I.circulant(30, [1, 2]), 3, None)])
+def test_weighted_energy_grad_terms_match_oracle(q, graph, p, values):
+    """Edge weights (Sec. 4: the Ising objective with coloured edges; an
+    alternating-sign cycle / circulant where values is None, an SK-like K_8
+    with random signs, weights of 2): energies and gradients against the FP64
+    oracle summed over every edge, representative terms, and the cone-class
+    plan's energies.  p = 3 cones with 10-13 inner qubits take the
+    large-state path."""
+    n, edges = graph
+    w = _alternating(edges) if values is None else np.random.default_rng(17).choice(values, len(edges))
+    theta = I.draw_params(p, 3, 71)
+    plan = q.Plan((n, edges), p, weights=w)
+    e, g = plan.energy_grad(_params(theta))
+    _, t = plan.energy(_params(theta), terms=True)
+    e_cc = q.Plan((n, edges), p, weights=w, cone_classes=True).energy(_params(theta))
+    adj = O.adjacency(n, edges)
+    every_edge = np.arange(len(edges))
+    reps = plan.reps()
+    for j in range(3):
+        eref, gref = O.orbit_grad_adjoint(n, edges, theta[j], p, every_edge, adj, weights=w)
+        assert abs(e[0, j].item() - eref) <= E_REL_TOL * max(abs(eref), 1.0)
+        assert abs(e_cc[0, j].item() - eref) <= E_REL_TOL * max(abs(eref), 1.0)
+        _check_grad(g[0, j].cpu().numpy(), gref)
+    for r in range(min(4, len(reps["edge"]))):
+        ref = O.lightcone_term(n, edges, edges[reps["edge"][r]], theta[1], p, adj, weights=w)
+        assert abs(t[r, 1].item() - ref) <= TERM_TOL
+    assert plan.device_status() == 0
+
+
+def test_weighted_cut_table_is_bit_exact(q):
+    """A weighted cone's cut table: sum_e w_e [z_a != z_b] plus the total |w| of
+    its negative edges (so that it stays unsigned), bit-exact."""
+    n, edges = I.erdos_renyi(14, 0.3, 2)
+    w = np.random.default_rng(17).choice([1, -1, 2], len(edges))
+    plan = q.Plan((n, edges), 1, weights=w)
+    for rep in range(min(6, plan.info()["n_reps"])):
+        verts, _, ce = plan.cone(rep)
+        cw = plan.cone_weights(rep)
+        tab = plan.cut_table(rep).cpu().numpy().astype(np.int64)
+        ref = O.cut_table(len(verts), ce, cw) + int(np.abs(cw[cw < 0]).sum())
+        assert np.array_equal(tab, ref)
+
+
 # ------------------------------------------ batching: CUDA graphs, tuning
 
 def _mixed_plan(q):

@@ -262,3 +262,91 @@ def test_params_recipe_first_draw():
     th = I.draw_params(1, 1, 0)
     u = np.random.default_rng(0).random(2)
     assert th[0, 0] == u[0] * np.pi and th[0, 1] == u[1] * np.pi / 2
+
+
+# --------------------------------------------- O6: weighted (coloured) edges
+
+def _signs(m, seed, values=(1, -1)):
+    return np.random.default_rng(seed).choice(values, m)
+
+
+def _dense_weighted(n, edges, weights, gam, bet):
+    X = np.array([[0, 1], [1, 0]], dtype=complex)
+    Z = np.diag([1.0, -1.0]).astype(complex)
+    dim = 1 << n
+    H = np.zeros((dim, dim), dtype=complex)
+    for (u, v), w in zip(edges, weights):
+        H += 0.5 * w * (np.eye(dim) - _pauli_on(n, int(u), Z) @ _pauli_on(n, int(v), Z))
+    B = sum(_pauli_on(n, q, X) for q in range(n))
+    psi = np.ones(dim, dtype=complex) / math.sqrt(dim)
+    for g, b in zip(gam, bet):
+        psi = scipy.linalg.expm(-1j * b * B) @ (scipy.linalg.expm(-1j * g * H) @ psi)
+    return psi, H
+
+
+@pytest.mark.parametrize("name", ["K3", "P4", "C5", "W5", "K23"])
+@pytest.mark.parametrize("p", [1, 2])
+def test_weighted_state_matches_dense_expm(name, p):
+    """Weighted cost H = sum_e w_e (I - Z_u Z_v)/2 (Sec. 4's objective with edge
+    colours) built from Pauli matrices, weights in {-2, -1, 1, 3}."""
+    n, edges = SMALL_GRAPHS[name]
+    w = _signs(len(edges), 5 + p, (-2, -1, 1, 3))
+    theta = _rand_theta(p, 7 * p + n)
+    gam, bet = theta[:p], theta[p:]
+    psi_ref, H = _dense_weighted(n, edges, w, gam, bet)
+    psi = O.qaoa_state(n, edges, gam, bet, w)
+    ov = np.vdot(psi_ref, psi)
+    assert abs(abs(ov) - 1.0) < 1e-12
+    assert np.allclose(psi * np.conj(ov) / abs(ov), psi_ref, atol=1e-12)
+    assert np.array_equal(O.cut_table(n, edges, w), np.real(np.diag(H)).round().astype(np.int64))
+    e_ref = float(np.real(np.vdot(psi_ref, H @ psi_ref)))
+    assert abs(O.full_energy(n, edges, theta, p, w) - e_ref) < 1e-10
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_weighted_lightcone_sum_equals_full_energy(p):
+    n, edges = SMALL_GRAPHS["petersen"]
+    w = _signs(len(edges), p)
+    th = _rand_theta(p, 40 + p)
+    assert abs(O.lightcone_energy(n, edges, th, p, weights=w) - O.full_energy(n, edges, th, p, w)) < 1e-10
+
+
+def test_all_negative_weights_mirror_the_unweighted_energy():
+    """C -> -C maps E(gamma, beta) to -E(-gamma, beta): an identity that ties the
+    weighted code path to the unweighted one."""
+    n, edges = SMALL_GRAPHS["rr3-10"]
+    for p in (1, 2):
+        th = _rand_theta(p, 60 + p)
+        mirrored = th.copy()
+        mirrored[:p] *= -1
+        e_neg = O.full_energy(n, edges, th, p, -np.ones(len(edges), dtype=np.int64))
+        assert abs(e_neg + O.full_energy(n, edges, mirrored, p)) < 1e-11
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_weighted_adjoint_matches_finite_differences(p):
+    n, edges = SMALL_GRAPHS["W5"]
+    w = _signs(len(edges), 3 + p, (-1, 1, 2))
+    th = _rand_theta(p, 80 + p)
+    e, g = O.grad_adjoint(n, edges, th, p, weights=w)
+    assert abs(e - O.lightcone_energy(n, edges, th, p, weights=w)) < 1e-11
+    assert np.max(np.abs(g - O.grad_fd(n, edges, th, p, h=1e-5, weights=w))) < 1e-7
+
+
+def test_weighted_orbits_respect_colours():
+    """An 8-cycle with alternating signs keeps only the rotations by two and the
+    reflections that map signs to signs: 8 automorphisms, two edge orbits (the
+    positive and the negative edges); all-positive gives the dihedral 16 and one."""
+    n, edges = I.cycle(8)
+    # edge (i, i+1) gets sign (-1)^i, the closing edge (0, 7) sign -1
+    alt = np.array([(-1) ** int(min(a, b)) if abs(int(a) - int(b)) == 1 else -1 for a, b in edges])
+    assert len(O.brute_automorphisms(n, edges)) == 16
+    assert len(O.brute_automorphisms(n, edges, alt)) == 8
+    orb = O.brute_edge_orbits(n, edges, alt)
+    assert len(set(orb)) == 2
+    for s in set(orb):
+        assert len(set(alt[orb == s])) == 1
+    th = _rand_theta(2, 5)
+    e1, g1 = O.grad_adjoint(n, edges, th, 2, weights=alt)
+    e2, g2 = O.orbit_grad_adjoint(n, edges, th, 2, orb, weights=alt)
+    assert abs(e1 - e2) < 1e-11 and np.max(np.abs(g1 - g2)) < 1e-11

@@ -59,6 +59,42 @@ def test_orbits_match_brute_force_families(qlib, graph):
     assert np.array_equal(_canon(oid), _canon(O.brute_edge_orbits(n, edges)))
 
 
+@pytest.mark.parametrize("n,q,count,values", [(7, 0.4, 40, (1, -1)), (8, 0.5, 30, (1, -1, 2)),
+                                              (9, 0.35, 20, (1, -1))])
+def test_weighted_orbits_match_brute_force(qlib, n, q, count, values):
+    """Edge colours (Sec. 4): the planner's orbits are those of the
+    weight-preserving automorphisms, as brute force enumerates them."""
+    rng = np.random.default_rng(100 + n)
+    for _ in range(count):
+        _, edges = I.erdos_renyi(n, q, int(rng.integers(1 << 30)))
+        if len(edges) == 0:
+            continue
+        w = rng.choice(values, len(edges))
+        plan = qlib.Plan((n, edges), 1, weights=w)
+        oid, norb, l10, comp = plan.orbits(0)
+        ref = O.brute_edge_orbits(n, edges, w)
+        assert comp and np.array_equal(_canon(oid), _canon(ref))
+        assert abs(10 ** l10 / len(O.brute_automorphisms(n, edges, w)) - 1) < 1e-9
+        reps = plan.reps()
+        for r in range(len(reps["edge"])):
+            e = int(reps["edge"][r])
+            assert reps["weight"][r] == int(np.sum(oid == e)) * int(w[e])
+
+
+def test_weighted_input_errors_and_caps(qlib):
+    n, edges = I.cycle(6)
+    for bad in (0, 65, -65):
+        w = np.ones(len(edges), dtype=np.int64)
+        w[2] = bad
+        with pytest.raises(qlib.QAOAError) as ei:
+            qlib.Plan((n, edges), 1, weights=w)
+        assert ei.value.code == qlib.QAOA_E_INVALID and "weight" in str(ei.value)
+    # a p = 1 cone of C_6 has 3 edges; weights 30 + 30 + 30 exceed the 64-bit cut word
+    with pytest.raises(qlib.QAOAError) as ei:
+        qlib.Plan((n, edges), 1, weights=np.full(len(edges), 30))
+    assert ei.value.code == qlib.QAOA_E_CONE_TOO_LARGE and "weight" in str(ei.value)
+
+
 def test_orbit_id_is_smallest_edge_of_orbit(qlib):
     n, edges = I.circulant(12, [1, 5])
     oid, *_ = qlib.edge_orbits(n, edges)
@@ -326,6 +362,36 @@ def test_cone_classes_are_the_isomorphism_classes(qlib, graph, p):
     assert list(cid) == ref
     assert ncls == len(reps) == cc.info()["n_reps"]
     assert int(cc.reps()["weight"].sum()) == len(edges)
+
+
+def test_weighted_cone_classes_are_the_coloured_isomorphism_classes(qlib):
+    """With edge weights a class joins only cones isomorphic as edge-coloured
+    graphs (networkx with an edge-weight match)."""
+    pytest.importorskip("networkx")
+    from networkx.algorithms.isomorphism import GraphMatcher, categorical_edge_match, categorical_node_match
+    n, edges = I.random_regular(30, 3, 2)
+    w = np.random.default_rng(4).choice([1, -1], len(edges))
+    plain = qlib.Plan((n, edges), 2, orbits=False, weights=w)
+    cc = qlib.Plan((n, edges), 2, orbits=False, cone_classes=True, weights=w)
+    cid, ncls = cc.cone_classes(0)
+    cones = []
+    for e in range(len(edges)):
+        g = _cone_nx(plain, e)
+        for (a, b), x in zip(plain.cone(e)[2], plain.cone_weights(e)):
+            g.edges[int(a), int(b)]["w"] = int(x)
+        cones.append(g)
+    nm, em = categorical_node_match("dist", -1), categorical_edge_match("w", 0)
+    ref, reps = [-1] * len(edges), []
+    for e, g in enumerate(cones):
+        for r in reps:
+            if GraphMatcher(g, cones[r], node_match=nm, edge_match=em).is_isomorphic():
+                ref[e] = r
+                break
+        if ref[e] < 0:
+            ref[e] = e
+            reps.append(e)
+    assert list(cid) == ref and ncls == len(reps)
+    assert int(cc.reps()["weight"].sum()) == int(np.sum(w))
 
 
 def test_cone_classes_refine_orbits_and_keep_weights(qlib):
