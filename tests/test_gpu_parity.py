@@ -551,6 +551,34 @@ def test_weighted_cut_table_is_bit_exact(q):
         assert np.array_equal(tab, ref)
 
 
+def _max_cut(n, edges, weights=None):
+    z = np.arange(1 << n, dtype=np.int64)
+    c = np.zeros(1 << n)
+    w = np.ones(len(edges)) if weights is None else weights
+    for (a, b), x in zip(edges, w):
+        c += x * (((z >> a) ^ (z >> b)) & 1)
+    return float(c.max())
+
+
+def test_rqaoa_reaches_good_cuts(q):
+    """RQAOA (Sec. 4.1) on top of training, terms and re-planning: the even
+    cycle (bipartite) is cut completely, a random cubic graph and a signed
+    (weighted) one come within 10% of the brute-force optimum, and the
+    reported cut is the assignment's value on the input objective."""
+    from paper_2101_10296_gb300 import rqaoa
+    n, edges = I.cycle(16)
+    out = rqaoa.rqaoa(n, edges, p=1, n_brute=6, steps=120, points=8, seed=1)
+    assert out["cut"] == len(edges) and len(out["rounds"]) == n - 6
+    for graph, w in ((I.random_regular(14, 3, 2), None),
+                     (I.random_regular(14, 3, 3), np.random.default_rng(5).choice([1, -1], 21))):
+        n, edges = graph
+        out = rqaoa.rqaoa(n, edges, w, p=1, n_brute=6, steps=120, points=8, seed=2)
+        assert out["cut"] == rqaoa.cut_value(edges, w, out["bits"])
+        best = _max_cut(n, edges, w)
+        assert best >= out["cut"] >= 0.9 * best
+        assert all(r["abs_zz"] > 0 for r in out["rounds"])
+
+
 # ------------------------------------------ batching: CUDA graphs, tuning
 
 def _mixed_plan(q):
