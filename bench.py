@@ -15,7 +15,8 @@ rank runs its own replica (the path shards into independent problems; there
 is no data-path collective), so the whole-job value is N x per-rank evals.
 
 ``--impl reference`` times the FP64 CPU oracle on the host cores on a bounded
-sample of the same workload.
+sample of the same workload: random cone terms of the four graphs at one
+parameter point, scaled to whole evaluations.
 """
 from __future__ import annotations
 
@@ -26,6 +27,7 @@ import math
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -171,7 +173,10 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # the raw samples go to $QAOA_BENCH_CLOCKS_DIR (default: the temp directory);
+        # the JSON line carries their summary
+        out_dir = os.environ.get("QAOA_BENCH_CLOCKS_DIR", tempfile.gettempdir())
+        self.path = os.path.join(out_dir, f"qaoa_clocks_rank{index}.csv")
 
     def __enter__(self):
         try:
@@ -527,7 +532,9 @@ G_P_EVALS = len(SEEDS) * N_POINTS
 # ------------------------------------------------------------------ suite
 
 def suite_configs():
-    """The five benchmark configurations (readings of their sizes as in the design doc)."""
+    """The five benchmark configurations (3 split by depth, 4 by graph: Q_12 and C_5000(1,7,23)
+    have cones of 134 and 38 qubits at p = 2, the 8x8 torus 32 at p = 3), plus a signed
+    objective on configuration 2's graphs."""
     from paper_2101_10296_gb300 import inputs as I
     return [
         ("1. C_20(1,4) p=1, 1 point", [I.circulant(20, [1, 4])], 1, 1),

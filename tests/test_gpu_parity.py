@@ -537,6 +537,35 @@ def test_weighted_energy_grad_terms_match_oracle(q, graph, p, values):
     assert plan.device_status() == 0
 
 
+def test_weighted_schedules_and_modes_agree(q):
+    """Signed weights through every large-state schedule and plan mode at p = 3
+    (cones of up to 13 inner qubits): full cones (general schedule), the
+    general schedule forced on pruned cones, every shell assignment evolved
+    separately, the default core-tile schedule, and the allocation-free
+    energy, all against the FP64 oracle."""
+    n, edges = I.random_regular(16, 3, 3)
+    w = np.random.default_rng(23).choice([1, -1], len(edges))
+    p = 3
+    theta = I.draw_params(p, 3, 81)
+    every_edge = np.arange(len(edges))
+    adj = O.adjacency(n, edges)
+    ref = [O.orbit_grad_adjoint(n, edges, theta[j], p, every_edge, adj, weights=w) for j in range(3)]
+    for kw in ({"full_cone": True}, {"big_general": True}, {"shell_plain": True}, {}):
+        plan = q.Plan((n, edges), p, weights=w, **kw)
+        assert plan.info()["n_big"] > 0
+        e, g = plan.energy_grad(_params(theta))
+        for j in range(3):
+            assert abs(e[0, j].item() - ref[j][0]) <= E_REL_TOL * max(abs(ref[j][0]), 1.0), kw
+            _check_grad(g[0, j].cpu().numpy(), ref[j][1])
+        assert plan.device_status() == 0
+    plan = q.Plan((n, edges), p, weights=w)
+    plan.upload()
+    e_na = plan.energy_noalloc(_params(theta))
+    torch.cuda.synchronize()
+    for j in range(3):
+        assert abs(e_na[0, j].item() - ref[j][0]) <= E_REL_TOL * max(abs(ref[j][0]), 1.0)
+
+
 def test_weighted_cut_table_is_bit_exact(q):
     """A weighted cone's cut table: sum_e w_e [z_a != z_b] plus the total |w| of
     its negative edges (so that it stays unsigned), bit-exact."""
