@@ -62,7 +62,7 @@ enum qaoa_flags {
     QAOA_BIG_GENERAL = 8u, /* large-state cones always use the general pass
                               schedule (psi and lambda both stored), never the
                               core-tile schedule; slower, for cross-checks */
-    QAOA_CONE_CLASSES = 16u /* simulate one cone per isomorphism class of the
+    QAOA_CONE_CLASSES = 16u, /* simulate one cone per isomorphism class of the
                                graph's cones (root edge fixed setwise), weighted
                                by the class's total orbit size: edges with
                                isomorphic cones have equal terms (the argument
@@ -70,6 +70,10 @@ enum qaoa_flags {
                                local symmetries of Sec. 6); a coarser partition
                                than the Aut(G) orbits, found by a verified
                                search (qaoa_plan_cone_classes) */
+    QAOA_BLOCK_PLAIN = 32u /* keep every shell class count vector as its own
+                              block instead of one block per orbit under the
+                              cone's symmetries (qaoa_plan_blocks); slower,
+                              for cross-checks */
 };
 
 /* Largest cone handled: qubits per cone and local edges per cone. */
@@ -222,6 +226,24 @@ int qaoa_plan_cone_weights(const qaoa_plan *plan, int64_t rep, int32_t *weights)
  */
 int qaoa_plan_shell(const qaoa_plan *plan, int64_t rep, int32_t *class_of,
                     int64_t *n_blocks);
+
+/*
+ * The shell blocks one representative's cone is evolved for.  Unless the plan
+ * has QAOA_BLOCK_PLAIN, blocks related by a symmetry of the cone (a
+ * permutation of its qubits that keeps every edge and weight, every distance
+ * from the root edge and the root edge itself) are merged: such a symmetry
+ * carries one block's evolution onto the other's with the inner qubits
+ * relabelled, so both contribute the same amount to the term and to every
+ * derivative (the argument of Sec. 3, Theorem 1, inside one cone).  counts:
+ * host uint8[n_blocks * n_classes], row b = the number of shell qubits set to
+ * 1 in each class (qaoa_plan_shell's class order) for block b; weight: host
+ * double[n_blocks], the number of shell assignments block b stands for (the
+ * product of binomials times its orbit's size; the weights sum to 2^(shell
+ * qubits)).  Call with both NULL to learn n_blocks and n_classes; either
+ * output pointer may be NULL.  QAOA_E_INVALID on a bad plan or index.
+ */
+int qaoa_plan_blocks(const qaoa_plan *plan, int64_t rep, int64_t *n_blocks,
+                     int32_t *n_classes, uint8_t *counts, double *weight);
 
 /*
  * Host-only edge-orbit finder on one graph (the plan's orbit step alone),

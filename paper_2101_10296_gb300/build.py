@@ -22,7 +22,7 @@ OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libqaoa.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-HOST_SRC = ["graph.cpp", "orbits.cpp", "plan.cpp", "cone_classes.cpp"]
+HOST_SRC = ["graph.cpp", "orbits.cpp", "plan.cpp", "cone_classes.cpp", "block_orbits.cpp"]
 CUDA_SRC = ["kernels.cu", "kernels_grad.cu", "big.cu", "big_split.cu", "capi.cu", "noalloc.cu"]
 HEADERS = ["host.hpp", "device.cuh", "big.cuh", "big_common.cuh", "devplan.cuh", "cone_kernel.cuh"]
 

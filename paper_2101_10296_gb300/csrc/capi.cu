@@ -345,7 +345,20 @@ extern "C" int qaoa_plan_upload(qaoa_plan *plan) {
         d.n_blocks = c.n_blocks;
         d.n_cls = int32_t(c.shell_classes.size());
         d.cls_off = int32_t(shell_tab.size());
-        if (d.neg) {
+        if (!c.blk_counts.empty()) {
+            // explicit block list (block orbits): (shell word, multiplicity bits) per block
+            d.n_cls = -1;
+            for (size_t b = 0; b < c.blk_counts.size(); ++b) {
+                uint64_t word = d.neg;
+                for (size_t k = 0; k < c.shell_classes.size(); ++k)
+                    for (int t = 0; t < c.blk_counts[b][k]; ++t) word ^= d.col[c.shell_classes[k][size_t(t)]];
+                const float f = float(c.blk_weight[b]);
+                uint32_t bits;
+                std::memcpy(&bits, &f, sizeof bits);
+                shell_tab.push_back(word);
+                shell_tab.push_back(bits);
+            }
+        } else if (d.neg) {
             // the negative edges' constant enters every cut word once, through a
             // class of no qubits in front of the shell classes (one block, weight 1)
             const float one = 1.f;
@@ -356,7 +369,7 @@ extern "C" int qaoa_plan_upload(qaoa_plan *plan) {
             shell_tab.push_back(one_bits);
             d.n_cls += 1;
         }
-        for (const auto &cls : c.shell_classes) {
+        for (const auto &cls : c.blk_counts.empty() ? c.shell_classes : std::vector<std::vector<int32_t>>()) {
             const size_t sz = cls.size();
             shell_tab.push_back(sz);
             uint64_t pm = 0;

@@ -32,7 +32,10 @@ struct alignas(16) DevCone {
     uint64_t neg;             // bits of negative-weight edges (already in the shell table's words)
 };
 
-// Shell table, per cone from cls_off, per class c of size s: word 0 = s,
+// Shell table, per cone from cls_off.  n_cls < 0: an explicit list of
+// n_blocks (shell word, multiplicity as float bits) pairs -- the blocks left
+// after merging those related by the cone's symmetries.  Otherwise per
+// class c of size s: word 0 = s,
 // words 1..s+1 = XOR of col[] over the class's first 0..s qubits, words
 // s+2..2s+2 = binomial(s, 0..s) as float bits.  Block beta of a cone is the
 // mixed-radix number (n_0, n_1, ...) with 0 <= n_c <= s_c, least significant
@@ -40,6 +43,15 @@ struct alignas(16) DevCone {
 // n_c and its multiplicity the product of binomial(s_c, n_c).
 __device__ __forceinline__ uint64_t shell_block(const DevCone *__restrict__ C, const uint64_t *__restrict__ tab,
                                                 uint32_t beta, float &mult) {
+    if (C->n_cls < 0) {  // explicit list: (word, multiplicity bits) per block
+        if (int64_t(beta) >= C->n_blocks) {
+            mult = 0.f;
+            return 0;
+        }
+        const uint64_t *e = tab + C->cls_off + 2 * size_t(beta);
+        mult = __uint_as_float(uint32_t(e[1]));
+        return e[0];
+    }
     const uint64_t *t = tab + C->cls_off;
     uint64_t m = 0;
     float w = 1.f;

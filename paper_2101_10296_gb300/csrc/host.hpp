@@ -55,7 +55,11 @@ struct Cone {
     // Shell (never-mixed) qubits grouped by their set of inner neighbours;
     // one block per vector of per-class counts of shell qubits set to 1.
     std::vector<std::vector<int32_t>> shell_classes;
-    int64_t n_blocks = 1;  // prod over classes of (size + 1)
+    int64_t n_blocks = 1;  // prod over classes of (size + 1), or blk_counts.size()
+    // Block orbits (block_orbits.cpp): when the cone's symmetries merge blocks,
+    // one count vector per orbit and its total multiplicity; empty = every block.
+    std::vector<std::vector<uint8_t>> blk_counts;
+    std::vector<double> blk_weight;
 };
 
 // Fills cone for edge `e` of g at depth p.  full_cone: mix every qubit in
@@ -69,6 +73,9 @@ int extract_cone(const Graph &g, int64_t e, int32_t p, bool full_cone, bool shel
 // list of cones: class_of[i] = index of the first cone of i's class.
 bool cones_isomorphic(const Cone &a, const Cone &b, int p);
 void cone_classes(const std::vector<const Cone *> &cones, int p, std::vector<int32_t> &class_of);
+
+// Merges the cone's shell blocks along its symmetries (block_orbits.cpp).
+void block_orbits(Cone &c);
 
 void set_error(const std::string &msg);
 

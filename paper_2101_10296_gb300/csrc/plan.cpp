@@ -218,7 +218,8 @@ extern "C" int qaoa_plan_graphs_weighted(int32_t n_graphs, const int32_t *n_vert
         set_error("p must be in [1, QAOA_MAX_P]");
         return QAOA_E_INVALID;
     }
-    if (flags & ~uint32_t(QAOA_ORBITS | QAOA_FULL_CONE | QAOA_SHELL_PLAIN | QAOA_BIG_GENERAL | QAOA_CONE_CLASSES)) {
+    if (flags & ~uint32_t(QAOA_ORBITS | QAOA_FULL_CONE | QAOA_SHELL_PLAIN | QAOA_BIG_GENERAL | QAOA_CONE_CLASSES |
+                            QAOA_BLOCK_PLAIN)) {
         set_error("unknown flag bits");
         return QAOA_E_INVALID;
     }
@@ -361,6 +362,9 @@ extern "C" int qaoa_plan_graphs_weighted(int32_t n_graphs, const int32_t *n_vert
                 pl->cone_class[g][e] = int32_t(rep_edge_of_cone[cone_of_edge[oid[e]]]);
         }
         pl->cones.swap(kept);
+        // block orbits: shell blocks related by a symmetry of their cone
+        if (!(flags & (QAOA_SHELL_PLAIN | QAOA_BLOCK_PLAIN)))
+            parallel_for(int64_t(pl->cones.size()), [&](int64_t i, int) { block_orbits(pl->cones[i]); });
         auto t2 = std::chrono::steady_clock::now();
         pl->t_orbits = std::chrono::duration<double>(t1 - t0).count();
         pl->t_cones = std::chrono::duration<double>(t2 - t1).count();
@@ -500,6 +504,37 @@ extern "C" int qaoa_plan_shell(const qaoa_plan *plan, int64_t rep, int32_t *clas
             for (int32_t q : c.shell_classes[k]) class_of[q] = int32_t(k);
     }
     if (n_blocks) *n_blocks = c.n_blocks;
+    return QAOA_OK;
+}
+
+extern "C" int qaoa_plan_blocks(const qaoa_plan *plan, int64_t rep, int64_t *n_blocks, int32_t *n_classes,
+                                uint8_t *counts, double *weight) {
+    if (!plan || rep < 0 || rep >= int64_t(plan->cones.size())) {
+        set_error("bad plan or representative index");
+        return QAOA_E_INVALID;
+    }
+    const Cone &c = plan->cones[rep];
+    const int32_t ncls = int32_t(c.shell_classes.size());
+    if (n_blocks) *n_blocks = c.n_blocks;
+    if (n_classes) *n_classes = ncls;
+    if (!counts && !weight) return QAOA_OK;
+    for (int64_t b = 0; b < c.n_blocks; ++b) {
+        double w = 1.0;
+        if (!c.blk_counts.empty()) {
+            if (counts) std::copy(c.blk_counts[b].begin(), c.blk_counts[b].end(), counts + b * ncls);
+            w = c.blk_weight[b];
+        } else {
+            int64_t r = b;  // mixed radix, least significant class first
+            for (int32_t k = 0; k < ncls; ++k) {
+                const int s = int(c.shell_classes[k].size());
+                const int nk = int(r % (s + 1));
+                r /= s + 1;
+                if (counts) counts[b * ncls + k] = uint8_t(nk);
+                for (int i = 0; i < nk; ++i) w = w * double(s - i) / double(i + 1);
+            }
+        }
+        if (weight) weight[b] = w;
+    }
     return QAOA_OK;
 }
 

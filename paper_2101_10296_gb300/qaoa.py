@@ -28,6 +28,7 @@ FULL_CONE = 2
 SHELL_PLAIN = 4
 BIG_GENERAL = 8
 CONE_CLASSES = 16
+BLOCK_PLAIN = 32
 
 
 class QAOAError(RuntimeError):
@@ -71,6 +72,7 @@ _SIGS = {
     "qaoa_plan_reps": (C.c_int, [_P, _I32P, _I64P, _I32P, _I32P, _I32P, _I32P, _I32P]),
     "qaoa_plan_cone": (C.c_int, [_P, C.c_int64, _I32P, _I32P, _I32P]),
     "qaoa_plan_shell": (C.c_int, [_P, C.c_int64, _I32P, _I64P]),
+    "qaoa_plan_blocks": (C.c_int, [_P, C.c_int64, _I64P, _I32P, C.POINTER(C.c_uint8), C.POINTER(C.c_double)]),
     "qaoa_edge_orbits": (C.c_int, [C.c_int32, C.c_int64, _I32P, C.c_int64, _I32P, _I64P, _I64P, _F64P, _I32P]),
     "qaoa_plan_upload": (C.c_int, [_P]),
     "qaoa_cut_table": (C.c_int, [_P, C.c_int64, _P, _P]),
@@ -150,7 +152,7 @@ class Plan:
     """A planned batch of graphs (orbits + cones), owning its device copy."""
 
     def __init__(self, graphs, p, orbits=True, full_cone=False, max_cone_qubits=0, search_budget=0,
-                 shell_plain=False, big_general=False, cone_classes=False, weights=None):
+                 shell_plain=False, big_general=False, cone_classes=False, weights=None, block_plain=False):
         """graphs: (n, edges) or a list of them; weights: None (MaxCut) or one
         integer array per graph (edge weights / colours, see
         qaoa_plan_graphs_weighted)."""
@@ -169,6 +171,7 @@ class Plan:
         offs = np.asarray(offs, dtype=np.int64)
         flags = (ORBITS if orbits else ORBITS_OFF) | (FULL_CONE if full_cone else 0) | (SHELL_PLAIN if shell_plain else 0)
         flags |= (BIG_GENERAL if big_general else 0) | (CONE_CLASSES if cone_classes else 0)
+        flags |= BLOCK_PLAIN if block_plain else 0
         h = C.c_void_p()
         if weights is None:
             _check(lib().qaoa_plan_graphs(len(graphs), _ptr(nv, C.c_int32), _ptr(offs, C.c_int64),
@@ -257,6 +260,17 @@ class Plan:
         nb = C.c_int64()
         _check(lib().qaoa_plan_shell(self._h, rep, _ptr(cls, C.c_int32), C.byref(nb)))
         return cls, nb.value
+
+    def blocks(self, rep):
+        """(counts [n_blocks, n_classes] uint8, weight [n_blocks] float64): the
+        shell blocks the cone is evolved for (see qaoa_plan_blocks)."""
+        nb, nc = C.c_int64(), C.c_int32()
+        _check(lib().qaoa_plan_blocks(self._h, rep, C.byref(nb), C.byref(nc), None, None))
+        counts = np.zeros((nb.value, nc.value), dtype=np.uint8)
+        w = np.zeros(nb.value, dtype=np.float64)
+        _check(lib().qaoa_plan_blocks(self._h, rep, None, None, _ptr(counts, C.c_uint8) if counts.size else None,
+                                      _ptr(w, C.c_double)))
+        return counts, w
 
     def shell_blocks(self):
         """Number of shell blocks of every representative (plan order)."""

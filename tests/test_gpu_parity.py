@@ -550,7 +550,7 @@ def test_weighted_schedules_and_modes_agree(q):
     every_edge = np.arange(len(edges))
     adj = O.adjacency(n, edges)
     ref = [O.orbit_grad_adjoint(n, edges, theta[j], p, every_edge, adj, weights=w) for j in range(3)]
-    for kw in ({"full_cone": True}, {"big_general": True}, {"shell_plain": True}, {}):
+    for kw in ({"full_cone": True}, {"big_general": True}, {"shell_plain": True}, {"block_plain": True}, {}):
         plan = q.Plan((n, edges), p, weights=w, **kw)
         assert plan.info()["n_big"] > 0
         e, g = plan.energy_grad(_params(theta))
@@ -564,6 +564,37 @@ def test_weighted_schedules_and_modes_agree(q):
     torch.cuda.synchronize()
     for j in range(3):
         assert abs(e_na[0, j].item() - ref[j][0]) <= E_REL_TOL * max(abs(ref[j][0]), 1.0)
+
+
+@pytest.mark.parametrize("graph,p", [(I.random_regular(200, 3, 1), 2), (I.torus(8, 8), 2), (I.circulant(60, [1, 7]), 2),
+                                     (I.random_regular(24, 3, 1), 3), (I.circulant(40, [1, 5]), 3)])
+def test_block_orbits_agree_with_every_block(q, graph, p):
+    """Merging shell blocks along the cone's symmetries changes no term: the
+    default plan and the plan that evolves every class count vector give the
+    same terms, energies and gradients -- on the register kernel (cubic tree
+    cones, torus, circulant) and on the core-tile and general schedules (p = 3
+    cones with 10 to 14 inner qubits) -- and the merged plan evolves fewer
+    blocks."""
+    n, edges = graph
+    theta = I.draw_params(p, 4, 91)
+    merged = q.Plan((n, edges), p)
+    every = q.Plan((n, edges), p, block_plain=True)
+    assert merged.shell_blocks().sum() < every.shell_blocks().sum()
+    assert np.array_equal(merged.reps()["edge"], every.reps()["edge"])
+    for kw in ({}, {"big_general": True}):
+        a = merged if not kw else q.Plan((n, edges), p, **kw)
+        e0, g0, t0 = every.energy_grad(_params(theta), terms=True)
+        e1, g1, t1 = a.energy_grad(_params(theta), terms=True)
+        assert torch.max(torch.abs(t1 - t0)).item() <= 2 * TERM_TOL
+        for j in range(4):
+            assert abs(e1[0, j].item() - e0[0, j].item()) <= 2 * E_REL_TOL * max(abs(e0[0, j].item()), 1.0)
+            _check_grad(g1[0, j].cpu().numpy(), g0[0, j].cpu().numpy(), scale=2.0)
+        assert a.device_status() == 0
+    merged.upload()
+    e_na = merged.energy_noalloc(_params(theta))
+    e0 = every.energy(_params(theta))
+    torch.cuda.synchronize()
+    assert torch.allclose(e_na, e0, rtol=2 * E_REL_TOL, atol=0)
 
 
 def test_weighted_cut_table_is_bit_exact(q):

@@ -317,7 +317,7 @@ def test_plan_flags(qlib):
     assert np.array_equal(a.shell_blocks(), b.shell_blocks())
     e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32))
     h = C.c_void_p()
-    rc = qlib.lib().qaoa_plan_graph(n, len(edges), qlib._ptr(e, C.c_int32), 3, 32, 0, 0, C.byref(h))
+    rc = qlib.lib().qaoa_plan_graph(n, len(edges), qlib._ptr(e, C.c_int32), 3, 64, 0, 0, C.byref(h))
     assert rc == qlib.QAOA_E_INVALID
 
 
@@ -441,7 +441,7 @@ def test_cone_classes_have_equal_oracle_terms(qlib):
 ])
 def test_shell_classes_partition_the_shell(qlib, graph, p):
     n, edges = graph
-    plan = qlib.Plan((n, edges), p, orbits=False)
+    plan = qlib.Plan((n, edges), p, orbits=False, block_plain=True)
     plain = qlib.Plan((n, edges), p, orbits=False, shell_plain=True)
     reps = plan.reps()
     for r in range(0, len(edges), max(1, len(edges) // 20)):
@@ -465,10 +465,126 @@ def test_shell_classes_partition_the_shell(qlib, graph, p):
 def test_shell_blocks_of_known_cones(qlib):
     # random cubic graph at p = 2: tree-like cones have 4 classes of 2 -> 3^4 blocks
     n, edges = I.random_regular(2000, 3, 1)
-    nbs = [qlib.Plan((n, edges), 2, orbits=False).shell(r)[1] for r in range(50)]
+    nbs = [qlib.Plan((n, edges), 2, orbits=False, block_plain=True).shell(r)[1] for r in range(50)]
     assert max(set(nbs), key=nbs.count) == 81
     # hypercube Q_12 at p = 1: neighbours of u only and of v only -> 12 x 12 blocks
-    assert qlib.Plan(I.hypercube(12), 1).shell(0)[1] == 144
+    assert qlib.Plan(I.hypercube(12), 1, block_plain=True).shell(0)[1] == 144
+
+
+def _tree_orbits(levels, k=3):
+    """Colourings of the leaves of the tree cone with k colours each, counted
+    up to the tree's symmetries: a vertex with two exchangeable subtrees of f
+    orbits each has f (f + 1) / 2 (unordered pairs), and the root edge's two
+    ends are exchangeable too."""
+    f = k
+    for _ in range(levels):
+        f = f * (f + 1) // 2
+    return f
+
+
+def test_block_orbits_of_known_cones(qlib):
+    """Block counts after merging along the cone's symmetries, against counts
+    fixed by hand (Burnside's lemma): a tree cone of a cubic graph at depth p
+    has 2^(p+1) shell classes of two qubits hanging from a binary tree whose
+    automorphisms fixing the root edge form an iterated wreath product; Q_12
+    at p = 1 has two classes of 11 exchanged by swapping the root edge's ends,
+    so 12 x 12 count pairs fall into 12 * 13 / 2 orbits."""
+    n, edges = I.random_regular(2000, 3, 1)
+    for p, expect in ((1, 6), (2, 21), (3, 231)):
+        assert _tree_orbits(p) == expect
+        plan = qlib.Plan((n, edges), p, orbits=False)
+        reps = plan.reps()
+        tree = [r for r in range(60) if reps["n_cone_edges"][r] == reps["n_qubits"][r] - 1]
+        assert len(tree) >= 40
+        for r in tree:
+            counts, w = plan.blocks(r)
+            assert len(counts) == expect == plan.shell(r)[1]
+            assert w.sum() == 2.0 ** (reps["n_qubits"][r] - reps["n_inner"][r])
+    plan = qlib.Plan(I.hypercube(12), 1)
+    counts, w = plan.blocks(0)
+    assert len(counts) == 78 and w.sum() == 2.0 ** 22
+    # every unordered pair of counts once
+    assert sorted(tuple(sorted(c)) for c in counts.tolist()) == sorted(
+        (a, b) for a in range(12) for b in range(a, 12))
+
+
+def _block_orbits_brute(plan_plain, rep, nx):
+    """Orbits of the class count vectors under every automorphism of the cone
+    (networkx enumerates the isomorphisms of the cone onto itself that keep
+    distances from the root edge and edge weights), with each orbit's number
+    of shell assignments; None if there are too many automorphisms to list."""
+    from networkx.algorithms.isomorphism import GraphMatcher, categorical_edge_match, categorical_node_match
+    g = _cone_nx(plan_plain, rep)
+    for (a, b), x in zip(plan_plain.cone(rep)[2], plan_plain.cone_weights(rep)):
+        g.edges[int(a), int(b)]["w"] = int(x)
+    cls, _ = plan_plain.shell(rep)
+    counts, w = plan_plain.blocks(rep)
+    index = {tuple(c): i for i, c in enumerate(counts.tolist())}
+    ncls = counts.shape[1]
+    perms = []
+    gm = GraphMatcher(g, g, node_match=categorical_node_match("dist", -1), edge_match=categorical_edge_match("w", 0))
+    for k, phi in enumerate(gm.isomorphisms_iter()):
+        if k > 20000:
+            return None
+        pm = [-1] * ncls
+        for q, img in phi.items():
+            if cls[q] >= 0:
+                assert pm[cls[q]] in (-1, cls[img])
+                pm[cls[q]] = int(cls[img])
+        perms.append(pm)
+    orbit = [-1] * len(counts)
+    for b in range(len(counts)):
+        if orbit[b] >= 0:
+            continue
+        stack, orbit[b] = [b], b
+        while stack:
+            x = counts[stack.pop()]
+            for pm in perms:
+                y = [0] * ncls
+                for k in range(ncls):
+                    y[pm[k]] = int(x[k])
+                j = index[tuple(y)]
+                if orbit[j] < 0:
+                    orbit[j] = b
+                    stack.append(j)
+    total = {}
+    for b, o in enumerate(orbit):
+        total[o] = total.get(o, 0.0) + w[b]
+    return {tuple(counts[b].tolist()): total[o] for b, o in enumerate(orbit)}, total
+
+
+@pytest.mark.parametrize("graph,p,weighted", [
+    (I.petersen(), 1, False), (I.petersen(), 2, False), (I.torus(5, 5), 2, False), (I.circulant(20, [1, 4]), 1, False),
+    (I.circulant(24, [1, 5]), 2, False), (I.hypercube(4), 2, False), (I.complete_bipartite(3, 4), 1, False),
+    (I.random_regular(40, 3, 3), 2, False), (I.random_regular(30, 4, 2), 1, False), (I.random_regular(30, 3, 5), 2, True),
+])
+def test_block_orbits_match_brute_force(qlib, graph, p, weighted):
+    """The planner's merged blocks are exactly the orbits of the class count
+    vectors under the cone's full automorphism group (root edge fixed
+    setwise), each carrying its orbit's number of shell assignments."""
+    nx = pytest.importorskip("networkx")
+    n, edges = graph
+    w = np.random.default_rng(1).choice([1, 2, -1], len(edges)) if weighted else None
+    plain = qlib.Plan((n, edges), p, orbits=False, block_plain=True, weights=w)
+    plan = qlib.Plan((n, edges), p, orbits=False, weights=w)
+    checked = 0
+    for r in range(0, len(edges), max(1, len(edges) // 12)):
+        ref = _block_orbits_brute(plain, r, nx)
+        if ref is None:
+            continue
+        of_block, total = ref
+        counts, wt = plan.blocks(r)
+        assert len(counts) == len(total) == plan.shell(r)[1]
+        # one block per orbit, each with the orbit's weight
+        keys = {}
+        for c, x in zip(counts.tolist(), wt):
+            o = of_block[tuple(c)]
+            assert x == o
+            keys[tuple(c)] = x
+        assert sorted(keys.values()) == sorted(total.values())
+        assert wt.sum() == 2.0 ** (plan.reps()["n_qubits"][r] - plan.reps()["n_inner"][r])
+        checked += 1
+    assert checked >= 6
 
 
 # ------------------------------------------------------- failure injection
