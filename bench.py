@@ -5,8 +5,11 @@ Workload (one step): 4 random 3-regular graphs with n = 2000 (3000 edges,
 seeds 1-4), depth p = 2, 64 parameter points per graph drawn with the
 project's recipe, orbit reduction on, energies and gradients of all
 4 x 64 = 256 (graph, point) evaluations in one launch of the adjoint cone
-kernel.  The inputs are synthetic, shaped like the asymmetric random graphs of
-the paper's benchmark (Sec. 5).
+kernel.  Every cone is evolved as blocks of its inner qubits, one per shell
+count vector up to the cone's own symmetries (exact: blocks related by a
+symmetry contribute equally); the line also reports the rate with every
+count vector evolved (``shell_blocks``).  The inputs are synthetic, shaped like
+the asymmetric random graphs of the paper's benchmark (Sec. 5).
 
 Timing: W untimed warm-up steps, then K steps each bracketed by CUDA events on
 the launching stream, with a 512 MB L2 flush written between steps outside the
@@ -45,7 +48,7 @@ N_VERT, DEG, P_DEPTH, N_POINTS = 2000, 3, 2, 64
 # DRAM bytes per launch of the adjoint cone kernel from one ncu capture of this
 # workload, with the hash of the kernel source they were taken on (a changed
 # kernel reports null until it is profiled again).
-TRAFFIC = {"kernels_sha1": "63d7d23cf44647f9bc34100c5d1ad46739345cd4", "bytes_per_launch": 7900000}
+TRAFFIC = {"kernels_sha1": "b71ffac90a385dfd11796e17c6dbab9844a8f461", "bytes_per_launch": 8400000}
 
 
 def log(*a):
@@ -397,6 +400,13 @@ def run_ours(args, rank, world, local_rank):
     plain = qaoa.Plan(graphs, p, orbits=False)
     plain.upload()
     plain_ms = timed(lambda: plain.energy_grad(params))
+    # every shell count vector evolved as its own block (no merging by the cones' symmetries)
+    every = qaoa.Plan(graphs, p, block_plain=True)
+    every.upload()
+    every_ms = timed(lambda: every.energy_grad(params))
+    blocks = {"merged": int(reps["n_blocks"].sum()), "every_count_vector": int(every.shell_blocks().sum()),
+              "every_block_evals_per_s": world * evals / (every_ms / 1e3)}
+    every.close()
     # local-symmetry reduction: one cone per isomorphism class of cones
     t_cc = time.perf_counter()
     ccplan = qaoa.Plan(graphs, p, cone_classes=True)
@@ -467,6 +477,7 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clocks,
         "energy_only_evals_per_s": world * evals / (energy_ms / 1e3),
         "plain_all_edge_evals_per_s": world * evals / (plain_ms / 1e3),
+        "shell_blocks": blocks,
         "training": training,
         "cone_classes": {"n_classes": int(ccplan.info()["n_reps"]), "plan_s": t_cc,
                          "energy_grad_evals_per_s": world * evals / (cc_ms / 1e3),
@@ -575,8 +586,9 @@ def run_suite(args):
     device = torch.device("cuda", 0)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=device)
 
-    def timed(fn, reps=3):
-        fn()
+    def timed(fn, reps=3, warmup=3):
+        for _ in range(warmup):
+            fn()
         torch.cuda.synchronize()
         out = []
         for k in range(reps):
@@ -606,6 +618,11 @@ def run_suite(args):
         ms_g = timed(lambda: plan.energy_grad(params))
         ms_e = timed(lambda: plan.energy(params))
         ms_pg = timed(lambda: plain.energy_grad(params))
+        every = qaoa.Plan(graphs, p, weights=wts, block_plain=True)  # every shell count vector its own block
+        every.upload()
+        ms_bp = timed(lambda: every.energy_grad(params))
+        blocks_every = int(every.shell_blocks().sum())
+        every.close()
         ccplan = qaoa.Plan(graphs, p, cone_classes=True, weights=wts)
         ccplan.upload()
         ms_cc = timed(lambda: ccplan.energy_grad(params))
@@ -649,6 +666,8 @@ def run_suite(args):
             "large_state_cones": int(info["n_big"]), "plan_s": t_plan, "t_orbits_s": info["t_orbits_s"],
             "energy_grad_evals_per_s": evals / (ms_g / 1e3), "energy_evals_per_s": evals / (ms_e / 1e3),
             "plain_energy_grad_evals_per_s": evals / (ms_pg / 1e3),
+            "shell_blocks": int(reps["n_blocks"].sum()), "shell_blocks_every_count_vector": blocks_every,
+            "every_block_energy_grad_evals_per_s": evals / (ms_bp / 1e3),
             "cone_class_reps": int(ccplan.info()["n_reps"]),
             "cone_class_energy_grad_evals_per_s": evals / (ms_cc / 1e3),
             "cone_class_max_rel_energy_diff": float(np.max(np.abs(e_cc - e_gpu) / np.abs(e_gpu))),

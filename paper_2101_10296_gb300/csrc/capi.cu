@@ -29,8 +29,10 @@ void free_work(DevWork &w) {
 }
 
 // Builds the slot list for R register qubits over the given plan indices:
-// cones sorted by (T_c descending, graph, plan order), each starting at an
-// offset aligned to min(T_c, 32); a new graph starts on a fresh warp.
+// cones sorted by (G_c = 2^max(n_in - R, 0) descending, graph, plan order)
+// and packed back to back, T_c slots each (a multiple of G_c, so every cone
+// starts at a multiple of its own G_c and its lane-qubit groups never
+// straddle a cone boundary); a new graph starts on a fresh warp.
 int build_work(const std::vector<DevCone> &hc, const std::vector<int32_t> &idx, int R, DevWork &w) {
     std::vector<int32_t> order(idx);
     auto G = [&](int32_t i) { return int64_t(1) << std::max(hc[i].n_in - R, 0); };
