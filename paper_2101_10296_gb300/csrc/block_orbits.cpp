@@ -1,25 +1,40 @@
-// Block orbits: shell blocks related by a symmetry of the cone contribute
-// equally.
+// Block merging: shell blocks whose evolutions are related contribute
+// equally, and are evolved once.
 //
-// A cone's term is a sum over its shell blocks (one per vector of per-class
-// counts of shell qubits set to 1, weighted by the product of binomials).  A
-// permutation of the cone's qubits that maps edges onto edges of the same
-// weight, keeps every distance from the root edge and maps the root edge
-// onto itself carries the evolution of block b onto that of its image, with
-// the inner qubits relabelled: Z_0 Z_1, the cut value C and the mixers are
-// all unchanged by it, so the block's share of the term and of every
-// derivative (sums over all qubits of a layer) is the same -- Theorem 1's
-// argument (Sec. 3) inside one cone.  On shell classes such a permutation
-// acts as a permutation of classes of equal size with equal neighbourhoods'
-// images, i.e. as an automorphism of the small "class graph": the inner
-// qubits plus one vertex per class, joined to the class's inner neighbours.
-// Generators of its automorphism group are found by backtracking (with a
-// budget: any set of genuine automorphisms gives valid merges), blocks are
-// merged along them by union-find, and one block per orbit is kept with the
-// orbit's total multiplicity.
+// A cone's term is a sum over its shell blocks (one per vector n of per-class
+// counts of shell qubits set to 1, weighted by the product of binomials).
+// Three exact relations between blocks are used.
+//
+// 1. The phase vector.  A shell qubit with value t adds sum_q w_q [z_q != t]
+//    over its inner neighbours q; a class of s such qubits with n of them 1
+//    adds n W + (s - 2n) sum_q w_q z_q, with W = sum_q w_q.  So up to a
+//    constant (a global phase of the block, which leaves its expectation and
+//    every derivative unchanged) block n sees the inner cut function
+//    C_in(z) + sum_q c_q z_q with c_q = sum_k (s_k - 2 n_k) w_kq: blocks with
+//    the same integer vector c evolve identically.
+// 2. Symmetries of the cone.  A permutation of the cone's qubits that maps
+//    edges onto edges of the same weight, keeps every distance from the root
+//    edge and maps the root edge onto itself carries block c onto block
+//    c o pi^-1 with the inner qubits relabelled: Z_0 Z_1, C and the mixers
+//    are unchanged by it, so both contribute the same to the term and to
+//    every derivative (sums over all qubits of a layer) -- Theorem 1's
+//    argument (Sec. 3) inside one cone.  Such permutations act on shell
+//    classes as automorphisms of a small "class graph" (the inner qubits plus
+//    one vertex per class, joined to the class's inner neighbours), and each
+//    of those lifts back, since the members of a class are interchangeable.
+// 3. The global spin flip.  Flipping every bit leaves any cut value, the
+//    mixers, |+>^n and Z_0 Z_1 unchanged; it maps block c onto block -c
+//    (C_in(~z) = C_in(z) and sum_q c_q (1 - z_q) = const - sum_q c_q z_q).
+//
+// Generators of the class graph's automorphism group are found by
+// backtracking (with a budget: any set of genuine automorphisms gives valid
+// merges), phase vectors are merged along them and along c -> -c by
+// union-find, and one count vector per orbit is kept with the orbit's total
+// number of shell assignments.
 #include <algorithm>
 #include <cstdint>
 #include <numeric>
+#include <unordered_map>
 #include <vector>
 
 #include "host.hpp"
@@ -145,6 +160,17 @@ struct Enumerator {
     }
 };
 
+struct VecHash {
+    size_t operator()(const std::vector<int32_t> &v) const {
+        uint64_t h = 0x9e3779b97f4a7c15ull;
+        for (int32_t x : v) {
+            h ^= uint64_t(uint32_t(x)) + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
+            h *= 0xff51afd7ed558ccdull;
+        }
+        return size_t(h ^ (h >> 33));
+    }
+};
+
 int64_t find(std::vector<int64_t> &parent, int64_t x) {
     while (parent[x] != x) x = parent[x] = parent[parent[x]];
     return x;
@@ -157,53 +183,82 @@ void block_orbits(Cone &c) {
     c.blk_weight.clear();
     const int ncls = int(c.shell_classes.size());
     if (ncls == 0 || c.n_blocks < 2 || c.n_blocks > kMaxBlocks) return;
-    const ClassGraph g = class_graph(c);
-    Enumerator en(g);
-    en.run();
-    // their action on the classes; those that move no class act trivially on blocks
-    std::vector<std::vector<int>> perms;
-    for (const auto &a : en.gens) {
-        std::vector<int> pm(static_cast<size_t>(ncls));
-        bool moves = false;
-        for (int k = 0; k < ncls; ++k) {
-            pm[k] = a[g.n_in + k] - g.n_in;
-            moves |= pm[k] != k;
-        }
-        if (moves) perms.push_back(pm);
+    const int n_in = c.n_in;
+    // inner neighbours of each class with their weights (shared by its members)
+    std::vector<int> cls_of(size_t(c.n), -1);
+    for (int k = 0; k < ncls; ++k)
+        for (int32_t q : c.shell_classes[k]) cls_of[q] = k;
+    std::vector<std::vector<std::pair<int, int>>> nbr(static_cast<size_t>(ncls));
+    for (size_t e = 0; e < c.ea.size(); ++e) {
+        int a = c.ea[e], b = c.eb[e];
+        if (a < n_in) std::swap(a, b);
+        if (a < n_in || b >= n_in) continue;  // inner-inner (shell-shell edges are not kept)
+        if (c.shell_classes[cls_of[a]][0] == a) nbr[cls_of[a]].emplace_back(b, c.ew[e]);
     }
-    if (perms.empty()) return;
-    // blocks as mixed-radix numbers, least significant class first (the device order)
+    // the phase vector of every count vector, and its number of shell assignments
     std::vector<int64_t> radix(size_t(ncls) + 1, 1);
     for (int k = 0; k < ncls; ++k) radix[k + 1] = radix[k] * int64_t(c.shell_classes[k].size() + 1);
     const int64_t nb = c.n_blocks;
-    std::vector<int64_t> parent(static_cast<size_t>(nb));
-    std::iota(parent.begin(), parent.end(), 0);
-    std::vector<int> digit(static_cast<size_t>(ncls));
+    std::unordered_map<std::vector<int32_t>, int64_t, VecHash> id_of;  // phase vector -> id
+    std::vector<std::vector<int32_t>> vec;                             // id -> phase vector
+    std::vector<int64_t> first;                                        // id -> first count vector
+    std::vector<double> weight;                                        // id -> shell assignments
+    std::vector<int32_t> cv(static_cast<size_t>(n_in));
     for (int64_t b = 0; b < nb; ++b) {
-        for (int k = 0; k < ncls; ++k) digit[k] = int((b / radix[k]) % int64_t(c.shell_classes[k].size() + 1));
-        for (const auto &pm : perms) {
-            int64_t image = 0;
-            for (int k = 0; k < ncls; ++k) image += int64_t(digit[k]) * radix[pm[k]];
-            const int64_t ra = find(parent, b), rb = find(parent, image);
-            if (ra != rb) parent[std::max(ra, rb)] = std::min(ra, rb);
-        }
-    }
-    std::vector<int64_t> size(size_t(nb), 0);
-    for (int64_t b = 0; b < nb; ++b) size[find(parent, b)]++;
-    for (int64_t b = 0; b < nb; ++b) {
-        if (find(parent, b) != b) continue;
-        std::vector<uint8_t> cnt(static_cast<size_t>(ncls));
+        std::fill(cv.begin(), cv.end(), 0);
         double mult = 1.0;
         for (int k = 0; k < ncls; ++k) {
             const int s = int(c.shell_classes[k].size());
             const int nk = int((b / radix[k]) % int64_t(s + 1));
-            cnt[k] = uint8_t(nk);
+            for (const auto &qw : nbr[k]) cv[qw.first] += (s - 2 * nk) * qw.second;
             double bin = 1.0;  // binomial(s, nk), exact in double for s <= 32
             for (int i = 0; i < nk; ++i) bin = bin * double(s - i) / double(i + 1);
             mult *= bin;
         }
+        auto it = id_of.find(cv);
+        if (it == id_of.end()) {
+            it = id_of.emplace(cv, int64_t(vec.size())).first;
+            vec.push_back(cv);
+            first.push_back(b);
+            weight.push_back(0.0);
+        }
+        weight[size_t(it->second)] += mult;
+    }
+    // merge phase vectors along the symmetries: c -> c o pi^-1 for the
+    // generators pi, and c -> -c (the global spin flip)
+    const ClassGraph g = class_graph(c);
+    Enumerator en(g);
+    en.run();
+    const int64_t nid = int64_t(vec.size());
+    std::vector<int64_t> parent(static_cast<size_t>(nid));
+    std::iota(parent.begin(), parent.end(), 0);
+    auto unite = [&](int64_t x, const std::vector<int32_t> &img) {
+        const auto it = id_of.find(img);
+        if (it == id_of.end()) return;  // cannot happen for genuine symmetries
+        const int64_t ra = find(parent, x), rb = find(parent, it->second);
+        if (ra != rb) parent[std::max(ra, rb)] = std::min(ra, rb);
+    };
+    std::vector<int32_t> img(static_cast<size_t>(n_in));
+    for (int64_t i = 0; i < nid; ++i) {
+        for (const auto &pi : en.gens) {
+            for (int q = 0; q < n_in; ++q) img[pi[q]] = vec[i][q];
+            unite(i, img);
+        }
+        for (int q = 0; q < n_in; ++q) img[q] = -vec[i][q];
+        unite(i, img);
+    }
+    std::vector<double> total(static_cast<size_t>(nid), 0.0);
+    for (int64_t i = 0; i < nid; ++i) total[find(parent, i)] += weight[i];
+    int64_t n_orbits = 0;
+    for (int64_t i = 0; i < nid; ++i) n_orbits += find(parent, i) == i;
+    if (n_orbits == nb) return;  // nothing merged: keep the class table
+    for (int64_t i = 0; i < nid; ++i) {
+        if (find(parent, i) != i) continue;
+        std::vector<uint8_t> cnt(static_cast<size_t>(ncls));
+        for (int k = 0; k < ncls; ++k)
+            cnt[k] = uint8_t((first[i] / radix[k]) % int64_t(c.shell_classes[k].size() + 1));
         c.blk_counts.push_back(std::move(cnt));
-        c.blk_weight.push_back(mult * double(size[b]));
+        c.blk_weight.push_back(total[i]);
     }
     c.n_blocks = int64_t(c.blk_counts.size());
 }

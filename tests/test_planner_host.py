@@ -471,27 +471,55 @@ def test_shell_blocks_of_known_cones(qlib):
     assert qlib.Plan(I.hypercube(12), 1, block_plain=True).shell(0)[1] == 144
 
 
-def _tree_orbits(levels, k=3):
-    """Colourings of the leaves of the tree cone with k colours each, counted
-    up to the tree's symmetries: a vertex with two exchangeable subtrees of f
-    orbits each has f (f + 1) / 2 (unordered pairs), and the root edge's two
-    ends are exchangeable too."""
-    f = k
-    for _ in range(levels):
-        f = f * (f + 1) // 2
-    return f
+def _orbit_count(vectors, generators):
+    """Number of orbits of a finite set of tuples under the group the given
+    maps (tuple -> tuple) generate, by breadth-first search."""
+    seen, count = set(), 0
+    for v in vectors:
+        if v in seen:
+            continue
+        count += 1
+        seen.add(v)
+        stack = [v]
+        while stack:
+            x = stack.pop()
+            for gen in generators:
+                y = gen(x)
+                if y not in seen:
+                    seen.add(y)
+                    stack.append(y)
+    return count
+
+
+def _tree_orbits(p):
+    """Blocks of a tree cone of a cubic graph at depth p after merging: the
+    2^p leaf classes (two shell qubits under each inner qubit at distance
+    p - 1) give the phase vector entries 2 - 2 n_k in {2, 0, -2}; the cone's
+    symmetries exchange the two subtrees below any inner vertex and the two
+    ends of the root edge (a complete binary tree over the leaf classes); the
+    global spin flip negates the vector."""
+    L = 1 << p
+    gens = [lambda v: tuple(-x for x in v)]
+    for size in (L >> d for d in range(p)):  # subtree sizes L, L/2, ..., 2
+        for off in range(0, L, size):
+            def swap(v, off=off, h=size // 2):
+                v = list(v)
+                v[off:off + h], v[off + h:off + 2 * h] = v[off + h:off + 2 * h], v[off:off + h]
+                return tuple(v)
+            gens.append(swap)
+    return _orbit_count(itertools.product((2, 0, -2), repeat=L), gens)
 
 
 def test_block_orbits_of_known_cones(qlib):
-    """Block counts after merging along the cone's symmetries, against counts
-    fixed by hand (Burnside's lemma): a tree cone of a cubic graph at depth p
-    has 2^(p+1) shell classes of two qubits hanging from a binary tree whose
-    automorphisms fixing the root edge form an iterated wreath product; Q_12
-    at p = 1 has two classes of 11 exchanged by swapping the root edge's ends,
-    so 12 x 12 count pairs fall into 12 * 13 / 2 orbits."""
+    """Block counts after merging, against counts from an independent orbit
+    enumeration: a tree cone of a cubic graph at depth p (binary-tree
+    symmetries plus the spin flip, 3^(2^p) count vectors); Q_12 at p = 1 (two
+    classes of 11 exchanged by swapping the root edge's ends, phase entries
+    11 - 2n odd, so the flip fixes nothing: (144 + 12 + 0 + 12) / 4 = 42)."""
+    assert [_tree_orbits(p) for p in (1, 2)] == [4, 13]  # Burnside by hand: 16 / 4, 208 / 16
     n, edges = I.random_regular(2000, 3, 1)
-    for p, expect in ((1, 6), (2, 21), (3, 231)):
-        assert _tree_orbits(p) == expect
+    for p in (1, 2, 3):
+        expect = _tree_orbits(p)
         plan = qlib.Plan((n, edges), p, orbits=False)
         reps = plan.reps()
         tree = [r for r in range(60) if reps["n_cone_edges"][r] == reps["n_qubits"][r] - 1]
@@ -502,26 +530,67 @@ def test_block_orbits_of_known_cones(qlib):
             assert w.sum() == 2.0 ** (reps["n_qubits"][r] - reps["n_inner"][r])
     plan = qlib.Plan(I.hypercube(12), 1)
     counts, w = plan.blocks(0)
-    assert len(counts) == 78 and w.sum() == 2.0 ** 22
-    # every unordered pair of counts once
-    assert sorted(tuple(sorted(c)) for c in counts.tolist()) == sorted(
-        (a, b) for a in range(12) for b in range(a, 12))
+    assert len(counts) == 42 and w.sum() == 2.0 ** 22
+
+
+def _phase_vector(plan, rep, counts):
+    """The coefficient of z_q in the shell edges' part of the cut, for the
+    assignment that sets the first n_k members of each class to 1: a shell
+    neighbour t of q adds w [z_q != t] = w t + w (1 - 2t) z_q."""
+    verts, dist, ce = plan.cone(rep)
+    cw = plan.cone_weights(rep)
+    cls, _ = plan.shell(rep)
+    n_in = int(plan.reps()["n_inner"][rep])
+    bits = _shell_bits(cls, counts)
+    c = [0] * n_in
+    for (a, b), w in zip(ce.tolist(), cw.tolist()):
+        if a >= n_in:
+            a, b = b, a
+        if a < n_in <= b:
+            c[a] += w * (1 - 2 * bits[b])
+    return tuple(c)
+
+
+def _shell_bits(cls, counts):
+    bits, seen = {}, {}
+    for q, k in enumerate(cls):
+        if k >= 0:
+            bits[q] = 1 if seen.get(k, 0) < counts[k] else 0
+            seen[k] = seen.get(k, 0) + 1
+    return bits
 
 
 def _block_orbits_brute(plan_plain, rep, nx):
-    """Orbits of the class count vectors under every automorphism of the cone
-    (networkx enumerates the isomorphisms of the cone onto itself that keep
-    distances from the root edge and edge weights), with each orbit's number
-    of shell assignments; None if there are too many automorphisms to list."""
+    """Merged blocks from first principles: count vectors with equal phase
+    vectors, count vectors related by an automorphism of the cone (networkx
+    enumerates every isomorphism of the cone onto itself that keeps distances
+    from the root edge and edge weights), and complementary count vectors
+    (s - n, the global spin flip) fall together; returns, per count vector,
+    the total number of shell assignments of its class, or None if there are
+    too many automorphisms to list."""
     from networkx.algorithms.isomorphism import GraphMatcher, categorical_edge_match, categorical_node_match
     g = _cone_nx(plan_plain, rep)
     for (a, b), x in zip(plan_plain.cone(rep)[2], plan_plain.cone_weights(rep)):
         g.edges[int(a), int(b)]["w"] = int(x)
     cls, _ = plan_plain.shell(rep)
     counts, w = plan_plain.blocks(rep)
-    index = {tuple(c): i for i, c in enumerate(counts.tolist())}
+    rows = [tuple(c) for c in counts.tolist()]
+    index = {c: i for i, c in enumerate(rows)}
     ncls = counts.shape[1]
-    perms = []
+    sizes = np.bincount(cls[cls >= 0], minlength=ncls)
+    parent = list(range(len(rows)))
+
+    def find(x):
+        while parent[x] != x:
+            parent[x] = parent[parent[x]]
+            x = parent[x]
+        return x
+
+    def union(a, b):
+        a, b = find(a), find(b)
+        if a != b:
+            parent[max(a, b)] = min(a, b)
+
     gm = GraphMatcher(g, g, node_match=categorical_node_match("dist", -1), edge_match=categorical_edge_match("w", 0))
     for k, phi in enumerate(gm.isomorphisms_iter()):
         if k > 20000:
@@ -529,39 +598,36 @@ def _block_orbits_brute(plan_plain, rep, nx):
         pm = [-1] * ncls
         for q, img in phi.items():
             if cls[q] >= 0:
-                assert pm[cls[q]] in (-1, cls[img])
                 pm[cls[q]] = int(cls[img])
-        perms.append(pm)
-    orbit = [-1] * len(counts)
-    for b in range(len(counts)):
-        if orbit[b] >= 0:
-            continue
-        stack, orbit[b] = [b], b
-        while stack:
-            x = counts[stack.pop()]
-            for pm in perms:
-                y = [0] * ncls
-                for k in range(ncls):
-                    y[pm[k]] = int(x[k])
-                j = index[tuple(y)]
-                if orbit[j] < 0:
-                    orbit[j] = b
-                    stack.append(j)
+        for i, x in enumerate(rows):
+            y = [0] * ncls
+            for j in range(ncls):
+                y[pm[j]] = x[j]
+            union(i, index[tuple(y)])
+    by_vec = {}
+    for i, x in enumerate(rows):
+        union(i, index[tuple(int(s) - v for s, v in zip(sizes, x))])
+        by_vec.setdefault(_phase_vector(plan_plain, rep, x), []).append(i)
+    for members in by_vec.values():
+        for i in members[1:]:
+            union(members[0], i)
     total = {}
-    for b, o in enumerate(orbit):
-        total[o] = total.get(o, 0.0) + w[b]
-    return {tuple(counts[b].tolist()): total[o] for b, o in enumerate(orbit)}, total
+    for i in range(len(rows)):
+        total[find(i)] = total.get(find(i), 0.0) + w[i]
+    return {x: total[find(i)] for i, x in enumerate(rows)}, total
 
 
 @pytest.mark.parametrize("graph,p,weighted", [
     (I.petersen(), 1, False), (I.petersen(), 2, False), (I.torus(5, 5), 2, False), (I.circulant(20, [1, 4]), 1, False),
     (I.circulant(24, [1, 5]), 2, False), (I.hypercube(4), 2, False), (I.complete_bipartite(3, 4), 1, False),
     (I.random_regular(40, 3, 3), 2, False), (I.random_regular(30, 4, 2), 1, False), (I.random_regular(30, 3, 5), 2, True),
+    (I.erdos_renyi(30, 0.2, 3), 1, False), (I.erdos_renyi(30, 0.2, 4), 1, True),
 ])
 def test_block_orbits_match_brute_force(qlib, graph, p, weighted):
-    """The planner's merged blocks are exactly the orbits of the class count
-    vectors under the cone's full automorphism group (root edge fixed
-    setwise), each carrying its orbit's number of shell assignments."""
+    """The planner's merged blocks are exactly the classes of count vectors
+    under equal phase vectors, the cone's full automorphism group (root edge
+    fixed setwise) and the spin flip, each carrying its class's number of
+    shell assignments."""
     nx = pytest.importorskip("networkx")
     n, edges = graph
     w = np.random.default_rng(1).choice([1, 2, -1], len(edges)) if weighted else None
@@ -575,16 +641,71 @@ def test_block_orbits_match_brute_force(qlib, graph, p, weighted):
         of_block, total = ref
         counts, wt = plan.blocks(r)
         assert len(counts) == len(total) == plan.shell(r)[1]
-        # one block per orbit, each with the orbit's weight
-        keys = {}
+        got = sorted(wt.tolist())
         for c, x in zip(counts.tolist(), wt):
-            o = of_block[tuple(c)]
-            assert x == o
-            keys[tuple(c)] = x
-        assert sorted(keys.values()) == sorted(total.values())
+            assert x == of_block[tuple(c)]
+        assert got == sorted(total.values())
         assert wt.sum() == 2.0 ** (plan.reps()["n_qubits"][r] - plan.reps()["n_inner"][r])
         checked += 1
     assert checked >= 6
+
+
+def _block_zz(plan, rep, counts, theta, p):
+    """<Z_0 Z_1> of one shell block, simulated from the definition: the inner
+    qubits start in |+>, the shell qubits hold the assignment (first n_k
+    members of class k set to 1); each layer applies exp(-i gamma C) with C
+    the weighted cut of the cone's edges and then exp(-i beta X) on the inner
+    qubits within distance p - l of the edge (the pruned circuit, Sec. 2.3)."""
+    verts, dist, ce = plan.cone(rep)
+    cw = plan.cone_weights(rep)
+    cls, _ = plan.shell(rep)
+    n_in = int(plan.reps()["n_inner"][rep])
+    bits = _shell_bits(cls, counts)
+    z = np.arange(1 << n_in, dtype=np.int64)
+    C = np.zeros(z.size)
+    for (a, b), w in zip(ce.tolist(), cw.tolist()):
+        za = (z >> a) & 1 if a < n_in else bits[a]
+        zb = (z >> b) & 1 if b < n_in else bits[b]
+        C += w * (za != zb)
+    psi = np.full(z.size, 2.0 ** (-n_in / 2), dtype=np.complex128)
+    g, b = theta[:p], theta[p:]
+    for l in range(p):
+        psi = psi * np.exp(-1j * g[l] * C)
+        for q in range(n_in):
+            if dist[q] <= p - 1 - l:
+                psi = O.apply_rx(psi, q, b[l])
+    return float(np.sum(np.abs(psi) ** 2 * (1 - 2 * (((z >> 0) ^ (z >> 1)) & 1))))
+
+
+@pytest.mark.parametrize("graph,p,weighted", [(I.torus(5, 5), 2, False), (I.random_regular(30, 3, 5), 2, True),
+                                              (I.erdos_renyi(24, 0.25, 3), 1, False), (I.circulant(24, [1, 5]), 2, False)])
+def test_merged_blocks_have_equal_contributions(qlib, graph, p, weighted):
+    """Every count vector merged into a block has the same <Z_0 Z_1> as the
+    block's own (simulated from the definition in FP64), and the merged
+    blocks weighted by their shell assignments give the oracle's term."""
+    n, edges = graph
+    w = np.random.default_rng(1).choice([1, 2, -1], len(edges)) if weighted else None
+    plain = qlib.Plan((n, edges), p, orbits=False, block_plain=True, weights=w)
+    plan = qlib.Plan((n, edges), p, orbits=False, weights=w)
+    theta = I.draw_params(p, 1, 5)[0]
+    adj = O.adjacency(n, edges)
+    merged_any = False
+    for r in range(0, len(edges), max(1, len(edges) // 5)):
+        counts, wt = plan.blocks(r)
+        all_counts, all_w = plain.blocks(r)
+        if len(counts) < len(all_counts):
+            merged_any = True
+        vals = {tuple(c): _block_zz(plain, r, c, theta, p) for c in all_counts.tolist()}
+        rep_vals = [_block_zz(plan, r, c, theta, p) for c in counts.tolist()]
+        # each count vector's value equals that of a kept block with the same class weight
+        kept = sorted(zip(rep_vals, wt.tolist()))
+        for c, x in zip(all_counts.tolist(), all_w):
+            assert any(abs(vals[tuple(c)] - v) <= 1e-12 for v, _ in kept)
+        shell = plan.reps()["n_qubits"][r] - plan.reps()["n_inner"][r]
+        term = float(np.dot(rep_vals, wt)) / 2.0 ** shell
+        ref = O.lightcone_term(n, edges, edges[plan.reps()["edge"][r]], theta, p, adj, weights=w)
+        assert abs(term - ref) <= 1e-12
+    assert merged_any
 
 
 # ------------------------------------------------------- failure injection
