@@ -71,9 +71,9 @@ enum qaoa_flags {
                                than the Aut(G) orbits, found by a verified
                                search (qaoa_plan_cone_classes) */
     QAOA_BLOCK_PLAIN = 32u /* keep every shell class count vector as its own
-                              block instead of one block per orbit under the
-                              cone's symmetries (qaoa_plan_blocks); slower,
-                              for cross-checks */
+                              block instead of merging those that contribute
+                              equally (qaoa_plan_blocks); slower, for
+                              cross-checks */
 };
 
 /* Largest cone handled: qubits per cone and local edges per cone. */
@@ -229,18 +229,22 @@ int qaoa_plan_shell(const qaoa_plan *plan, int64_t rep, int32_t *class_of,
 
 /*
  * The shell blocks one representative's cone is evolved for.  Unless the plan
- * has QAOA_BLOCK_PLAIN, blocks related by a symmetry of the cone (a
- * permutation of its qubits that keeps every edge and weight, every distance
- * from the root edge and the root edge itself) are merged: such a symmetry
- * carries one block's evolution onto the other's with the inner qubits
- * relabelled, so both contribute the same amount to the term and to every
- * derivative (the argument of Sec. 3, Theorem 1, inside one cone).  counts:
- * host uint8[n_blocks * n_classes], row b = the number of shell qubits set to
- * 1 in each class (qaoa_plan_shell's class order) for block b; weight: host
- * double[n_blocks], the number of shell assignments block b stands for (the
- * product of binomials times its orbit's size; the weights sum to 2^(shell
- * qubits)).  Call with both NULL to learn n_blocks and n_classes; either
- * output pointer may be NULL.  QAOA_E_INVALID on a bad plan or index.
+ * has QAOA_BLOCK_PLAIN, count vectors that contribute equally are merged into
+ * one block: (1) those with the same phase vector c_q = sum_k (s_k - 2 n_k)
+ * w_kq (a class of s shell qubits with n set to 1 adds n W + (s - 2n) times
+ * the weighted sum of its inner neighbours' bits to the cut, so c fixes the
+ * block's evolution up to a global phase); (2) those related by a symmetry of
+ * the cone (a permutation of its qubits that keeps every edge and weight,
+ * every distance from the root edge and the root edge itself), which carries
+ * one block's evolution onto the other's with the inner qubits relabelled
+ * (the argument of Sec. 3, Theorem 1, inside one cone); (3) c and -c (the
+ * global spin flip leaves the cut, the mixers, |+> and Z_u Z_v unchanged).
+ * counts: host uint8[n_blocks * n_classes], row b = the number of shell
+ * qubits set to 1 in each class (qaoa_plan_shell's class order) for the
+ * block evolved; weight: host double[n_blocks], the number of shell
+ * assignments block b stands for (the weights sum to 2^(shell qubits)).
+ * Call with both NULL to learn n_blocks and n_classes; either output pointer
+ * may be NULL.  QAOA_E_INVALID on a bad plan or index.
  */
 int qaoa_plan_blocks(const qaoa_plan *plan, int64_t rep, int64_t *n_blocks,
                      int32_t *n_classes, uint8_t *counts, double *weight);

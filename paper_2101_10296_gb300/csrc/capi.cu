@@ -348,7 +348,7 @@ extern "C" int qaoa_plan_upload(qaoa_plan *plan) {
         d.n_cls = int32_t(c.shell_classes.size());
         d.cls_off = int32_t(shell_tab.size());
         if (!c.blk_counts.empty()) {
-            // explicit block list (block orbits): (shell word, multiplicity bits) per block
+            // explicit block list (merged blocks): (shell word, multiplicity bits) per block
             d.n_cls = -1;
             for (size_t b = 0; b < c.blk_counts.size(); ++b) {
                 uint64_t word = d.neg;

@@ -56,7 +56,7 @@ struct Cone {
     // one block per vector of per-class counts of shell qubits set to 1.
     std::vector<std::vector<int32_t>> shell_classes;
     int64_t n_blocks = 1;  // prod over classes of (size + 1), or blk_counts.size()
-    // Block orbits (block_orbits.cpp): when the cone's symmetries merge blocks,
+    // Block merging (block_orbits.cpp): when blocks that contribute equally merge,
     // one count vector per orbit and its total multiplicity; empty = every block.
     std::vector<std::vector<uint8_t>> blk_counts;
     std::vector<double> blk_weight;
@@ -74,7 +74,7 @@ int extract_cone(const Graph &g, int64_t e, int32_t p, bool full_cone, bool shel
 bool cones_isomorphic(const Cone &a, const Cone &b, int p);
 void cone_classes(const std::vector<const Cone *> &cones, int p, std::vector<int32_t> &class_of);
 
-// Merges the cone's shell blocks along its symmetries (block_orbits.cpp).
+// Merges the cone's shell blocks that contribute equally (block_orbits.cpp).
 void block_orbits(Cone &c);
 
 void set_error(const std::string &msg);

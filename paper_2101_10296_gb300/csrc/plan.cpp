@@ -362,7 +362,8 @@ extern "C" int qaoa_plan_graphs_weighted(int32_t n_graphs, const int32_t *n_vert
                 pl->cone_class[g][e] = int32_t(rep_edge_of_cone[cone_of_edge[oid[e]]]);
         }
         pl->cones.swap(kept);
-        // block orbits: shell blocks related by a symmetry of their cone
+        // block merging: shell blocks that contribute equally (phase vectors,
+        // symmetries of the cone, the global spin flip)
         if (!(flags & (QAOA_SHELL_PLAIN | QAOA_BLOCK_PLAIN)))
             parallel_for(int64_t(pl->cones.size()), [&](int64_t i, int) { block_orbits(pl->cones[i]); });
         auto t2 = std::chrono::steady_clock::now();
