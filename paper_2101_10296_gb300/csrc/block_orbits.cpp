@@ -12,25 +12,25 @@
 //    every derivative unchanged) block n sees the inner cut function
 //    C_in(z) + sum_q c_q z_q with c_q = sum_k (s_k - 2 n_k) w_kq: blocks with
 //    the same integer vector c evolve identically.
-// 2. Symmetries of the cone.  A permutation of the cone's qubits that maps
-//    edges onto edges of the same weight, keeps every distance from the root
-//    edge and maps the root edge onto itself carries block c onto block
-//    c o pi^-1 with the inner qubits relabelled: Z_0 Z_1, C and the mixers
-//    are unchanged by it, so both contribute the same to the term and to
-//    every derivative (sums over all qubits of a layer) -- Theorem 1's
-//    argument (Sec. 3) inside one cone.  Such permutations act on shell
-//    classes as automorphisms of a small "class graph" (the inner qubits plus
-//    one vertex per class, joined to the class's inner neighbours), and each
-//    of those lifts back, since the members of a class are interchangeable.
+// 2. Symmetries of the inner part.  A block evolves on the inner qubits
+//    under C_in(z) + sum_q c_q z_q and the mixers, so a permutation pi of the
+//    inner qubits that keeps the inner edges and their weights and every
+//    distance from the root edge (hence every layer's mixer set, and the root
+//    edge itself, which alone has distance 0) carries block c onto block
+//    c o pi^-1 with the qubits relabelled: Z_0 Z_1 is unchanged by it, so
+//    both contribute the same to the term and to every derivative (sums over
+//    all qubits of a layer) -- Theorem 1's argument (Sec. 3) inside one cone,
+//    whenever c o pi^-1 occurs as a phase vector as well.
 // 3. The global spin flip.  Flipping every bit leaves any cut value, the
 //    mixers, |+>^n and Z_0 Z_1 unchanged; it maps block c onto block -c
 //    (C_in(~z) = C_in(z) and sum_q c_q (1 - z_q) = const - sum_q c_q z_q).
 //
-// Generators of the class graph's automorphism group are found by
-// backtracking (with a budget: any set of genuine automorphisms gives valid
-// merges), phase vectors are merged along them and along c -> -c by
-// union-find, and one count vector per orbit is kept with the orbit's total
-// number of shell assignments.
+// Count vectors are grouped by c; generators of the inner graph's
+// automorphism group are found by backtracking (with a budget: any set of
+// genuine automorphisms gives valid merges); the occurring phase vectors are
+// merged into their orbits under that group and c -> -c by union-find, and
+// one count vector per orbit is kept with the orbit's total number of shell
+// assignments.
 #include <algorithm>
 #include <cstdint>
 #include <numeric>
@@ -46,33 +46,26 @@ constexpr int64_t kMaxBlocks = int64_t(1) << 16;  // larger block sets keep the 
 constexpr int kMaxGens = 256;
 constexpr int64_t kMaxNodes = 200000;
 
-struct ClassGraph {
-    int V = 0, n_in = 0;
-    std::vector<int> colour;             // inner: distance; class: 1000 + size
-    std::vector<std::vector<int>> w;     // edge weight, 0 = no edge
-    std::vector<int> wdeg;               // sorted-signature proxy: sum over edges of (weight code)
+// The inner part of a cone as a coloured, edge-weighted graph: vertices are
+// the inner qubits coloured by their distance from the root edge (so an
+// automorphism keeps every layer's mixer set and maps the root edge onto
+// itself), edges the inner edges with their weights.
+struct InnerGraph {
+    int V = 0;
+    std::vector<int> colour;          // distance from the root edge
+    std::vector<std::vector<int>> w;  // edge weight, 0 = no edge
+    std::vector<int> wdeg;            // an invariant for pruning: sum over edges of a weight code
 };
 
-ClassGraph class_graph(const Cone &c) {
-    ClassGraph g;
-    g.n_in = c.n_in;
-    const int ncls = int(c.shell_classes.size());
-    g.V = c.n_in + ncls;
+InnerGraph inner_graph(const Cone &c) {
+    InnerGraph g;
+    g.V = c.n_in;
     g.colour.assign(size_t(g.V), 0);
     g.w.assign(size_t(g.V), std::vector<int>(size_t(g.V), 0));
     for (int v = 0; v < c.n_in; ++v) g.colour[v] = c.dist[v];
-    std::vector<int> cls_of(size_t(c.n), -1);
-    for (int k = 0; k < ncls; ++k) {
-        g.colour[c.n_in + k] = 1000 + int(c.shell_classes[k].size());
-        for (int32_t q : c.shell_classes[k]) cls_of[q] = k;
-    }
     for (size_t e = 0; e < c.ea.size(); ++e) {
-        int a = c.ea[e], b = c.eb[e];
-        const int w = c.ew[e];
-        // a shell endpoint stands for its class (all members share neighbours and weights)
-        if (a >= c.n_in) a = c.n_in + cls_of[a];
-        if (b >= c.n_in) b = c.n_in + cls_of[b];
-        g.w[a][b] = g.w[b][a] = w;
+        const int a = c.ea[e], b = c.eb[e];
+        if (a < c.n_in && b < c.n_in) g.w[a][b] = g.w[b][a] = c.ew[e];
     }
     g.wdeg.assign(size_t(g.V), 0);
     for (int v = 0; v < g.V; ++v)
@@ -81,17 +74,17 @@ ClassGraph class_graph(const Cone &c) {
     return g;
 }
 
-// Generators of the class graph's automorphism group: for base points
+// Generators of the inner graph's automorphism group: for base points
 // v = 0, 1, ... (the earlier ones fixed) one automorphism per image t of v
 // outside the orbit already reached -- a transversal at every level, which
 // together generate the whole group.  Each search stops at its first leaf.
 struct Enumerator {
-    const ClassGraph &g;
+    const InnerGraph &g;
     std::vector<int> img, used;
     std::vector<std::vector<int>> gens;  // full vertex permutations
     int64_t nodes = 0;
 
-    explicit Enumerator(const ClassGraph &cg) : g(cg), img(size_t(cg.V), -1), used(size_t(cg.V), 0) {}
+    explicit Enumerator(const InnerGraph &cg) : g(cg), img(size_t(cg.V), -1), used(size_t(cg.V), 0) {}
 
     bool fits(int v, int t) const {
         if (used[t] || g.colour[t] != g.colour[v] || g.wdeg[t] != g.wdeg[v]) return false;
@@ -160,6 +153,8 @@ struct Enumerator {
     }
 };
 
+constexpr int64_t kMaxOrbitNodes = int64_t(1) << 20;  // phase vectors reached by the orbit search
+
 struct VecHash {
     size_t operator()(const std::vector<int32_t> &v) const {
         uint64_t h = 0x9e3779b97f4a7c15ull;
@@ -226,26 +221,61 @@ void block_orbits(Cone &c) {
     }
     // merge phase vectors along the symmetries: c -> c o pi^-1 for the
     // generators pi, and c -> -c (the global spin flip)
-    const ClassGraph g = class_graph(c);
-    Enumerator en(g);
-    en.run();
     const int64_t nid = int64_t(vec.size());
+    // A block's evolution depends on the shell only through c, so a symmetry
+    // of the inner part alone (inner edges and weights, distances from the
+    // root edge, the root edge) relates block c to block c o pi^-1 whenever
+    // that phase vector occurs.  Orbits of the occurring vectors under the
+    // inner group: breadth-first search from each along the generators,
+    // through vectors that do not occur as well (two occurring vectors of one
+    // orbit may only be joined through such), by union-find over all vectors
+    // reached; up to kMaxOrbitNodes vectors, beyond which the search stops
+    // (every merge made is still valid).
+    const InnerGraph gi = inner_graph(c);
+    Enumerator ei(gi);
+    ei.run();
     std::vector<int64_t> parent(static_cast<size_t>(nid));
     std::iota(parent.begin(), parent.end(), 0);
-    auto unite = [&](int64_t x, const std::vector<int32_t> &img) {
-        const auto it = id_of.find(img);
-        if (it == id_of.end()) return;  // cannot happen for genuine symmetries
-        const int64_t ra = find(parent, x), rb = find(parent, it->second);
+    std::vector<char> visited(static_cast<size_t>(nid), 0);
+    auto node = [&](const std::vector<int32_t> &v) {  // id of v, added if new
+        const auto it = id_of.emplace(v, int64_t(vec.size()));
+        if (it.second) {
+            vec.push_back(v);
+            parent.push_back(int64_t(parent.size()));
+            visited.push_back(0);
+        }
+        return it.first->second;
+    };
+    auto unite = [&](int64_t x, int64_t y) {
+        const int64_t ra = find(parent, x), rb = find(parent, y);
         if (ra != rb) parent[std::max(ra, rb)] = std::min(ra, rb);
     };
     std::vector<int32_t> img(static_cast<size_t>(n_in));
-    for (int64_t i = 0; i < nid; ++i) {
-        for (const auto &pi : en.gens) {
-            for (int q = 0; q < n_in; ++q) img[pi[q]] = vec[i][q];
-            unite(i, img);
+    std::vector<int64_t> queue;
+    for (int64_t i = 0; i < nid && !ei.gens.empty(); ++i) {
+        if (visited[i] || int64_t(vec.size()) > kMaxOrbitNodes) continue;
+        visited[i] = 1;
+        queue.assign(1, i);
+        while (!queue.empty()) {
+            const int64_t x = queue.back();
+            queue.pop_back();
+            for (const auto &pi : ei.gens) {
+                for (int q = 0; q < n_in; ++q) img[pi[q]] = vec[x][q];
+                if (int64_t(vec.size()) > kMaxOrbitNodes && id_of.find(img) == id_of.end()) continue;
+                const int64_t y = node(img);
+                unite(x, y);
+                if (!visited[y]) {
+                    visited[y] = 1;
+                    queue.push_back(y);
+                }
+            }
         }
+    }
+    // the spin flip maps orbits onto orbits, and -c of an occurring c occurs
+    for (int64_t i = 0; i < nid; ++i) {
         for (int q = 0; q < n_in; ++q) img[q] = -vec[i][q];
-        unite(i, img);
+        const auto it = id_of.find(img);
+        if (it != id_of.end()) unite(i, it->second);
     }
     std::vector<double> total(static_cast<size_t>(nid), 0.0);
     for (int64_t i = 0; i < nid; ++i) total[find(parent, i)] += weight[i];

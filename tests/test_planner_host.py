@@ -562,16 +562,19 @@ def _shell_bits(cls, counts):
 
 def _block_orbits_brute(plan_plain, rep, nx):
     """Merged blocks from first principles: count vectors with equal phase
-    vectors, count vectors related by an automorphism of the cone (networkx
-    enumerates every isomorphism of the cone onto itself that keeps distances
-    from the root edge and edge weights), and complementary count vectors
-    (s - n, the global spin flip) fall together; returns, per count vector,
-    the total number of shell assignments of its class, or None if there are
-    too many automorphisms to list."""
+    vectors, count vectors whose phase vectors are related by an automorphism
+    of the cone's inner part (networkx enumerates every isomorphism of the
+    inner subgraph onto itself that keeps distances from the root edge and
+    edge weights), and complementary count vectors (s - n, the global spin
+    flip) fall together; returns, per count vector, the total number of shell
+    assignments of its class, or None if there are too many automorphisms to
+    list."""
     from networkx.algorithms.isomorphism import GraphMatcher, categorical_edge_match, categorical_node_match
+    n_in = int(plan_plain.reps()["n_inner"][rep])
     g = _cone_nx(plan_plain, rep)
     for (a, b), x in zip(plan_plain.cone(rep)[2], plan_plain.cone_weights(rep)):
         g.edges[int(a), int(b)]["w"] = int(x)
+    inner = g.subgraph(range(n_in)).copy()
     cls, _ = plan_plain.shell(rep)
     counts, w = plan_plain.blocks(rep)
     rows = [tuple(c) for c in counts.tolist()]
@@ -591,19 +594,6 @@ def _block_orbits_brute(plan_plain, rep, nx):
         if a != b:
             parent[max(a, b)] = min(a, b)
 
-    gm = GraphMatcher(g, g, node_match=categorical_node_match("dist", -1), edge_match=categorical_edge_match("w", 0))
-    for k, phi in enumerate(gm.isomorphisms_iter()):
-        if k > 20000:
-            return None
-        pm = [-1] * ncls
-        for q, img in phi.items():
-            if cls[q] >= 0:
-                pm[cls[q]] = int(cls[img])
-        for i, x in enumerate(rows):
-            y = [0] * ncls
-            for j in range(ncls):
-                y[pm[j]] = x[j]
-            union(i, index[tuple(y)])
     by_vec = {}
     for i, x in enumerate(rows):
         union(i, index[tuple(int(s) - v for s, v in zip(sizes, x))])
@@ -611,6 +601,18 @@ def _block_orbits_brute(plan_plain, rep, nx):
     for members in by_vec.values():
         for i in members[1:]:
             union(members[0], i)
+    gm = GraphMatcher(inner, inner, node_match=categorical_node_match("dist", -1),
+                      edge_match=categorical_edge_match("w", 0))
+    for k, phi in enumerate(gm.isomorphisms_iter()):
+        if k > 20000:
+            return None
+        for c, members in by_vec.items():
+            img = [0] * n_in
+            for q in range(n_in):
+                img[phi[q]] = c[q]
+            other = by_vec.get(tuple(img))
+            if other is not None:
+                union(members[0], other[0])
     total = {}
     for i in range(len(rows)):
         total[find(i)] = total.get(find(i), 0.0) + w[i]
@@ -621,13 +623,13 @@ def _block_orbits_brute(plan_plain, rep, nx):
     (I.petersen(), 1, False), (I.petersen(), 2, False), (I.torus(5, 5), 2, False), (I.circulant(20, [1, 4]), 1, False),
     (I.circulant(24, [1, 5]), 2, False), (I.hypercube(4), 2, False), (I.complete_bipartite(3, 4), 1, False),
     (I.random_regular(40, 3, 3), 2, False), (I.random_regular(30, 4, 2), 1, False), (I.random_regular(30, 3, 5), 2, True),
-    (I.erdos_renyi(30, 0.2, 3), 1, False), (I.erdos_renyi(30, 0.2, 4), 1, True),
+    (I.erdos_renyi(30, 0.2, 3), 1, False), (I.erdos_renyi(30, 0.2, 4), 1, True), (I.random_regular(24, 3, 1), 3, False),
 ])
 def test_block_orbits_match_brute_force(qlib, graph, p, weighted):
     """The planner's merged blocks are exactly the classes of count vectors
-    under equal phase vectors, the cone's full automorphism group (root edge
-    fixed setwise) and the spin flip, each carrying its class's number of
-    shell assignments."""
+    under equal phase vectors, the full automorphism group of the cone's
+    inner part (distances kept, so the root edge is fixed setwise) and the
+    spin flip, each carrying its class's number of shell assignments."""
     nx = pytest.importorskip("networkx")
     n, edges = graph
     w = np.random.default_rng(1).choice([1, 2, -1], len(edges)) if weighted else None
@@ -678,7 +680,8 @@ def _block_zz(plan, rep, counts, theta, p):
 
 
 @pytest.mark.parametrize("graph,p,weighted", [(I.torus(5, 5), 2, False), (I.random_regular(30, 3, 5), 2, True),
-                                              (I.erdos_renyi(24, 0.25, 3), 1, False), (I.circulant(24, [1, 5]), 2, False)])
+                                              (I.erdos_renyi(24, 0.25, 3), 1, False), (I.circulant(24, [1, 5]), 2, False),
+                                              (I.random_regular(24, 3, 1), 3, False)])
 def test_merged_blocks_have_equal_contributions(qlib, graph, p, weighted):
     """Every count vector merged into a block has the same <Z_0 Z_1> as the
     block's own (simulated from the definition in FP64), and the merged
