@@ -46,9 +46,9 @@ SEEDS = (1, 2, 3, 4)
 N_VERT, DEG, P_DEPTH, N_POINTS = 2000, 3, 2, 64
 
 # DRAM bytes per launch of the adjoint cone kernel from one ncu capture of this
-# workload, with the hash of the kernel source they were taken on (a changed
-# kernel reports null until it is profiled again).
-TRAFFIC = {"kernels_sha1": "b71ffac90a385dfd11796e17c6dbab9844a8f461", "bytes_per_launch": 8400000}
+# workload, with the hash of the sources they were taken on (the kernel and
+# the planner; a change to either reports null until it is profiled again).
+TRAFFIC = {"kernels_sha1": "ef36ee279ce3af8d8db60b76f20b8f3697a89692", "bytes_per_launch": 6790000}
 
 
 def log(*a):
@@ -160,8 +160,10 @@ def hbm_path_measurement(device, flush, stream):
 
 
 def kernels_sha1():
+    """Hash of the adjoint kernel's sources and of the planner and upload code
+    that decide what it reads (the shell block lists, the descriptors)."""
     h = hashlib.sha1()
-    for f in ("cone_kernel.cuh", "kernels_grad.cu", "device.cuh"):
+    for f in ("cone_kernel.cuh", "kernels_grad.cu", "device.cuh", "capi.cu", "plan.cpp", "block_orbits.cpp"):
         h.update(open(os.path.join(ROOT, "paper_2101_10296_gb300", "csrc", f), "rb").read())
     return h.hexdigest()
 
