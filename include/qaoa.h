@@ -342,8 +342,9 @@ int qaoa_device_status(const qaoa_plan *plan, int32_t *status);
  * Launch tuning of a plan (applies to every later call).  Any field 0 means
  * "default".
  *   points_per_task  parameter points one warp task of the register kernels
- *                    evaluates for the same cone slots (default: up to 16,
- *                    while their phase tables fit 6 KB of shared memory)
+ *                    evaluates for the same cone slots (default: up to 32,
+ *                    while their phase tables fit 8 KB of shared memory;
+ *                    larger values are cut to what fits 12 KB per warp)
  *   blocks_per_sm    resident blocks per SM of the persistent grid (default:
  *                    the occupancy limit)
  *   big_scratch_bytes scratch per call for large-state cones, which sets how

@@ -42,7 +42,7 @@ def _time(plan, params, grad, reps):
 def candidates(plan, n_points):
     info = plan.info()
     row_bytes = info["p"] * (info["max_edges"] + 1) * 8
-    jpts = [j for j in (1, 2, 4, 8, 16) if j <= max(1, n_points) and j * row_bytes * 4 <= 48 * 1024]
+    jpts = [j for j in (1, 2, 4, 8, 16, 32) if j <= max(1, n_points) and j * row_bytes * 4 <= 48 * 1024]
     bpsm = [0, 1, 2]
     bigs = [0] if info["n_big"] == 0 else [0, 32 << 20, 96 << 20, 256 << 20]
     return [(j, b, g) for j in jpts for b in bpsm for g in bigs]

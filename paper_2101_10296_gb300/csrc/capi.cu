@@ -237,11 +237,13 @@ int run(const qaoa_plan *plan, int64_t n_points, const double *params, double *e
         RegLaunch L;
         L.n_points = n_points;
         L.p = p;
-        // points per warp task: up to 16, phase tables of at most 6 KB per warp
+        // points per warp task: up to 32, phase tables of at most 8 KB per warp
+        // (a tuned value is held to the 48 KB of shared memory of 4 warps)
         {
             const int64_t row_bytes = int64_t(p) * d->cmax1 * int64_t(sizeof(float2));
             int64_t jpt = d->points_per_task > 0 ? d->points_per_task
-                                                 : std::min<int64_t>(16, std::max<int64_t>(1, 6144 / row_bytes));
+                                                 : std::min<int64_t>(32, std::max<int64_t>(1, 8192 / row_bytes));
+            jpt = std::min<int64_t>(jpt, std::max<int64_t>(1, 12288 / row_bytes));
             L.jpt = int32_t(std::min<int64_t>(jpt, n_points));
         }
         const size_t smem = size_t(kRegBlock / 32) * L.jpt * p * d->cmax1 * sizeof(float2);

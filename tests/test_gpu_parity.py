@@ -679,6 +679,14 @@ def test_tuning_leaves_results_unchanged(q):
         e1, g1 = plan.energy_grad(th)
         assert np.allclose(e1.cpu().numpy(), e0.cpu().numpy(), rtol=E_REL_TOL, atol=0)
         assert np.allclose(g1.cpu().numpy(), g0.cpu().numpy(), rtol=1e-4, atol=1e-6)
+    # more points per task than the phase tables' shared memory holds: cut to what fits
+    plan.set_tuning()
+    th64 = _params(np.stack([I.draw_params(3, 64, 50 + g) for g in range(G)]))
+    e0, g0 = plan.energy_grad(th64)
+    plan.set_tuning(points_per_task=1000)
+    e1, g1 = plan.energy_grad(th64)
+    assert np.allclose(e1.cpu().numpy(), e0.cpu().numpy(), rtol=E_REL_TOL, atol=0)
+    assert np.allclose(g1.cpu().numpy(), g0.cpu().numpy(), rtol=1e-4, atol=1e-6)
     plan.set_tuning()
     assert plan.device_status() == 0
 
