@@ -237,12 +237,18 @@ int run(const qaoa_plan *plan, int64_t n_points, const double *params, double *e
         RegLaunch L;
         L.n_points = n_points;
         L.p = p;
-        // points per warp task: up to 32, phase tables of at most 8 KB per warp
-        // (a tuned value is held to the 48 KB of shared memory of 4 warps)
+        // points per warp task: up to 32, phase tables of at most 8 KB per warp,
+        // halved while the tasks would not give every SM 16 warps (small
+        // plans: more tasks of fewer points); a tuned value is held to the
+        // 48 KB of shared memory of 4 warps
         {
             const int64_t row_bytes = int64_t(p) * d->cmax1 * int64_t(sizeof(float2));
-            int64_t jpt = d->points_per_task > 0 ? d->points_per_task
-                                                 : std::min<int64_t>(32, std::max<int64_t>(1, 8192 / row_bytes));
+            const int64_t warps = grad ? d->reg_g.warps : d->reg_e.warps;
+            int64_t jpt = d->points_per_task;
+            if (jpt <= 0) {
+                jpt = std::min<int64_t>(32, std::max<int64_t>(1, 8192 / row_bytes));
+                while (jpt > 1 && warps * ((n_points + jpt - 1) / jpt) < int64_t(sm_count()) * 16) jpt = (jpt + 1) / 2;
+            }
             jpt = std::min<int64_t>(jpt, std::max<int64_t>(1, 12288 / row_bytes));
             L.jpt = int32_t(std::min<int64_t>(jpt, n_points));
         }
