@@ -303,6 +303,19 @@ def test_bad_call_arguments(qlib):
     assert qlib.lib().qaoa_plan_graph(3, 1, qlib._ptr(e, C.c_int32), 1, 1, 0, 0, None) == qlib.QAOA_E_INVALID
     assert qlib.lib().qaoa_plan_info(None, None) == qlib.QAOA_E_INVALID
     assert qlib.lib().qaoa_energy(None, 1, None, None, None, None) == qlib.QAOA_E_INVALID
+    nb = C.c_int64()
+    assert qlib.lib().qaoa_plan_blocks(None, 0, C.byref(nb), None, None, None) == qlib.QAOA_E_INVALID
+    plan = qlib.Plan(I.petersen(), 1)
+    for rep in (-1, plan.info()["n_reps"]):
+        assert qlib.lib().qaoa_plan_blocks(plan.handle, rep, C.byref(nb), None, None, None) == qlib.QAOA_E_INVALID
+    # counts only, weights only: the same rows as both together
+    counts, w = plan.blocks(0)
+    nc = counts.shape[1]
+    c2 = np.zeros_like(counts)
+    w2 = np.zeros_like(w)
+    assert qlib.lib().qaoa_plan_blocks(plan.handle, 0, None, None, qlib._ptr(c2, C.c_uint8), None) == qlib.QAOA_OK
+    assert qlib.lib().qaoa_plan_blocks(plan.handle, 0, None, None, None, qlib._ptr(w2, C.c_double)) == qlib.QAOA_OK
+    assert np.array_equal(c2, counts) and np.array_equal(w2, w) and nc >= 1
 
 
 def test_plan_flags(qlib):
