@@ -5,7 +5,6 @@ matrix-exponential construction built from Pauli matrices, the published p = 1
 closed form, exact special values, symmetries of the energy, textbook
 automorphism-group orders, and finite differences of the definition.
 """
-import itertools
 import math
 
 import numpy as np
