@@ -153,7 +153,7 @@ struct Enumerator {
     }
 };
 
-constexpr int64_t kMaxOrbitNodes = int64_t(1) << 20;  // phase vectors reached by the orbit search
+constexpr int64_t kMaxOrbitNodes = int64_t(1) << 18;  // phase vectors reached by the orbit search
 
 struct VecHash {
     size_t operator()(const std::vector<int32_t> &v) const {
@@ -219,8 +219,6 @@ void block_orbits(Cone &c) {
         }
         weight[size_t(it->second)] += mult;
     }
-    // merge phase vectors along the symmetries: c -> c o pi^-1 for the
-    // generators pi, and c -> -c (the global spin flip)
     const int64_t nid = int64_t(vec.size());
     // A block's evolution depends on the shell only through c, so a symmetry
     // of the inner part alone (inner edges and weights, distances from the
