@@ -33,7 +33,10 @@
 // assignments.
 #include <algorithm>
 #include <cstdint>
+#include <cstring>
+#include <mutex>
 #include <numeric>
+#include <string>
 #include <unordered_map>
 #include <vector>
 
@@ -171,14 +174,74 @@ int64_t find(std::vector<int64_t> &parent, int64_t x) {
     return x;
 }
 
+// Everything the merging reads from a cone, in its local labels: the inner
+// distances and edges, and per shell class its size and the inner
+// neighbours (with weights) of its first member.  Cones with equal keys get
+// equal block lists; tree-like cones of one graph share a handful of keys.
+std::string structure_key(const Cone &c, const std::vector<int> &cls_of) {
+    std::vector<int32_t> k;
+    k.push_back(c.n_in);
+    k.push_back(int32_t(c.shell_classes.size()));
+    for (int q = 0; q < c.n_in; ++q) k.push_back(c.dist[q]);
+    for (const auto &cls : c.shell_classes) k.push_back(int32_t(cls.size()));
+    for (size_t e = 0; e < c.ea.size(); ++e) {
+        int a = c.ea[e], b = c.eb[e];
+        if (a < c.n_in && b < c.n_in) {
+            k.insert(k.end(), {a, b, c.ew[e]});
+            continue;
+        }
+        if (a < c.n_in) std::swap(a, b);  // a: the shell end
+        if (a < c.n_in || b >= c.n_in || c.shell_classes[cls_of[a]][0] != a) continue;
+        k.insert(k.end(), {-1 - cls_of[a], b, c.ew[e]});
+    }
+    std::string out(k.size() * sizeof(int32_t), '\0');
+    std::memcpy(&out[0], k.data(), out.size());
+    return out;
+}
+
+void merge_blocks(Cone &c, int n_in, int ncls);
+
 }  // namespace
 
-void block_orbits(Cone &c) {
+struct BlockMemo {
+    std::mutex mu;
+    std::unordered_map<std::string, std::pair<std::vector<std::vector<uint8_t>>, std::vector<double>>> done;
+};
+
+BlockMemo *block_memo_new() { return new BlockMemo(); }
+void block_memo_free(BlockMemo *m) { delete m; }
+
+void block_orbits(Cone &c, BlockMemo *memo) {
     c.blk_counts.clear();
     c.blk_weight.clear();
     const int ncls = int(c.shell_classes.size());
     if (ncls == 0 || c.n_blocks < 2 || c.n_blocks > kMaxBlocks) return;
     const int n_in = c.n_in;
+    std::string key;
+    if (memo) {
+        std::vector<int> cls(size_t(c.n), -1);
+        for (int k = 0; k < ncls; ++k)
+            for (int32_t q : c.shell_classes[k]) cls[q] = k;
+        key = structure_key(c, cls);
+        std::lock_guard<std::mutex> lk(memo->mu);
+        const auto it = memo->done.find(key);
+        if (it != memo->done.end()) {
+            c.blk_counts = it->second.first;
+            c.blk_weight = it->second.second;
+            if (!c.blk_counts.empty()) c.n_blocks = int64_t(c.blk_counts.size());
+            return;
+        }
+    }
+    merge_blocks(c, n_in, ncls);
+    if (memo) {
+        std::lock_guard<std::mutex> lk(memo->mu);
+        memo->done.emplace(std::move(key), std::make_pair(c.blk_counts, c.blk_weight));
+    }
+}
+
+namespace {
+
+void merge_blocks(Cone &c, const int n_in, const int ncls) {
     // inner neighbours of each class with their weights (shared by its members)
     std::vector<int> cls_of(size_t(c.n), -1);
     for (int k = 0; k < ncls; ++k)
@@ -291,4 +354,5 @@ void block_orbits(Cone &c) {
     c.n_blocks = int64_t(c.blk_counts.size());
 }
 
+}  // namespace
 }  // namespace qaoa

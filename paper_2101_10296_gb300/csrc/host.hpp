@@ -75,7 +75,12 @@ bool cones_isomorphic(const Cone &a, const Cone &b, int p);
 void cone_classes(const std::vector<const Cone *> &cones, int p, std::vector<int32_t> &class_of);
 
 // Merges the cone's shell blocks that contribute equally (block_orbits.cpp).
-void block_orbits(Cone &c);
+// With a memo (shared by the threads of one planning call), cones whose
+// local structure was merged before reuse that result.
+struct BlockMemo;
+BlockMemo *block_memo_new();
+void block_memo_free(BlockMemo *m);
+void block_orbits(Cone &c, BlockMemo *memo = nullptr);
 
 void set_error(const std::string &msg);
 

@@ -5,6 +5,7 @@
 #include <chrono>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <thread>
 #include <unordered_map>
@@ -363,9 +364,11 @@ extern "C" int qaoa_plan_graphs_weighted(int32_t n_graphs, const int32_t *n_vert
         }
         pl->cones.swap(kept);
         // block merging: shell blocks that contribute equally (phase vectors,
-        // symmetries of the cone, the global spin flip)
-        if (!(flags & (QAOA_SHELL_PLAIN | QAOA_BLOCK_PLAIN)))
-            parallel_for(int64_t(pl->cones.size()), [&](int64_t i, int) { block_orbits(pl->cones[i]); });
+        // symmetries of the inner part, the global spin flip)
+        if (!(flags & (QAOA_SHELL_PLAIN | QAOA_BLOCK_PLAIN))) {
+            std::unique_ptr<BlockMemo, void (*)(BlockMemo *)> memo(block_memo_new(), block_memo_free);
+            parallel_for(int64_t(pl->cones.size()), [&](int64_t i, int) { block_orbits(pl->cones[i], memo.get()); });
+        }
         auto t2 = std::chrono::steady_clock::now();
         pl->t_orbits = std::chrono::duration<double>(t1 - t0).count();
         pl->t_cones = std::chrono::duration<double>(t2 - t1).count();

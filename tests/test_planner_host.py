@@ -546,6 +546,26 @@ def test_block_orbits_of_known_cones(qlib):
     assert len(counts) == 42 and w.sum() == 2.0 ** 22
 
 
+def test_block_merging_is_independent_of_batching(qlib):
+    """Cones with the same local structure share one merging result within a
+    planning call; every representative's blocks come out the same whether
+    its graph is planned alone or in a batch (and whichever thread merged
+    that structure first)."""
+    graphs = [I.random_regular(300, 3, s) for s in (1, 2)] + [I.torus(6, 6)]
+    batch = qlib.Plan(graphs, 2)
+    rows = [r for r in range(batch.info()["n_reps"])]
+    graph_of = batch.reps()["graph"]
+    alone = [qlib.Plan(g, 2) for g in graphs]
+    start = {}
+    for r in rows:
+        start.setdefault(int(graph_of[r]), r)
+    for r in rows:
+        g = int(graph_of[r])
+        c1, w1 = batch.blocks(r)
+        c2, w2 = alone[g].blocks(r - start[g])
+        assert np.array_equal(c1, c2) and np.array_equal(w1, w2)
+
+
 def _phase_vector(plan, rep, counts):
     """The coefficient of z_q in the shell edges' part of the cut, for the
     assignment that sets the first n_k members of each class to 1: a shell
