@@ -5,7 +5,11 @@
 // orbits (Sec. 3).  This file is the project's own solver:
 //
 //  1. colour refinement to the coarsest equitable partition (splitting cells
-//     by the number of neighbours in a splitter cell until stable);
+//     by the number of neighbours in a splitter cell until stable), started
+//     from a vertex invariant read off the balls of radius 1..3 around each
+//     vertex (cycles near a vertex show up there, so in a graph without
+//     symmetry the few vertices on short cycles are told apart before any
+//     search);
 //  2. an individualisation-refinement search: along a first path of the
 //     search tree (individualise the first element of the first smallest
 //     non-singleton cell, refine, repeat until discrete) the tree is explored
@@ -183,6 +187,54 @@ class Refiner {
     std::vector<Frag> frag_;
 };
 
+// Vertex invariant, from a breadth-first search of radius 1..3 around each
+// vertex (stopped once the ball holds more than kBallCap vertices): per
+// radius r the number of vertices first reached at distance r, and the edge
+// codes summed separately over the edges scanned from distance r - 1 that
+// lead back to distance <= r - 1 and over those that reach a vertex at
+// distance r already reached from another vertex (both zero in a tree, so
+// cycles near a vertex show).  The counts do not depend on the order of the
+// search, and an automorphism maps a vertex's balls onto its image's, so
+// vertices of one orbit get equal values.
+constexpr int kBallRadius = 3;
+constexpr int32_t kBallCap = 512;
+
+void ball_invariants(const Graph &g, std::vector<uint64_t> &col) {
+    const int32_t n = g.n;
+    col.assign(size_t(n), 0);
+    std::vector<int32_t> stamp(size_t(n), -1), dist(size_t(n), 0), ball;
+    for (int32_t v = 0; v < n; ++v) {
+        ball.assign(1, v);
+        stamp[v] = v;
+        dist[v] = 0;
+        uint64_t h = hmix(0x243f6a8885a308d3ull, uint64_t(g.degree(v)));
+        size_t frontier = 0;
+        for (int r = 1; r <= kBallRadius && int32_t(ball.size()) <= kBallCap; ++r) {
+            const size_t end = ball.size();
+            uint64_t back = 0, cross = 0;
+            for (size_t i = frontier; i < end; ++i) {
+                const int32_t x = ball[i];
+                for (int64_t k = g.off[x]; k < g.off[x + 1]; ++k) {
+                    const int32_t y = g.adj[k];
+                    const uint64_t code = Refiner::ecode(g.ew[g.eid[k]]);
+                    if (stamp[y] != v) {
+                        stamp[y] = v;
+                        dist[y] = r;
+                        ball.push_back(y);
+                    } else if (dist[y] < r) {
+                        back += code;
+                    } else {
+                        cross += code;
+                    }
+                }
+            }
+            frontier = end;
+            h = hmix(hmix(hmix(h, uint64_t(ball.size() - end)), back), cross);
+        }
+        col[v] = h;
+    }
+}
+
 void individualize(Partition &P, int32_t v, std::vector<int32_t> &queue) {
     int32_t X = P.cell[v], L = P.len[X];
     if (L == 1) return;
@@ -214,16 +266,31 @@ class AutSearch {
             complete = true;
             return;
         }
+        // the initial partition: cells of equal ball invariants, ordered by value
+        std::vector<uint64_t> col;
+        ball_invariants(g_, col);
         Partition P0;
         P0.lab.resize(n);
         P0.pos.resize(n);
         P0.cell.assign(n, 0);
         P0.len.assign(n, 0);
         std::iota(P0.lab.begin(), P0.lab.end(), 0);
-        std::iota(P0.pos.begin(), P0.pos.end(), 0);
-        P0.len[0] = n;
-        P0.ncells = 1;
-        std::vector<int32_t> queue{0};
+        std::sort(P0.lab.begin(), P0.lab.end(), [&](int32_t a, int32_t b) {
+            return col[a] != col[b] ? col[a] < col[b] : a < b;
+        });
+        std::vector<int32_t> queue;
+        for (int32_t i = 0; i < n;) {
+            int32_t j = i;
+            while (j < n && col[P0.lab[j]] == col[P0.lab[i]]) ++j;
+            P0.len[i] = j - i;
+            for (int32_t k = i; k < j; ++k) {
+                P0.pos[P0.lab[k]] = k;
+                P0.cell[P0.lab[k]] = i;
+            }
+            queue.push_back(i);
+            ++P0.ncells;
+            i = j;
+        }
         std::vector<uint64_t> ev;
         ref_.refine(P0, queue, &ev, nullptr);
         path_.push_back(P0);
