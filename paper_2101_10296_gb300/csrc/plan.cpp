@@ -366,8 +366,11 @@ extern "C" int qaoa_plan_graphs_weighted(int32_t n_graphs, const int32_t *n_vert
         // block merging: shell blocks that contribute equally (phase vectors,
         // symmetries of the inner part, the global spin flip)
         if (!(flags & (QAOA_SHELL_PLAIN | QAOA_BLOCK_PLAIN))) {
-            std::unique_ptr<BlockMemo, void (*)(BlockMemo *)> memo(block_memo_new(), block_memo_free);
-            parallel_for(int64_t(pl->cones.size()), [&](int64_t i, int) { block_orbits(pl->cones[i], memo.get()); });
+            // one memo per worker thread (parallel_for runs at most 16): no lock contention
+            std::vector<std::unique_ptr<BlockMemo, void (*)(BlockMemo *)>> memo;
+            for (int t = 0; t < 16; ++t) memo.emplace_back(block_memo_new(), block_memo_free);
+            parallel_for(int64_t(pl->cones.size()),
+                         [&](int64_t i, int t) { block_orbits(pl->cones[i], memo[size_t(t)].get()); });
         }
         auto t2 = std::chrono::steady_clock::now();
         pl->t_orbits = std::chrono::duration<double>(t1 - t0).count();
