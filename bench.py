@@ -247,6 +247,14 @@ def _oracle_term_job(job):
     return O.term_grad_adjoint(len(verts), ledges, _W["theta"][g, j], P_DEPTH)
 
 
+def _oracle_serial_job(jobs):
+    """Runs the given terms one after another in one worker; returns seconds."""
+    t0 = time.perf_counter()
+    for job in jobs:
+        _oracle_term_job(job)
+    return time.perf_counter() - t0
+
+
 def make_oracle_pool(cores):
     """One single-threaded oracle process per host core (spawned, so it is safe
     to create after CUDA is initialised)."""
@@ -259,8 +267,9 @@ def make_oracle_pool(cores):
 def oracle_sample(target_s=15.0, pool=None, seed=0):
     """Times the FP64 oracle (per-edge cone energy + adjoint gradient) on a
     random sample of (graph, edge) terms at point 0, sized to about target_s
-    of wall time; returns (evals/s extrapolated to whole (graph, point) evals,
-    processes, seconds, terms)."""
+    of wall time, and a smaller sample on one core; returns (evals/s
+    extrapolated to whole (graph, point) evals, processes, seconds, terms,
+    one-core evals/s)."""
     rng = np.random.default_rng(seed)
     cores = os.cpu_count() or 1
     own = pool is None
@@ -277,12 +286,15 @@ def oracle_sample(target_s=15.0, pool=None, seed=0):
         t0 = time.perf_counter()
         pool.map(_oracle_term_job, jobs, chunksize=max(1, n_terms // (8 * cores)))
         dt = time.perf_counter() - t0
+        # the same kind of terms on one core, about a tenth of the time budget
+        n_one = int(max(1, min(n_terms, 0.1 * target_s / max(t_one, 1e-4))))
+        dt_one = pool.apply(_oracle_serial_job, (jobs[:n_one],))
     finally:
         if own:
             pool.close()
             pool.join()
     terms_per_eval = N_VERT * DEG // 2  # random 3-regular: trivial Aut, one cone per edge
-    return n_terms / dt / terms_per_eval, cores, dt, n_terms
+    return n_terms / dt / terms_per_eval, cores, dt, n_terms, n_one / dt_one / terms_per_eval
 
 
 def max_over_ranks(x, dist, device):
@@ -493,11 +505,12 @@ def run_ours(args, rank, world, local_rank):
     }
     if pool is not None:
         try:
-            v, cores, dt, nt = oracle_sample(target_s=args.cpu_seconds, pool=pool)
+            v, cores, dt, nt, v1 = oracle_sample(target_s=args.cpu_seconds, pool=pool)
             out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                    "sample": f"{nt} random (graph, edge) cone terms at point 0, FP64 energy + "
                                              f"adjoint gradient, {dt:.1f} s on {cores} processes, "
-                                             f"scaled to whole evals of 3000 terms"}
+                                             f"scaled to whole evals of 3000 terms",
+                                   "one_core_value": v1}
         finally:
             pool.close()
             pool.join()
@@ -514,11 +527,13 @@ def run_reference(args, rank, world):
         budget = max(5.0, min(30.0, 150.0 / max(args.steps + args.warmup, 1)))
         vals = []
         samples = []
+        ones = []
         for k in range(args.warmup + args.steps):
-            v, c, dt, nt = oracle_sample(target_s=budget, pool=pool, seed=k)
+            v, c, dt, nt, v1 = oracle_sample(target_s=budget, pool=pool, seed=k)
             if k >= args.warmup:
                 vals.append(v)
                 samples.append(nt)
+                ones.append(v1)
     finally:
         pool.close()
         pool.join()
@@ -533,7 +548,8 @@ def run_reference(args, rank, world):
                    "parallelism": f"{cores} host processes"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"per step {statistics.mean(samples):.0f} random cone terms at point 0 "
-                                   f"(FP64 energy + adjoint gradient), scaled to whole evals of 3000 terms"},
+                                   f"(FP64 energy + adjoint gradient), scaled to whole evals of 3000 terms",
+                         "one_core_value": statistics.mean(ones)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 

@@ -65,3 +65,12 @@ def test_clock_log_parser(tmp_path):
         f.write("0, 2000, 2070, 990.0, 0x0, Not Active, Not Active, Not Active, Not Active\n")
     s = c.summary()
     assert s["sm_mhz"] == 1950 and s["sm_max_mhz"] == 2070 and s["reasons"] == ["sw_power_cap"]
+
+
+def test_oracle_sample_reports_parallel_and_one_core_rates():
+    """The CPU baseline leg: a pool of oracle processes and a one-core run of
+    the same kind of terms, both scaled to whole evaluations."""
+    import bench
+    v, cores, dt, nt, v1 = bench.oracle_sample(target_s=1.0)
+    assert v > 0 and v1 > 0 and cores >= 1 and dt > 0 and nt >= cores
+    assert v1 <= v * 1.5  # one process is not faster than the pool
