@@ -714,7 +714,8 @@ def _block_zz(plan, rep, counts, theta, p):
 
 @pytest.mark.parametrize("graph,p,weighted", [(I.torus(5, 5), 2, False), (I.random_regular(30, 3, 5), 2, True),
                                               (I.erdos_renyi(24, 0.25, 3), 1, False), (I.circulant(24, [1, 5]), 2, False),
-                                              (I.random_regular(24, 3, 1), 3, False)])
+                                              (I.random_regular(24, 3, 1), 3, False), (I.erdos_renyi(20, 0.2, 6), 2, True),
+                                              (I.circulant(16, [1, 3]), 2, True)])
 def test_merged_blocks_have_equal_contributions(qlib, graph, p, weighted):
     """Every count vector merged into a block has the same <Z_0 Z_1> as the
     block's own (simulated from the definition in FP64), and the merged
