@@ -566,6 +566,18 @@ def test_block_merging_is_independent_of_batching(qlib):
         assert np.array_equal(c1, c2) and np.array_equal(w1, w2)
 
 
+def test_block_merging_cap_keeps_every_count_vector(qlib):
+    """A cone with more than 2^16 count vectors keeps the plain enumeration
+    (Q_6 at p = 2: twenty singleton shell classes, 2^20 blocks), and the
+    block query still lists every one with weight 1."""
+    plan = qlib.Plan(I.hypercube(6), 2)
+    cls, nb = plan.shell(0)
+    assert nb == 2 ** 20 == 2 ** int((cls >= 0).sum())
+    counts, w = plan.blocks(0)
+    assert counts.shape == (2 ** 20, 20) and np.all(w == 1.0)
+    assert np.array_equal(counts[5], [1, 0, 1] + [0] * 17)  # mixed radix, least significant class first
+
+
 def _phase_vector(plan, rep, counts):
     """The coefficient of z_q in the shell edges' part of the cut, for the
     assignment that sets the first n_k members of each class to 1: a shell
