@@ -1,15 +1,24 @@
 #!/usr/bin/env python3
-"""Benchmark: QAOA MaxCut energy + adjoint gradient evaluations per second.
+"""Benchmark: QAOA MaxCut energy + adjoint gradient evaluations per second,
+orbit-reduced against plain all-edge, on one GPU.
 
-Workload (one step): 4 random 3-regular graphs with n = 2000 (3000 edges,
-seeds 1-4), depth p = 2, 64 parameter points per graph drawn with the
-project's recipe, orbit reduction on, energies and gradients of all
-4 x 64 = 256 (graph, point) evaluations in one launch of the adjoint cone
-kernel.  Every cone is evolved as blocks of its inner qubits, one per shell
-count vector up to the cone's own symmetries (exact: blocks related by a
-symmetry contribute equally); the line also reports the rate with every
-count vector evolved (``shell_blocks``).  The inputs are synthetic, shaped like
-the asymmetric random graphs of the paper's benchmark (Sec. 5).
+Workload (one step): the 48-graph mix shaped like the paper's benchmark set
+(Sec. 5; 100 to 10,000 vertices: random 3-, 4- and 5-regular graphs,
+Erdos-Renyi graphs of mean degree 4, tori, hypercubes Q_8..Q_13 and
+circulants), depth p = 1, 256 parameter points per graph drawn with the
+project's recipe, orbit reduction on (one cone per edge orbit of Aut(G),
+weighted by the orbit size; Sec. 3), energies and gradients of all
+48 x 256 = 12,288 (graph, point) evaluations in one batched call.  The same
+workload with every edge its own cone (orbit reduction off, same kernels) is
+timed the same way and reported beside it (``plain_all_edge_evals_per_s``):
+the contrast the metric names.  The inputs are synthetic stand-ins for the
+paper's benchmark files, which are not available.
+
+Side measurements (none enters ``value``): 4 random 3-regular graphs with
+n = 2000 at p = 2 and 64 points (graphs without symmetry, where the orbit
+step must cost nothing), the energy-only rate, every shell count vector
+evolved as its own block, the cone-class plan, a training run, and the
+large-state path on a plan whose cones exceed on-chip memory.
 
 Timing: W untimed warm-up steps, then K steps each bracketed by CUDA events on
 the launching stream, with a 512 MB L2 flush written between steps outside the
@@ -18,8 +27,9 @@ rank runs its own replica (the path shards into independent problems; there
 is no data-path collective), so the whole-job value is N x per-rank evals.
 
 ``--impl reference`` times the FP64 CPU oracle on the host cores on a bounded
-sample of the same workload: random cone terms of the four graphs at one
-parameter point, scaled to whole evaluations.
+sample of the same workload: random cone terms at one parameter point, scaled
+to whole evaluations by a cost model calibrated on the sample (extrapolated,
+as the paper extrapolates its infeasible runs in Sec. 5).
 """
 from __future__ import annotations
 
@@ -40,14 +50,20 @@ sys.path.insert(0, ROOT)
 
 METRIC = "QAOA energy+grad evals/s on 1 GB300, orbit-reduced batched vs plain all-edge"
 UNIT = "evals/s"
-WORKLOAD = "rr3-n2000x4-p2-P64: 4 random 3-regular graphs n=2000 (seeds 1-4), p=2, 64 points each, energy+grad"
-SEEDS = (1, 2, 3, 4)
-N_VERT, DEG, P_DEPTH, N_POINTS = 2000, 3, 2, 64
+WORKLOAD = ("mix48-p1-P256: the 48-graph benchmark-shaped mix (100-10,000 vertices: random 3/4/5-regular, "
+            "Erdos-Renyi <k>=4, tori, hypercubes Q8-Q13, circulants), p=1, 256 points per graph, energy+grad, "
+            "orbit-reduced")
+P_DEPTH, N_POINTS = 1, 256
+PARAM_SEED0 = 1000  # graph k draws its points with seed PARAM_SEED0 + k
+SIDE_SEEDS = (1, 2, 3, 4)
 
-# DRAM bytes per launch of the adjoint cone kernel from one ncu capture of this
-# workload, with the hash of the sources they were taken on (the kernel and
-# the planner; a change to either reports null until it is profiled again).
-TRAFFIC = {"kernels_sha1": "7394f4e8f6fbe9a04c969fe48c59dfdfe7c3d158", "bytes_per_launch": 6790000}
+# DRAM bytes per launch of the dominant kernel (the adjoint register kernel on
+# this workload) from a one-pass ncu capture of `bench.py --case reg-mix48`
+# (dram__bytes_read.sum + dram__bytes_write.sum), with the hash of the sources
+# they were taken on; a change to any of them reports null until it is
+# captured again.
+TRAFFIC = {"kernels_sha1": None, "bytes_per_launch": None,
+           "source": "ncu one-pass capture of `python bench.py --case reg-mix48`, summarised in profiles/"}
 
 
 def log(*a):
@@ -55,10 +71,34 @@ def log(*a):
 
 
 def workload():
+    """The 48 graphs of the mix and their parameter points [48, 256, 2]."""
     from paper_2101_10296_gb300 import inputs as I
-    graphs = [I.random_regular(N_VERT, DEG, s) for s in SEEDS]
-    theta = np.stack([I.draw_params(P_DEPTH, N_POINTS, s) for s in SEEDS])
+    graphs = [b() for _, b in I.mixed_benchmark_graphs()]
+    theta = np.stack([I.draw_params(P_DEPTH, N_POINTS, PARAM_SEED0 + k) for k in range(len(graphs))])
     return graphs, theta
+
+
+def side_workload():
+    """4 random 3-regular graphs n = 2000 (seeds 1-4), p = 2, 64 points each."""
+    from paper_2101_10296_gb300 import inputs as I
+    graphs = [I.random_regular(2000, 3, s) for s in SIDE_SEEDS]
+    theta = np.stack([I.draw_params(2, 64, s) for s in SIDE_SEEDS])
+    return graphs, theta
+
+
+def config_dict(world, info=None):
+    """The workload's config keys (the same on both arms)."""
+    d = {
+        "workload": WORKLOAD,
+        "graphs": 48, "p": P_DEPTH, "points_per_graph": N_POINTS, "evals_per_step": 48 * N_POINTS,
+        "orbit_reduction": True,
+        "l2": "512 MB buffer written between timed steps (outside the events)",
+        "parallelism": f"replicas x{world}",
+    }
+    if info is not None:
+        d.update({"n_edges": int(info["n_edges_total"]), "n_reps": int(info["n_reps"]),
+                  "max_cone_qubits": int(info["max_qubits"]), "max_inner_qubits": int(info["max_inner"])})
+    return d
 
 
 # ------------------------------------------------------------------ roofline
@@ -89,42 +129,62 @@ def algorithmic_flops(reps, p, grad):
     return float(flops.sum())
 
 
-def fp32_peak_tflops():
-    """152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x the maximum SM clock."""
-    mhz = 2070.0
+def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
         try:
-            mhz = float(json.load(open(path)).get("sm_max_mhz", mhz))
+            return json.load(open(path))
         except Exception:
             pass
-    return 152 * 128 * 2 * mhz * 1e6 / 1e12, mhz
+    return {}
+
+
+def fp32_peak_tflops(sm_count):
+    """FP32 peak: the device's SM count x 128 FP32 lanes x 2 FLOP (FMA) x the
+    maximum SM clock (measured file, else the part's 2070 MHz)."""
+    mhz = float(_peaks().get("sm_max_mhz", 2070.0))
+    return sm_count * 128 * 2 * mhz * 1e6 / 1e12, mhz
 
 
 def hbm_peak_gbs():
-    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(path):
-        try:
-            return float(json.load(open(path))["hbm_gbs"]), "measured"
-        except Exception:
-            pass
+    pk = _peaks()
+    if "hbm_gbs" in pk:
+        return float(pk["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
 
 
-def hbm_path_measurement(device, flush, stream):
-    """The large-state path on 24-qubit cones: Q_12 with QAOA_FULL_CONE at p = 1
-    (the whole 2^24 cone state mixed on every qubit, one orbit), 32 points.
-    Algorithmic bytes per (cone, point) block = one write and one read of the
-    complex64 state (8 * 2^24 bytes each): the minimum once a block exceeds
-    on-chip memory.  Schedule bytes = the block transfers the pass list makes."""
+def kernels_sha1():
+    """Hash of the register kernel's sources and of the planner and upload code
+    that decide what it reads (the shell block lists, the descriptors)."""
+    h = hashlib.sha1()
+    for f in ("cone_kernel.cuh", "kernels_grad.cu", "device.cuh", "capi.cu", "plan.cpp", "block_orbits.cpp"):
+        h.update(open(os.path.join(ROOT, "paper_2101_10296_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def large_state_measurement(device, flush, product=True):
+    """The large-state path: energy of the 6x6 torus at p = 3 (one 28-qubit
+    cone: an 18-qubit inner block per merged shell block, 2 MiB each; the
+    product plan) or the Q_12 full cone at p = 1 (24-qubit blocks, a
+    cross-check plan), 32 points.  Algorithmic bytes per (cone, point, block)
+    = one write and one read of the complex64 block: the minimum once a block
+    exceeds on-chip memory."""
     import torch
     from paper_2101_10296_gb300 import inputs as I
     from paper_2101_10296_gb300 import qaoa
     P = 32
-    plan = qaoa.Plan(I.hypercube(12), 1, full_cone=True)
+    if product:
+        plan = qaoa.Plan(I.torus(6, 6), 3)
+        params = torch.tensor(I.draw_params(3, P, 36)[None], device=device)
+        what = "6x6 torus, p=3, 32 points, energy (product plan: 28-qubit cone, 18-qubit inner blocks)"
+    else:
+        plan = qaoa.Plan(I.hypercube(12), 1, full_cone=True)
+        params = torch.tensor(I.draw_params(1, P, 12)[None], device=device)
+        what = "Q12 full cone, p=1, 32 points, energy (cross-check plan: 24-qubit blocks)"
     plan.upload()
-    params = torch.tensor(I.draw_params(1, P, 12)[None], device=device)
-    for _ in range(2):
+    reps = plan.reps()
+    blocks = plan.shell_blocks()
+    for _ in range(3):
         plan.energy(params)
     torch.cuda.synchronize()
     plan.set_timing(True)
@@ -135,36 +195,20 @@ def hbm_path_measurement(device, flush, stream):
     ms, launches, _ = plan.kernel_time()
     plan.set_timing(False)
     ms /= max(launches, 1)
-    block = 8 * 2 ** 24
-    alg = 2 * block * P
-    # core-tile schedule, energy: the 14 outer qubits in one shared-memory chunk
-    # window of 10 and one register window of 4 -> a generating pass (write), a
-    # mixing pass (read + write) and the core pass (read)
-    windows, left = 0, 24 - 10
-    while left > 0:
-        left -= min(left, 10) if left > 5 else left
-        windows += 1
-    sched = 2 * windows * block * P
+    alg = float(sum(2 * 8 * (2 ** int(n)) * int(b) for n, b in zip(reps["n_inner"], blocks))) * P
     peak, basis = hbm_peak_gbs()
+    status = plan.device_status()
+    plan.close()
     return {
-        "workload": "Q12 full cone, p=1, 32 points: 24-qubit blocks (energy)",
+        "workload": what,
         "ms_per_call": ms,
+        "algorithmic_bytes_per_call": alg,
         "achieved_algorithmic_gbs": alg / (ms / 1e3) / 1e9,
-        "achieved_schedule_gbs": sched / (ms / 1e3) / 1e9,
         "peak_gbs": peak,
         "peak_basis": basis,
         "frac_algorithmic": alg / (ms / 1e3) / 1e9 / peak,
-        "frac_schedule": sched / (ms / 1e3) / 1e9 / peak,
+        "device_status": status,
     }
-
-
-def kernels_sha1():
-    """Hash of the adjoint kernel's sources and of the planner and upload code
-    that decide what it reads (the shell block lists, the descriptors)."""
-    h = hashlib.sha1()
-    for f in ("cone_kernel.cuh", "kernels_grad.cu", "device.cuh", "capi.cu", "plan.cpp", "block_orbits.cpp"):
-        h.update(open(os.path.join(ROOT, "paper_2101_10296_gb300", "csrc", f), "rb").read())
-    return h.hexdigest()
 
 
 # -------------------------------------------------------------------- clocks
@@ -174,8 +218,9 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
+    def __init__(self, index, period_ms=100):
         self.index = index
+        self.period_ms = period_ms
         self.proc = None
         # the raw samples go to $QAOA_BENCH_CLOCKS_DIR (default: the temp directory);
         # the JSON line carries their summary
@@ -187,8 +232,15 @@ class ClockSampler:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.period_ms)],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
+            # start timing only once the sampler is producing samples
+            t0 = time.perf_counter()
+            while time.perf_counter() - t0 < 3.0 and self.proc.poll() is None:
+                self.fh.flush()
+                if os.path.getsize(self.path) > 0:
+                    break
+                time.sleep(0.02)
         except Exception:
             self.proc = None
         return self
@@ -264,37 +316,72 @@ def make_oracle_pool(cores):
     return mp.get_context("spawn").Pool(cores, initializer=_init_oracle_worker)
 
 
-def oracle_sample(target_s=15.0, pool=None, seed=0):
-    """Times the FP64 oracle (per-edge cone energy + adjoint gradient) on a
-    random sample of (graph, edge) terms at point 0, sized to about target_s
-    of wall time, and a smaller sample on one core; returns (evals/s
-    extrapolated to whole (graph, point) evals, processes, seconds, terms,
-    one-core evals/s)."""
+_REPS = {}
+
+
+def workload_reps():
+    """(graph, edge, cone qubits, cone edges) of every representative of the
+    orbit-reduced workload, from the host planner (plan time, like the paper's
+    t_aut, is outside every rate on both arms)."""
+    if "reps" not in _REPS:
+        from paper_2101_10296_gb300 import qaoa
+        graphs, _ = workload()
+        plan = qaoa.Plan(graphs, P_DEPTH, orbits=True)
+        r = plan.reps()
+        plan.close()
+        _REPS["reps"] = (r["graph"].astype(np.int64), r["edge"].astype(np.int64),
+                         r["n_qubits"].astype(np.int64), r["n_cone_edges"].astype(np.int64))
+    return _REPS["reps"]
+
+
+def oracle_cost(nq, ne):
+    """The oracle's work on one cone, up to a constant: a cut table of ne edges
+    and about 3 nq butterfly passes over 2^nq amplitudes."""
+    return (np.asarray(ne, dtype=np.float64) + 3.0 * np.asarray(nq, dtype=np.float64)) * np.ldexp(
+        1.0, np.asarray(nq, dtype=np.int64))
+
+
+def oracle_sample(target_s=15.0, pool=None, seed=0, max_qubits=18):
+    """Times the FP64 oracle (per-cone energy + adjoint gradient) on a random
+    sample of the workload's representatives (cones of at most max_qubits
+    qubits) at point 0, sized to about target_s of wall time, and a smaller
+    sample on one core.  The time of one whole evaluation point (every
+    representative of the 48 graphs) is extrapolated with the cost model
+    ``oracle_cost`` calibrated on the sample.  Returns (evals/s, processes,
+    seconds, terms, one-core evals/s)."""
     rng = np.random.default_rng(seed)
     cores = os.cpu_count() or 1
+    g_of, e_of, nq, ne = workload_reps()
+    total_cost = float(oracle_cost(nq, ne).sum())
+    small = np.nonzero(nq <= max_qubits)[0]
     own = pool is None
     if own:
         pool = make_oracle_pool(cores)
     try:
-        probe = [(0, k, 0) for k in range(cores)]
+        probe = [(int(g_of[r]), int(e_of[r]), 0) for r in rng.choice(small, cores)]
         pool.map(_oracle_term_job, probe, chunksize=1)  # warms the workers
         t0 = time.perf_counter()
         pool.map(_oracle_term_job, probe, chunksize=1)
         t_one = (time.perf_counter() - t0)  # ~ one term per process
         n_terms = int(max(cores, min(50000, 0.8 * target_s / max(t_one, 1e-4) * cores)))
-        jobs = [(int(rng.integers(len(SEEDS))), int(rng.integers(N_VERT * DEG // 2)), 0) for _ in range(n_terms)]
+        pick = rng.choice(small, n_terms)
+        jobs = [(int(g_of[r]), int(e_of[r]), 0) for r in pick]
         t0 = time.perf_counter()
         pool.map(_oracle_term_job, jobs, chunksize=max(1, n_terms // (8 * cores)))
         dt = time.perf_counter() - t0
+        cost = float(oracle_cost(nq[pick], ne[pick]).sum())
         # the same kind of terms on one core, about a tenth of the time budget
         n_one = int(max(1, min(n_terms, 0.1 * target_s / max(t_one, 1e-4))))
         dt_one = pool.apply(_oracle_serial_job, (jobs[:n_one],))
+        cost_one = float(oracle_cost(nq[pick[:n_one]], ne[pick[:n_one]]).sum())
     finally:
         if own:
             pool.close()
             pool.join()
-    terms_per_eval = N_VERT * DEG // 2  # random 3-regular: trivial Aut, one cone per edge
-    return n_terms / dt / terms_per_eval, cores, dt, n_terms, n_one / dt_one / terms_per_eval
+    n_graphs = int(g_of.max()) + 1
+    t_point = dt / cost * total_cost            # all representatives of every graph, one point, on the pool
+    t_point_one = dt_one / cost_one * total_cost  # the same on one core
+    return n_graphs / t_point, cores, dt, n_terms, n_graphs / t_point_one
 
 
 def max_over_ranks(x, dist, device):
@@ -314,6 +401,25 @@ def whole_job_value(world, evals_per_rank, ms_per_step):
 
 # ---------------------------------------------------------------- GPU arm
 
+def timed_steps(fn, steps, warmup, flush, stream):
+    """W warm-up calls, then K calls each between CUDA events on ``stream``
+    with the L2 flush written before the first event; returns ms per call."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    out = []
+    for k in range(steps):
+        flush.fill_(k & 0xFF)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        out.append(a.elapsed_time(b))
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2101_10296_gb300 import qaoa
@@ -323,12 +429,14 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as dist
     device = torch.device("cuda", local_rank)
     torch.cuda.set_device(device)
+    sm_count = torch.cuda.get_device_properties(device).multi_processor_count
     graphs, theta = workload()
     G, P, p = len(graphs), N_POINTS, P_DEPTH
     evals = G * P
 
     pool = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        workload_reps()  # plan the representatives before the pool spawns
         pool = make_oracle_pool(os.cpu_count() or 1)  # spawned before the first GPU call
 
     t0 = time.perf_counter()
@@ -374,6 +482,16 @@ def run_ours(args, rank, world, local_rank):
     ms_per_step = max_over_ranks(sum(step_ms) / len(step_ms), dist, device)
     value = whole_job_value(world, evals, ms_per_step)
 
+    # plain all-edge: the same workload with every edge its own cone, same kernels, same timing
+    t0 = time.perf_counter()
+    plain = qaoa.Plan(graphs, p, orbits=False)
+    t_plain = time.perf_counter() - t0
+    plain.upload()
+    plain_ms = max_over_ranks(statistics.mean(timed_steps(lambda: plain.energy_grad(params), args.steps,
+                                                          args.warmup, flush, stream)), dist, device)
+    plain_reps = int(plain.info()["n_reps"])
+    plain.close()
+
     # e2e: public API with host buffers, copies inside the timed region
     host_params = torch.tensor(theta).pin_memory()
     host_e = torch.empty(G, P, dtype=torch.float64).pin_memory()
@@ -393,26 +511,10 @@ def run_ours(args, rank, world, local_rank):
             e2e_ms.append(s_ev.elapsed_time(e_ev))
     e2e_step = max_over_ranks(sum(e2e_ms) / len(e2e_ms), dist, device)
 
-    # energy-only and plain all-edge comparisons (same kernels, not the headline)
     def timed(fn, reps_=5):
-        for _ in range(2):
-            fn()
-        torch.cuda.synchronize()
-        out = []
-        for k in range(reps_):
-            flush.fill_(k & 0xFF)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            fn()
-            b.record(stream)
-            torch.cuda.synchronize()
-            out.append(a.elapsed_time(b))
-        return sum(out) / len(out)
+        return statistics.mean(timed_steps(fn, reps_, 2, flush, stream))
 
     energy_ms = timed(lambda: plan.energy(params))
-    plain = qaoa.Plan(graphs, p, orbits=False)
-    plain.upload()
-    plain_ms = timed(lambda: plain.energy_grad(params))
     # every shell count vector evolved as its own block (no merging by the cones' symmetries)
     every = qaoa.Plan(graphs, p, block_plain=True)
     every.upload()
@@ -429,26 +531,56 @@ def run_ours(args, rank, world, local_rank):
     cc_e, _ = ccplan.energy_grad(params)
     ref_e, _ = plan.energy_grad(params)
     cc_err = float((cc_e - ref_e).abs().max() / ref_e.abs().max())
-    # the training driver on this workload: Adam on -E from the same 64 starts per graph
+    cc_reps = int(ccplan.info()["n_reps"])
+    ccplan.close()
+
+    # graphs without symmetry: 4 x random 3-regular n = 2000, p = 2, 64 points
+    sg, stheta = side_workload()
+    sparams = torch.tensor(stheta, device=device)
+    splan = qaoa.Plan(sg, 2, orbits=True)
+    splan.upload()
+    s_ms = timed(lambda: splan.energy_grad(sparams))
+    splain = qaoa.Plan(sg, 2, orbits=False)
+    splain.upload()
+    sp_ms = timed(lambda: splain.energy_grad(sparams))
+    s_evals = len(sg) * stheta.shape[1]
+    side = {"workload": "rr3-n2000x4-p2-P64: 4 random 3-regular graphs n=2000 (seeds 1-4), p=2, 64 points each, "
+                        "energy+grad",
+            "energy_grad_evals_per_s": world * s_evals / (s_ms / 1e3),
+            "plain_all_edge_evals_per_s": world * s_evals / (sp_ms / 1e3),
+            "n_reps": int(splan.info()["n_reps"])}
+    # the training driver: Adam on -E from 64 starts per graph, timed after a warm-up step
     from paper_2101_10296_gb300 import train as qtrain
     tr_steps = 50
-    tr = qtrain.train(graphs, p, points=P, steps=tr_steps, lr=0.03, seed=1, plan=plan, device=device)
-    training = {"steps": tr_steps, "points_per_graph": P, "seconds": tr["seconds"],
+    target = 0.75 * np.array([len(e) for _, e in sg], dtype=np.float64)
+    tr = qtrain.train(sg, 2, points=64, steps=tr_steps, lr=0.03, seed=1, plan=splan, device=device, target=target)
+    training = {"workload": side["workload"], "steps": tr_steps, "points_per_graph": 64, "seconds": tr["seconds"],
                 "energy_grad_evals_per_s": world * tr["evals"] / tr["seconds"],
-                "best_energy_per_edge": float(np.mean(tr["energy"] / np.array([len(e) for _, e in graphs]))),
-                "note": "Adam (torch.optim) on the autograd energy, best point tracked on the host every step"}
+                "best_energy_per_edge": float(np.mean(tr["energy"] / np.array([len(e) for _, e in sg]))),
+                "target_energy_per_edge": 0.75,
+                "steps_to_target": [None if s is None else int(s) for s in tr["steps_to_target"]],
+                "seconds_to_target": tr["seconds_to_target"],
+                "note": "Adam (torch.optim) on the autograd energy; one warm-up step before the clock starts; "
+                        "best point tracked on the device, one host read per step"}
+    splan.close()
+    splain.close()
 
-    # roofline of the dominant kernel (the adjoint cone kernel)
+    # roofline of the dominant kernel: the adjoint register kernel (every cone of the
+    # workload is register-resident at p = 1; the events bracket its launch)
     flops = algorithmic_flops(reps, p, grad=True) * P
     kern_avg_ms = kern_ms / max(kern_launches, 1)
     achieved = flops / (kern_avg_ms / 1e3) / 1e12
-    peak, mhz = fp32_peak_tflops()
+    peak, mhz = fp32_peak_tflops(sm_count)
     traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["kernels_sha1"] == kernels_sha1() else None
     amp_updates = float((np.ldexp(1.0, reps["n_qubits"].astype(np.int64)) * p).sum()) * P
     evolved = float((reps["n_blocks"] * np.ldexp(1.0, reps["n_inner"].astype(np.int64)) * p).sum()) * P
 
-    hbm = hbm_path_measurement(device, flush, stream) if not args.no_aux else None
+    large = None
+    if not args.no_aux:
+        large = {"product": large_state_measurement(device, flush, product=True),
+                 "full_cone_q12": large_state_measurement(device, flush, product=False)}
     status = plan.device_status()
+    plan.close()
     if rank != 0:
         return None
     out = {
@@ -463,53 +595,54 @@ def run_ours(args, rank, world, local_rank):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f32",
-        "data": "synthetic",
-        "config": {
-            "workload": WORKLOAD,
-            "graphs": G, "n": N_VERT, "degree": DEG, "p": p, "points_per_graph": P,
-            "orbit_reduction": True, "n_reps": int(info["n_reps"]), "max_cone_qubits": int(info["max_qubits"]),
-            "max_inner_qubits": int(info["max_inner"]),
-            "l2": "512 MB buffer written between timed steps (outside the events)",
-            "parallelism": f"replicas x{world}",
-        },
+        "data": "synthetic (seeded stand-ins for the paper's benchmark graphs)",
+        "config": config_dict(world, info),
+        "plain_all_edge_evals_per_s": whole_job_value(world, evals, plain_ms),
+        "orbit_speedup_vs_plain": plain_ms / ms_per_step,
+        "plain_all_edge": {"n_reps": plain_reps, "ms_per_step": plain_ms, "plan_s": t_plain},
         "roofline": {
             "bound": "alu",
-            "kernel": "reg_cone_kernel<4, u32, adjoint, p=2>",
+            "kernel": "reg_cone_kernel<R=4, u32, adjoint, p=1>",
             "achieved": achieved,
             "peak": peak,
             "unit": "TFLOP/s",
             "frac": achieved / peak,
             "traffic": traffic,
+            "traffic_source": TRAFFIC["source"] if traffic is not None else
+            "null: the kernel or planner sources changed since the last ncu capture",
             "algorithmic_flops_per_launch": flops,
             "kernel_ms_per_launch": kern_avg_ms,
-            "peak_basis": f"FP32: 152 SMs x 128 lanes x 2 FLOP x {mhz:.0f} MHz (max SM clock)",
+            "peak_basis": f"FP32: {sm_count} SMs (device property) x 128 lanes x 2 FLOP x {mhz:.0f} MHz "
+                          f"(maximum SM clock, MEASURED_PEAKS.json)",
         },
         "e2e": {"value": whole_job_value(world, evals, e2e_step), "unit": UNIT,
                 "h2d_bytes_per_step": int(theta.nbytes), "d2h_bytes_per_step": int(G * P * (1 + 2 * p) * 8)},
         "gpu_launches": int(all_launches),
         "clocks": clocks,
         "energy_only_evals_per_s": world * evals / (energy_ms / 1e3),
-        "plain_all_edge_evals_per_s": world * evals / (plain_ms / 1e3),
         "shell_blocks": blocks,
-        "training": training,
-        "cone_classes": {"n_classes": int(ccplan.info()["n_reps"]), "plan_s": t_cc,
+        "cone_classes": {"n_classes": cc_reps, "plan_s": t_cc,
                          "energy_grad_evals_per_s": world * evals / (cc_ms / 1e3),
                          "max_rel_energy_diff_vs_orbit_path": cc_err},
+        "no_symmetry_side": side,
+        "training": training,
         "amp_updates_per_s": world * amp_updates / (ms_per_step / 1e3),
         "evolved_amp_updates_per_s": world * evolved / (ms_per_step / 1e3),
         "plan_s": t_plan,
         "t_orbits_s": info["t_orbits_s"],
         "wall_s_timed_region": wall,
         "device_status": status,
-        "hbm_path": hbm,
+        "large_state": large,
     }
     if pool is not None:
         try:
             v, cores, dt, nt, v1 = oracle_sample(target_s=args.cpu_seconds, pool=pool)
             out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                   "sample": f"{nt} random (graph, edge) cone terms at point 0, FP64 energy + "
-                                             f"adjoint gradient, {dt:.1f} s on {cores} processes, "
-                                             f"scaled to whole evals of 3000 terms",
+                                   "sample": f"{nt} random representative cone terms (<= 18 qubits) at point 0, "
+                                             f"FP64 energy + adjoint gradient, {dt:.1f} s on {cores} processes; "
+                                             f"extrapolated to whole evals (all {len(workload_reps()[0])} "
+                                             f"representatives) by a cost model calibrated on the sample",
+                                   "extrapolated": True,
                                    "one_core_value": v1}
         finally:
             pool.close()
@@ -522,6 +655,7 @@ def run_reference(args, rank, world):
     if rank != 0:
         return None
     cores = os.cpu_count() or 1
+    workload_reps()
     pool = make_oracle_pool(cores)
     try:
         budget = max(5.0, min(30.0, 150.0 / max(args.steps + args.warmup, 1)))
@@ -538,23 +672,22 @@ def run_reference(args, rank, world):
         pool.close()
         pool.join()
     value = statistics.mean(vals)
+    sample = (f"per step {statistics.mean(samples):.0f} random representative cone terms (<= 18 qubits) at point 0 "
+              f"(FP64 energy + adjoint gradient) on {cores} processes, extrapolated to whole evals by a cost "
+              f"model calibrated on the sample")
     return {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * G_P_EVALS / value if value else None,
+        "warmup": args.warmup, "ms_per_step": 1e3 * 48 * N_POINTS / value if value else None,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "impl": "reference",
-        "config": {"workload": WORKLOAD, "graphs": 4, "n": N_VERT, "degree": DEG, "p": P_DEPTH,
-                   "points_per_graph": N_POINTS, "orbit_reduction": True,
-                   "parallelism": f"{cores} host processes"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"per step {statistics.mean(samples):.0f} random cone terms at point 0 "
-                                   f"(FP64 energy + adjoint gradient), scaled to whole evals of 3000 terms",
-                         "one_core_value": statistics.mean(ones)},
+        "data": "synthetic (seeded stand-ins for the paper's benchmark graphs)", "impl": "reference",
+        "extrapolated": True,
+        "config": config_dict(world, {"n_edges_total": sum(len(e) for _, e in workload()[0]),
+                                      "n_reps": len(workload_reps()[0]),
+                                      "max_qubits": int(workload_reps()[2].max()), "max_inner": 2}),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                         "extrapolated": True, "one_core_value": statistics.mean(ones)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
-
-
-G_P_EVALS = len(SEEDS) * N_POINTS
 
 
 # ------------------------------------------------------------------ suite
@@ -566,17 +699,17 @@ def suite_configs():
     from paper_2101_10296_gb300 import inputs as I
     return [
         ("1. C_20(1,4) p=1, 1 point", [I.circulant(20, [1, 4])], 1, 1),
-        ("2. rr3 n=2000 x4, p=2, 64 points", [I.random_regular(2000, 3, s) for s in SEEDS], 2, 64),
+        ("2. rr3 n=2000 x4, p=2, 64 points", [I.random_regular(2000, 3, s) for s in SIDE_SEEDS], 2, 64),
         ("3a. torus 100x100 + C_5000(1,7), p=2, 32 points", [I.torus(100, 100), I.circulant(5000, [1, 7])], 2, 32),
         ("3b. Q_12 + C_5000(1,7,23), p=1, 32 points", [I.hypercube(12), I.circulant(5000, [1, 7, 23])], 1, 32),
-        ("4a. rr3 n=24 x4, p=3, 128 points", [I.random_regular(24, 3, s) for s in SEEDS], 3, 128),
+        ("4a. rr3 n=24 x4, p=3, 128 points", [I.random_regular(24, 3, s) for s in SIDE_SEEDS], 3, 128),
         ("4b. torus 8x8, p=2, 128 points", [I.torus(8, 8)], 2, 128),
         ("4c. torus 6x6, p=3, 128 points", [I.torus(6, 6)], 3, 128),
         ("5. 48-graph mix, p=1, 256 points", [b() for _, b in I.mixed_benchmark_graphs()], 1, 256),
         # beyond the five: a signed (edge-coloured) objective of Sec. 4 on configuration 2's graphs
         ("6. rr3 n=2000 x4 with random +-1 weights, p=2, 64 points",
-         [I.random_regular(2000, 3, s) for s in SEEDS], 2, 64,
-         [np.random.default_rng(10 + s).choice([1, -1], 3000) for s in SEEDS]),
+         [I.random_regular(2000, 3, s) for s in SIDE_SEEDS], 2, 64,
+         [np.random.default_rng(10 + s).choice([1, -1], 3000) for s in SIDE_SEEDS]),
     ]
 
 
@@ -604,19 +737,7 @@ def run_suite(args):
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=device)
 
     def timed(fn, reps=3, warmup=3):
-        for _ in range(warmup):
-            fn()
-        torch.cuda.synchronize()
-        out = []
-        for k in range(reps):
-            flush.fill_(k & 0xFF)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record()
-            fn()
-            b.record()
-            torch.cuda.synchronize()
-            out.append(a.elapsed_time(b))
-        return sum(out) / len(out)
+        return statistics.mean(timed_steps(fn, reps, warmup, flush, torch.cuda.current_stream()))
 
     rows = []
     for cfg in suite_configs():
@@ -715,10 +836,13 @@ def run_suite(args):
 # times, so these hold at most a few GB on the device).  Each runs the call
 # twice: a warm-up and the one to capture.
 PROFILE_CASES = {
+    "reg-mix48": "the benchmark workload (48-graph mix, p=1, 256 points): energy+grad",
+    "reg-mix48-small": "the 48-graph mix, p=1, 16 points: energy+grad",
     "reg-adjoint-rr3-n2000": "1 random 3-regular graph n=2000 (seed 1), p=2, 8 points: energy+grad",
-    "reg-bench": "the benchmark workload (4 x rr3 n=2000, p=2, 64 points): energy+grad",
+    "reg-rr3-x4": "4 x rr3 n=2000, p=2, 64 points: energy+grad",
     "split-adjoint-rr3-n24": "1 random 3-regular graph n=24 (seed 1), p=3, 8 points: energy+grad",
     "split-adjoint-torus6": "6x6 torus, p=3, 2 points: energy+grad",
+    "split-energy-torus6": "6x6 torus, p=3, 4 points: energy",
     "split-energy-q12-fullcone": "Q_12 full cone, p=1, 2 points: energy",
 }
 
@@ -727,13 +851,19 @@ def run_case(name):
     import torch
     from paper_2101_10296_gb300 import inputs as I
     from paper_2101_10296_gb300 import qaoa
-    if name == "reg-bench":
+    if name in ("reg-mix48", "reg-mix48-small"):
         graphs, theta = workload()
+        if name == "reg-mix48-small":
+            theta = np.ascontiguousarray(theta[:, :16])
+        p, grad, kw = 1, True, {}
+    elif name == "reg-rr3-x4":
+        graphs, theta = side_workload()
         p, grad, kw = 2, True, {}
     else:
         spec = {"reg-adjoint-rr3-n2000": ([I.random_regular(2000, 3, 1)], 2, 8, True, {}),
                 "split-adjoint-rr3-n24": ([I.random_regular(24, 3, 1)], 3, 8, True, {}),
                 "split-adjoint-torus6": ([I.torus(6, 6)], 3, 2, True, {}),
+                "split-energy-torus6": ([I.torus(6, 6)], 3, 4, False, {}),
                 "split-energy-q12-fullcone": ([I.hypercube(12)], 1, 2, False, {"full_cone": True})}[name]
         graphs, p, P, grad, kw = spec
         theta = np.stack([I.draw_params(p, P, s + 1) for s in range(len(graphs))])
@@ -756,7 +886,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-aux", action="store_true", help="skip the auxiliary large-state measurement")
+    ap.add_argument("--no-aux", action="store_true", help="skip the auxiliary large-state measurements")
     ap.add_argument("--suite", action="store_true", help="measure every benchmark configuration instead")
     ap.add_argument("--case", choices=sorted(PROFILE_CASES), help="run one small profiling workload and exit")
     args = ap.parse_args()

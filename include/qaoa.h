@@ -317,9 +317,13 @@ int qaoa_energy_grad(const qaoa_plan *plan, int64_t n_points,
  * path -- is carved from one static device array of QAOA_NOALLOC_SCRATCH_MB
  * MiB that every device loading the library keeps until the process exits.
  * The plan must already be on the device (qaoa_plan_upload, which does
- * allocate; call it during set-up).  The first call on a device looks up the
- * array's device address once; make that first call before any stream
- * capture.  A call whose tables plus one state block would not fit returns
+ * allocate; call it during set-up).  The array occupies device memory from
+ * the moment its module is loaded on a device; qaoa_plan_upload forces that
+ * load and looks up the array's device address, so the memory is committed
+ * during set-up and a qaoa_energy_noalloc call allocates nothing, not even
+ * its first.  Should that lookup fail at upload (it is not reported there),
+ * the first qaoa_energy_noalloc call on the device repeats it, which loads
+ * the module then; make that first call before any stream capture.  A call whose tables plus one state block would not fit returns
  * QAOA_E_INVALID with the sizes in the message, before launching anything.
  * Every call uses the same array and leaves its contents behind (all of it
  * is rewritten before being read, nothing needs clearing); calls that

@@ -14,6 +14,10 @@
 
 using namespace qaoa;
 
+namespace qaoa {
+int noalloc_prepare();  // noalloc.cu
+}
+
 namespace {
 
 int cuda_fail(cudaError_t e, const char *what) {
@@ -475,6 +479,12 @@ extern "C" int qaoa_plan_upload(qaoa_plan *plan) {
             rc = cuda_fail(e, "cudaMemset");
     }
     if (rc == QAOA_OK && !d->big.empty() && (e = split_prepare()) != cudaSuccess) rc = cuda_fail(e, "kernel attributes");
+    // commit qaoa_energy_noalloc's static scratch on this device now, during set-up
+    // (not fatal here: that entry point repeats the lookup and reports a failure)
+    if (rc == QAOA_OK) {
+        const std::string keep = qaoa_last_error();
+        if (noalloc_prepare() != QAOA_OK) set_error(keep);
+    }
     if (rc == QAOA_OK && (e = cudaDeviceSynchronize()) != cudaSuccess) rc = cuda_fail(e, "upload");
     if (rc != QAOA_OK) qaoa_device_release(plan);
     return rc;

@@ -6,7 +6,11 @@
 // state blocks of cones on the large-state path) comes from one file-scope
 // device array of fixed size instead of cudaMallocAsync.  Nothing is
 // allocated by this call; the plan's own device copy must already exist
-// (qaoa_plan_upload, a set-up step that does allocate).
+// (qaoa_plan_upload, a set-up step that does allocate).  The array itself
+// takes device memory when the CUDA module holding it is loaded, which with
+// lazy module loading happens at the first use of its symbol: the upload
+// makes that first use (noalloc_prepare), so the array's memory is committed
+// during set-up and not inside a qaoa_energy_noalloc call.
 #include <mutex>
 #include <string>
 
@@ -49,6 +53,19 @@ int scratch_address(int dev, unsigned char **out) {
 }
 
 }  // namespace
+
+namespace qaoa {
+// Looks up the array's address on the current device (loading its module, the
+// one allocation the array ever makes).  Called by qaoa_plan_upload; a failure
+// there is not fatal, since qaoa_energy_noalloc repeats the lookup and reports
+// it.
+int noalloc_prepare() {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return QAOA_E_CUDA;
+    unsigned char *p = nullptr;
+    return scratch_address(dev, &p);
+}
+}  // namespace qaoa
 
 extern "C" int qaoa_energy_noalloc(const qaoa_plan *plan, int64_t n_points, const double *params_dev,
                                    double *energy_dev, double *terms_dev, qaoa_stream_t stream) {

@@ -325,6 +325,20 @@ class Plan:
         G, P = params.shape[0], params.shape[1]
         if out is None:
             out = torch.empty(G, P, dtype=torch.float64, device=params.device)
+
+        def _need(t, shape, name):
+            # the library writes float64 values through the raw pointer: anything
+            # else would be written past the end of the caller's buffer
+            if not isinstance(t, torch.Tensor):
+                raise TypeError(f"{name} must be a torch tensor")
+            if t.dtype != torch.float64 or not t.is_cuda or t.device != params.device:
+                raise ValueError(f"{name} must be a float64 tensor on {params.device}")
+            if tuple(t.shape) != shape or not t.is_contiguous():
+                raise ValueError(f"{name} must be a contiguous tensor of shape {list(shape)}")
+
+        _need(out, (G, P), "out")
+        if terms is not None:
+            _need(terms, (self.info()["n_reps"], P), "terms")
         _check(lib().qaoa_energy_noalloc(self._h, P, C.c_void_p(params.data_ptr()), C.c_void_p(out.data_ptr()),
                                          C.c_void_p(terms.data_ptr()) if terms is not None else None,
                                          _stream_handle(stream)))
