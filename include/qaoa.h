@@ -163,6 +163,11 @@ typedef struct qaoa_plan_info_t {
     double t_orbits_s;      /* wall time of orbit finding (all graphs) */
     double t_cones_s;       /* wall time of cone extraction */
     int32_t orbits_complete; /* 1 if every graph's search finished in budget */
+    /* large-state cones by schedule (0 without large-state cones): on the
+     * general schedule for the energy, and for the gradient (the rest of
+     * n_big runs on the core-tile schedule) */
+    int64_t n_big_general_energy;
+    int64_t n_big_general_grad;
 } qaoa_plan_info_t;
 
 int qaoa_plan_info(const qaoa_plan *plan, qaoa_plan_info_t *info);

@@ -24,7 +24,7 @@ LIB = os.path.join(PKG, "libqaoa.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 HOST_SRC = ["graph.cpp", "orbits.cpp", "plan.cpp", "cone_classes.cpp", "block_orbits.cpp"]
 CUDA_SRC = ["kernels.cu", "kernels_grad.cu", "big.cu", "big_split.cu", "capi.cu", "noalloc.cu"]
-HEADERS = ["host.hpp", "device.cuh", "big.cuh", "big_common.cuh", "devplan.cuh", "cone_kernel.cuh"]
+HEADERS = ["host.hpp", "device.cuh", "big.cuh", "big_common.cuh", "devplan.cuh", "cone_kernel.cuh", "dev_math.cuh"]
 
 
 def _nvcc():

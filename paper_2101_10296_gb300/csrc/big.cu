@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(128) big_pass_kernel(const __grid_constant__ B
         const int g = C->graph;
         const int64_t gj = int64_t(g) * L.P + j;
         const float2 *__restrict__ lut = L.lut + gj * p * L.cmax1;
-        const float2 *__restrict__ cs = L.cs + gj * p;
+        const float4 *__restrict__ cs = L.cs + gj * p;
         // inner index of (lane, register i): xb | (i << b) | lane
         const int64_t lowmask = (int64_t(1) << (b - 5)) - 1;
         const int64_t xb = ((tile & lowmask) << 5) | ((tile >> (b - 5)) << (b + 5));
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(128) big_pass_kernel(const __grid_constant__ B
                     break;
                 }
                 case kOpMix: {
-                    const float2 c_s = __ldg(cs + l);
+                    const float4 c_s = __ldg(cs + l);
                     for (int q = op.q0; q < op.q1; ++q) {
                         if (q < 5) {
                             const int m = 1 << q;
@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(128) big_pass_kernel(const __grid_constant__ B
                                 float2 ot;
                                 ot.x = __shfl_xor_sync(kFull, x[i].x, m);
                                 ot.y = __shfl_xor_sync(kFull, x[i].y, m);
-                                x[i] = rot(x[i], ot, c_s.x, c_s.y);
+                                x[i] = rot(x[i], ot, c_s);
                             }
                         } else {
                             const int rq = q - b;
@@ -119,8 +119,8 @@ __global__ void __launch_bounds__(128) big_pass_kernel(const __grid_constant__ B
                                     if (i & (1 << rb)) continue;
                                     const int i2 = i | (1 << rb);
                                     const float2 a = x[i], bb = x[i2];
-                                    x[i] = rot(a, bb, c_s.x, c_s.y);
-                                    x[i2] = rot(bb, a, c_s.x, c_s.y);
+                                    x[i] = rot(a, bb, c_s);
+                                    x[i2] = rot(bb, a, c_s);
                                 }
                             }
                         }
@@ -147,9 +147,15 @@ __global__ void __launch_bounds__(128) big_pass_kernel(const __grid_constant__ B
                 }
                 case kOpUnmix: {
                     if (GRAD) {
-                        const float2 c_s = __ldg(cs + l);
-                        float d = 0.f;
+                        const float4 c_s = __ldg(cs + l);
+                        // At the last layer lambda = O psi (O = -1/2 Z_0 Z_1), and
+                        // <psi|O X_q|psi> is real for every q other than 0 and 1 (X_q
+                        // commutes with O and with the mixers of other qubits): only
+                        // those two enter d/d beta_p, the others are rounding noise.
+                        const int qd = l == p - 1 ? 2 : QAOA_MAX_CONE_QUBITS;
+                        Dfl acc{0.f, 0.f};
                         for (int q = op.q0; q < op.q1; ++q) {
+                            float d = 0.f;  // this qubit's terms, then added compensated
                             if (q < 5) {
                                 const int m = 1 << q;
 #pragma unroll
@@ -160,8 +166,8 @@ __global__ void __launch_bounds__(128) big_pass_kernel(const __grid_constant__ B
                                     ro.x = __shfl_xor_sync(kFull, r[i].x, m);
                                     ro.y = __shfl_xor_sync(kFull, r[i].y, m);
                                     d += imconj(r[i], xo);
-                                    x[i] = rot(x[i], xo, c_s.x, -c_s.y);
-                                    r[i] = rot(r[i], ro, c_s.x, -c_s.y);
+                                    x[i] = unrot(x[i], xo, c_s);
+                                    r[i] = unrot(r[i], ro, c_s);
                                 }
                             } else {
                                 const int rq = q - b;
@@ -174,15 +180,16 @@ __global__ void __launch_bounds__(128) big_pass_kernel(const __grid_constant__ B
                                         const int i2 = i | (1 << rb);
                                         const float2 a = x[i], bb = x[i2], ra = r[i], rbv = r[i2];
                                         d += imconj(ra, bb) + imconj(rbv, a);
-                                        x[i] = rot(a, bb, c_s.x, -c_s.y);
-                                        x[i2] = rot(bb, a, c_s.x, -c_s.y);
-                                        r[i] = rot(ra, rbv, c_s.x, -c_s.y);
-                                        r[i2] = rot(rbv, ra, c_s.x, -c_s.y);
+                                        x[i] = unrot(a, bb, c_s);
+                                        x[i2] = unrot(bb, a, c_s);
+                                        r[i] = unrot(ra, rbv, c_s);
+                                        r[i2] = unrot(rbv, ra, c_s);
                                     }
                                 }
                             }
+                            if (q < qd) dfl_add(acc, d);
                         }
-                        add_gp(2.f * wgt * sig * d, L.grad, gj * 2 * p + p + l);
+                        add_gp(acc, 2.f * wgt * sig, L.grad, gj * 2 * p + p + l);
                     }
                     break;
                 }
@@ -190,18 +197,23 @@ __global__ void __launch_bounds__(128) big_pass_kernel(const __grid_constant__ B
                     if (GRAD) {
                         const float2 *__restrict__ lt = lut + l * L.cmax1;
                         const float c0 = 0.5f * float(C->m);  // Im<r|x> = 0: C - c0 in place of C
+                        Dfl acc{0.f, 0.f};
                         float d = 0.f;
 #pragma unroll
                         for (int i = 0; i < NR; ++i) {
                             const int c = __popcll(lo[i & 3] ^ hi[i >> 2]);
                             d = fmaf(float(c) - c0, imconj(r[i], x[i]), d);
+                            if ((i & 7) == 7) {  // eight terms at a time into the compensated sum
+                                dfl_add(acc, d);
+                                d = 0.f;
+                            }
                             if (op.q0) {
                                 const float2 ph = __ldg(lt + c);
                                 x[i] = cmulc(x[i], ph);
                                 r[i] = cmulc(r[i], ph);
                             }
                         }
-                        add_gp(2.f * wgt * sig * d, L.grad, gj * 2 * p + l);
+                        add_gp(acc, 2.f * wgt * sig, L.grad, gj * 2 * p + l);
                     }
                     break;
                 }
@@ -238,7 +250,7 @@ __global__ void __launch_bounds__(128, 4) big_mix_kernel(const __grid_constant__
         int64_t j, y;
         decode_item(L, L.item0 + it, ci, j, y);
         const DevCone *__restrict__ C = L.cones + L.cone_ids[ci];
-        const float2 *__restrict__ cs = L.cs + (int64_t(C->graph) * L.P + j) * L.p;
+        const float4 *__restrict__ cs = L.cs + (int64_t(C->graph) * L.P + j) * L.p;
         const int64_t lowmask = (int64_t(1) << (b - 5)) - 1;
         const int64_t xb = ((tile & lowmask) << 5) | ((tile >> (b - 5)) << (b + 5));
         float2 *__restrict__ sp = L.psi + it * block_amps + xb + lane;
@@ -247,7 +259,7 @@ __global__ void __launch_bounds__(128, 4) big_mix_kernel(const __grid_constant__
         for (int i = 0; i < NR; ++i) x[i] = sp[int64_t(i) << b];
         for (int o = 0; o < ps.nops; ++o) {
             const BigOp op = ps.ops[o];
-            const float2 c_s = __ldg(cs + op.layer);
+            const float4 c_s = __ldg(cs + op.layer);
             for (int q = op.q0; q < op.q1; ++q) {
                 if (q < 5) {
                     const int m = 1 << q;
@@ -256,7 +268,7 @@ __global__ void __launch_bounds__(128, 4) big_mix_kernel(const __grid_constant__
                         float2 ot;
                         ot.x = __shfl_xor_sync(kFull, x[i].x, m);
                         ot.y = __shfl_xor_sync(kFull, x[i].y, m);
-                        x[i] = rot(x[i], ot, c_s.x, c_s.y);
+                        x[i] = rot(x[i], ot, c_s);
                     }
                 } else {
                     const int rq = q - b;
@@ -268,8 +280,8 @@ __global__ void __launch_bounds__(128, 4) big_mix_kernel(const __grid_constant__
                             if (i & (1 << rb)) continue;
                             const int i2 = i | (1 << rb);
                             const float2 a = x[i], bb = x[i2];
-                            x[i] = rot(a, bb, c_s.x, c_s.y);
-                            x[i2] = rot(bb, a, c_s.x, c_s.y);
+                            x[i] = rot(a, bb, c_s);
+                            x[i2] = rot(bb, a, c_s);
                         }
                     }
                 }
@@ -280,18 +292,25 @@ __global__ void __launch_bounds__(128, 4) big_mix_kernel(const __grid_constant__
     }
 }
 
-__global__ void big_prep_kernel(const double *params, int64_t GPp, int p, float2 *cs) {
+// (cos beta, sin beta) for the exact rotations, each as an FP32 pair hi + lo.
+// Rounded to one FP32 number each, the gate becomes r exp(-i beta' X) with
+// beta' - beta up to ~4e-8: the same shift for every amplitude, layer after
+// layer, which a small gradient (near a stationary point, a second
+// derivative times that shift) feels in full.  The lo parts (two more FMAs
+// per output) take the shift away; what remains is per-operation rounding.
+__global__ void big_prep_kernel(const double *params, int64_t GPp, int p, float4 *cs) {
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < GPp; i += int64_t(gridDim.x) * blockDim.x) {
         const int64_t gj = i / p, l = i % p;
         double sn, c;
         sincos(params[gj * 2 * p + p + l], &sn, &c);
-        cs[i] = make_float2(float(c), float(sn));
+        const float ch = float(c), sh = float(sn);
+        cs[i] = make_float4(ch, sh, float(c - double(ch)), float(sn - double(sh)));
     }
 }
 
 }  // namespace
 
-cudaError_t launch_big_prep(const double *params, int64_t GP, int p, float2 *cs, cudaStream_t s) {
+cudaError_t launch_big_prep(const double *params, int64_t GP, int p, float4 *cs, cudaStream_t s) {
     const int64_t n = GP * p;
     int blocks = int(std::min<int64_t>((n + 255) / 256, 1024));
     big_prep_kernel<<<blocks < 1 ? 1 : blocks, 256, 0, s>>>(params, n, p, cs);

@@ -2,30 +2,36 @@
 #pragma once
 
 #include "big.cuh"
+#include "dev_math.cuh"
 
 namespace qaoa {
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
-
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+// c me - i s other: one output of exp(-i beta X) on the pair (me, other),
+// with c = cs.x + cs.z and s = cs.y + cs.w (hi and lo FP32 parts)
+__device__ __forceinline__ float2 rot(float2 me, float2 o, float4 cs) {
+    return make_float2(fmaf(cs.x, me.x, fmaf(cs.y, o.y, fmaf(cs.z, me.x, cs.w * o.y))),
+                       fmaf(cs.x, me.y, fmaf(-cs.y, o.x, fmaf(cs.z, me.y, -cs.w * o.x))));
 }
-__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
-    return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
-}
-// Im(conj(a) b)
-__device__ __forceinline__ float imconj(float2 a, float2 b) { return a.x * b.y - a.y * b.x; }
-// c me - i s other: one output of exp(-i beta X) on the pair (me, other)
-__device__ __forceinline__ float2 rot(float2 me, float2 o, float c, float s) {
-    return make_float2(fmaf(c, me.x, s * o.y), fmaf(c, me.y, -s * o.x));
+// the same for exp(+i beta X)
+__device__ __forceinline__ float2 unrot(float2 me, float2 o, float4 cs) {
+    return make_float2(fmaf(cs.x, me.x, fmaf(-cs.y, o.y, fmaf(cs.z, me.x, -cs.w * o.y))),
+                       fmaf(cs.x, me.y, fmaf(cs.y, o.x, fmaf(cs.z, me.y, cs.w * o.x))));
 }
 
-// Warp sum in FP32, then one FP64 atomic into base[idx].
+// Warp sum in FP32, then one FP64 atomic into base[idx] (energies and terms,
+// whose sums do not cancel).
 __device__ __forceinline__ void add_gp(float v, double *base, int64_t idx) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
     if ((threadIdx.x & 31) == 0) atomicAdd(base + idx, double(v));
+}
+
+// Compensated warp sum of a derivative partial times w, then one FP64
+// atomic into base[idx].
+__device__ __forceinline__ void add_gp(Dfl v, float w, double *base, int64_t idx) {
+    v = dfl_warp_sum(dfl_scale(v, w));
+    if ((threadIdx.x & 31) == 0) atomicAdd(base + idx, dfl_value(v));
 }
 
 // Item -> (cone of the shape, point j, shell block y).  Cone c owns the items

@@ -124,7 +124,7 @@ __device__ __forceinline__ FirstMix first_mix(const BigLaunch &L, int64_t gj, in
 
 // exp(-i beta X) on register qubits [0, nbits) (nbits <= log2 NR).
 template <int NR>
-__device__ __forceinline__ void mix_regs(float2 (&x)[NR], int nbits, float c, float s) {
+__device__ __forceinline__ void mix_regs(float2 (&x)[NR], int nbits, float4 cs) {
 #pragma unroll
     for (int rb = 0; (1 << rb) < NR; ++rb) {
         if (rb < nbits) {
@@ -133,8 +133,8 @@ __device__ __forceinline__ void mix_regs(float2 (&x)[NR], int nbits, float c, fl
                 if (i & (1 << rb)) continue;
                 const int i2 = i | (1 << rb);
                 const float2 a = x[i], bb = x[i2];
-                x[i] = rot(a, bb, c, s);
-                x[i2] = rot(bb, a, c, s);
+                x[i] = rot(a, bb, cs);
+                x[i2] = rot(bb, a, cs);
             }
         }
     }
@@ -142,7 +142,7 @@ __device__ __forceinline__ void mix_regs(float2 (&x)[NR], int nbits, float c, fl
 
 // exp(-i beta X) on lane bits [0, nb).
 template <int NR>
-__device__ __forceinline__ void mix_lanes(float2 (&x)[NR], int nb, float c, float s) {
+__device__ __forceinline__ void mix_lanes(float2 (&x)[NR], int nb, float4 cs) {
     for (int lb = 0; lb < nb; ++lb) {
         const int m = 1 << lb;
 #pragma unroll
@@ -150,38 +150,41 @@ __device__ __forceinline__ void mix_lanes(float2 (&x)[NR], int nb, float c, floa
             float2 o;
             o.x = __shfl_xor_sync(kFull, x[i].x, m);
             o.y = __shfl_xor_sync(kFull, x[i].y, m);
-            x[i] = rot(x[i], o, c, s);
+            x[i] = rot(x[i], o, cs);
         }
     }
 }
 
 // Adjoint step of a mixer on register qubits [0, nbits): adds
-// Im<r|X_q|x> for each, then applies exp(+i beta X) to both states.
+// Im<r|X_q|x> for each (one qubit's terms at a time into the compensated
+// sum), then applies exp(+i beta X) to both states.
 template <int NR>
-__device__ __forceinline__ void unmix_regs_d(float2 (&x)[NR], float2 (&r)[NR], int nbits, float c, float s,
-                                             float &d) {
+__device__ __forceinline__ void unmix_regs_d(float2 (&x)[NR], float2 (&r)[NR], int nbits, float4 cs, Dfl &acc) {
 #pragma unroll
     for (int rb = 0; (1 << rb) < NR; ++rb) {
         if (rb < nbits) {
+            float d = 0.f;
 #pragma unroll
             for (int i = 0; i < NR; ++i) {
                 if (i & (1 << rb)) continue;
                 const int i2 = i | (1 << rb);
                 const float2 a = x[i], bb = x[i2], ra = r[i], rbv = r[i2];
                 d += imconj(ra, bb) + imconj(rbv, a);
-                x[i] = rot(a, bb, c, -s);
-                x[i2] = rot(bb, a, c, -s);
-                r[i] = rot(ra, rbv, c, -s);
-                r[i2] = rot(rbv, ra, c, -s);
+                x[i] = unrot(a, bb, cs);
+                x[i2] = unrot(bb, a, cs);
+                r[i] = unrot(ra, rbv, cs);
+                r[i2] = unrot(rbv, ra, cs);
             }
+            dfl_add(acc, d);
         }
     }
 }
 
 template <int NR>
-__device__ __forceinline__ void unmix_lanes_d(float2 (&x)[NR], float2 (&r)[NR], int nb, float c, float s, float &d) {
+__device__ __forceinline__ void unmix_lanes_d(float2 (&x)[NR], float2 (&r)[NR], int nb, float4 cs, Dfl &acc) {
     for (int lb = 0; lb < nb; ++lb) {
         const int m = 1 << lb;
+        float d = 0.f;
 #pragma unroll
         for (int i = 0; i < NR; ++i) {
             float2 xo, ro;
@@ -190,30 +193,35 @@ __device__ __forceinline__ void unmix_lanes_d(float2 (&x)[NR], float2 (&r)[NR], 
             ro.x = __shfl_xor_sync(kFull, r[i].x, m);
             ro.y = __shfl_xor_sync(kFull, r[i].y, m);
             d += imconj(r[i], xo);
-            x[i] = rot(x[i], xo, c, -s);
-            r[i] = rot(r[i], ro, c, -s);
+            x[i] = unrot(x[i], xo, cs);
+            r[i] = unrot(r[i], ro, cs);
         }
+        dfl_add(acc, d);
     }
 }
 
 // Sum of Im<r|X_q|x> over every register and lane qubit (only qubits 0 and 1
-// unless `all`), states unchanged.
+// unless `all`), states unchanged; one qubit's terms at a time into the
+// compensated sum.
 template <int NR>
-__device__ __forceinline__ float xterms(const float2 (&x)[NR], const float2 (&r)[NR], bool all) {
-    float d = 0.f;
+__device__ __forceinline__ Dfl xterms(const float2 (&x)[NR], const float2 (&r)[NR], bool all) {
+    Dfl acc{0.f, 0.f};
 #pragma unroll
     for (int rb = 0; (1 << rb) < NR; ++rb) {
         if (!all && rb >= 2) continue;
+        float d = 0.f;
 #pragma unroll
         for (int i = 0; i < NR; ++i) {
             if (i & (1 << rb)) continue;
             const int i2 = i | (1 << rb);
             d += imconj(r[i], x[i2]) + imconj(r[i2], x[i]);
         }
+        dfl_add(acc, d);
     }
-    if (!all) return d;
+    if (!all) return acc;
 #pragma unroll
     for (int lb = 0; lb < 5; ++lb) {
+        float d = 0.f;
 #pragma unroll
         for (int i = 0; i < NR; ++i) {
             float2 xo;
@@ -221,8 +229,9 @@ __device__ __forceinline__ float xterms(const float2 (&x)[NR], const float2 (&r)
             xo.y = __shfl_xor_sync(kFull, x[i].y, 1 << lb);
             d += imconj(r[i], xo);
         }
+        dfl_add(acc, d);
     }
-    return d;
+    return acc;
 }
 
 // <Z_0 Z_1> sign of register i (qubits 0 and 1 are register bits 0 and 1).
@@ -258,7 +267,7 @@ __global__ void __launch_bounds__(128, GRAD ? QAOA_SPLIT_GRAD_BLOCKS : 3) split_
         }
         const int64_t gj = int64_t(C->graph) * L.P + j;
         const float2 *__restrict__ lut = L.lut + gj * p * L.cmax1;
-        const float2 *__restrict__ cs = L.cs + gj * p;
+        const float4 *__restrict__ cs = L.cs + gj * p;
         // cut word of the tile's fixed bits: shell block, outer qubits, lane qubits
         float mult = 1.f;
         uint64_t base = shell_block(C, L.shell, uint32_t(y), mult);
@@ -304,10 +313,10 @@ __global__ void __launch_bounds__(128, GRAD ? QAOA_SPLIT_GRAD_BLOCKS : 3) split_
             const float2 *__restrict__ lt = lut + l * L.cmax1;
 #pragma unroll
             for (int i = 0; i < NR; ++i) x[i] = cmul(x[i], __ldg(lt + cut(i)));
-            const float2 c_s = __ldg(cs + l);
+            const float4 c_s = __ldg(cs + l);
             const int kl = C->k[l];
-            mix_regs<NR>(x, kl < RB ? kl : RB, c_s.x, c_s.y);
-            if (kl > RB) mix_lanes<NR>(x, kl - RB, c_s.x, c_s.y);
+            mix_regs<NR>(x, kl < RB ? kl : RB, c_s);
+            if (kl > RB) mix_lanes<NR>(x, kl - RB, c_s);
         }
         float acc = 0.f;
 #pragma unroll
@@ -329,12 +338,12 @@ __global__ void __launch_bounds__(128, GRAD ? QAOA_SPLIT_GRAD_BLOCKS : 3) split_
             // FP32 sums.
             const float c0 = 0.5f * float(C->m);
             for (int l = p - 1; l >= 1; --l) {
-                const float2 c_s = __ldg(cs + l);
+                const float4 c_s = __ldg(cs + l);
                 const int kl = C->k[l];
-                float d = 0.f;
-                unmix_regs_d<NR>(x, r, kl < RB ? kl : RB, c_s.x, c_s.y, d);
-                if (kl > RB) unmix_lanes_d<NR>(x, r, kl - RB, c_s.x, c_s.y, d);
-                add_gp(wgt2 * d, L.grad, gj * 2 * p + p + l);
+                Dfl d{0.f, 0.f};
+                unmix_regs_d<NR>(x, r, kl < RB ? kl : RB, c_s, d);
+                if (kl > RB) unmix_lanes_d<NR>(x, r, kl - RB, c_s, d);
+                add_gp(d, wgt2, L.grad, gj * 2 * p + p + l);
                 const float2 *__restrict__ lt = lut + l * L.cmax1;
                 // keep the shifted cut values from being hoisted out of the layer
                 // loop into sixteen live registers
@@ -349,13 +358,13 @@ __global__ void __launch_bounds__(128, GRAD ? QAOA_SPLIT_GRAD_BLOCKS : 3) split_
                     x[i] = cmulc(x[i], ph);
                     r[i] = cmulc(r[i], ph);
                 }
-                add_gp(wgt2 * dg, L.grad, gj * 2 * p + l);
+                add_gp(Dfl{dg, 0.f}, wgt2, L.grad, gj * 2 * p + l);
             }
             // first mixer: the core qubits' terms, then lambda alone un-mixed
             // At p = 1 the first layer is the last: lambda = O psi with
             // O = -1/2 Z_0 Z_1, and <psi|O X_q|psi> is real for every q other
             // than 0 and 1 (X_q and O commute), so only those two contribute.
-            add_gp(wgt2 * xterms<NR>(x, r, p > 1), L.grad, gj * 2 * p + p);
+            add_gp(xterms<NR>(x, r, p > 1), wgt2, L.grad, gj * 2 * p + p);
             first_mix_regs<NR, true>(r, 0, RB, f1.a, f1.b);
             first_mix_lanes<NR, true>(r, 5, f1.a, f1.b);
 #pragma unroll
@@ -437,7 +446,7 @@ __global__ void __launch_bounds__(128, MODE == kOuterGen ? 4 : 3) split_outer_ke
                 // layer is the last (only qubits 0 and 1 contribute there)
                 const bool outer_terms = p > 1;
                 const float c0 = 0.5f * float(C->m);  // Im<lambda|psi> = 0: C - c0 in place of C
-                float dg = 0.f, db = 0.f;
+                float dg = 0.f, dq[5] = {0.f, 0.f, 0.f, 0.f, 0.f};  // per window qubit
 #pragma unroll
                 for (int i = 0; i < 32; ++i) {
                     const int c = __popcll(lo[i & 3] ^ hi[i >> 2]);
@@ -446,19 +455,24 @@ __global__ void __launch_bounds__(128, MODE == kOuterGen ? 4 : 3) split_outer_ke
                     if (outer_terms) {
 #pragma unroll
                         for (int rb = 0; rb < 5; ++rb)
-                            if (rb >= r0 && rb < r1) db += imconj(x[i ^ (1 << rb)], ph);
+                            if (rb >= r0 && rb < r1) dq[rb] += imconj(x[i ^ (1 << rb)], ph);
                     }
                 }
+                Dfl db{0.f, 0.f};
+#pragma unroll
+                for (int rb = 0; rb < 5; ++rb) dfl_add(db, dq[rb]);
                 for (int q = L.x0; q < (outer_terms ? L.x1 : L.x0); ++q) {  // outer qubits outside the window
                     const uint64_t cq = C->col[q];
+                    float t = 0.f;
 #pragma unroll
                     for (int i = 0; i < 32; ++i)
-                        db += imconj(x[i], __ldg(lut + __popcll(lo[i & 3] ^ hi[i >> 2] ^ cq)));
+                        t += imconj(x[i], __ldg(lut + __popcll(lo[i & 3] ^ hi[i >> 2] ^ cq)));
+                    dfl_add(db, t);
                 }
                 // lambda = 2^(-n/2) kappa_1^(2 n_in) x once the first mixer is undone
                 const float wgt2 = 2.f * float(C->weight) * mult * __int_as_float((127 - C->n) << 23) * f1.k2n;
-                add_gp(wgt2 * dg, L.grad, gj * 2 * p);
-                if (outer_terms) add_gp(wgt2 * db, L.grad, gj * 2 * p + p);
+                add_gp(Dfl{dg, 0.f}, wgt2, L.grad, gj * 2 * p);
+                if (outer_terms) add_gp(db, wgt2, L.grad, gj * 2 * p + p);
             }
         }
         if (MODE != kOuterFirst) {
@@ -616,7 +630,7 @@ __global__ void __launch_bounds__(kChunkThreads, 2) split_chunk_kernel(const __g
             const float c0 = 0.5f * float(C->m);  // Im<lambda|psi> = 0: C - c0 in place of C
             const int gn = min(5, w);
             const int nreg = 1 << gn;
-            float dg = 0.f, db = 0.f;
+            Dfl dg{0.f, 0.f}, db{0.f, 0.f};  // this thread's slots, compensated
             for (int slot = tid; slot < (n_el >> gn); slot += kChunkThreads) {
                 const int sb = spread_slot(slot, lo_bits, gn);
                 float2 x[32];
@@ -629,30 +643,36 @@ __global__ void __launch_bounds__(kChunkThreads, 2) split_chunk_kernel(const __g
                     if ((sb >> b) & 1) base ^= C->col[w0 + b - lo_bits];
                 uint64_t lo[4], hi[8];
                 slot_words<5>(C, base, w0, lo, hi);  // w > 5 here: five window qubits in registers
+                float dgs = 0.f, dq[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
                 for (int i = 0; i < 32; ++i) {
                     const int c = __popcll(lo[i & 3] ^ hi[i >> 2]);
                     const float2 ph = __ldg(lut + c);
-                    dg = fmaf(float(c) - c0, imconj(x[i], ph), dg);
+                    dgs = fmaf(float(c) - c0, imconj(x[i], ph), dgs);
                     if (outer_terms) {
 #pragma unroll
-                        for (int rb = 0; rb < 5; ++rb) db += imconj(x[i ^ (1 << rb)], ph);
+                        for (int rb = 0; rb < 5; ++rb) dq[rb] += imconj(x[i ^ (1 << rb)], ph);
                     }
                 }
+                dfl_add(dg, dgs);
                 if (outer_terms) {
+#pragma unroll
+                    for (int rb = 0; rb < 5; ++rb) dfl_add(db, dq[rb]);
                     // the other outer qubits: the rest of the window, then beyond it
                     for (int q = w0 + 5; q < L.x1; ++q) {
                         const uint64_t cq = C->col[q];
+                        float t = 0.f;
 #pragma unroll
                         for (int i = 0; i < 32; ++i)
-                            db += imconj(x[i], __ldg(lut + __popcll(lo[i & 3] ^ hi[i >> 2] ^ cq)));
+                            t += imconj(x[i], __ldg(lut + __popcll(lo[i & 3] ^ hi[i >> 2] ^ cq)));
+                        dfl_add(db, t);
                     }
                 }
             }
             // lambda = 2^(-n/2) kappa_1^(2 n_in) x once the first mixer is undone
             const float wgt2 = 2.f * float(C->weight) * mult * __int_as_float((127 - C->n) << 23) * f1.k2n;
-            add_gp(wgt2 * dg, L.grad, gj * 2 * p);
-            if (outer_terms) add_gp(wgt2 * db, L.grad, gj * 2 * p + p);
+            add_gp(dg, wgt2, L.grad, gj * 2 * p);
+            if (outer_terms) add_gp(db, wgt2, L.grad, gj * 2 * p + p);
         } else {
             for (int e2 = tid; e2 < (n_el >> 1); e2 += kChunkThreads) {
                 const int e = e2 << 1;

@@ -126,8 +126,8 @@ cudaError_t run_big(const qaoa_device_plan *d, const qaoa_plan *plan, int64_t P,
                     double *terms, cudaStream_t s) {
     qaoa_device_plan *dm = const_cast<qaoa_device_plan *>(d);
     const int p = plan->p;
-    float2 *cs = nullptr;
-    cudaError_t e = cudaMallocAsync(&cs, size_t(plan->n_graphs) * P * p * sizeof(float2), s);
+    float4 *cs = nullptr;
+    cudaError_t e = cudaMallocAsync(&cs, size_t(plan->n_graphs) * P * p * sizeof(float4), s);
     if (e != cudaSuccess) return e;
     e = launch_big_prep(params, int64_t(plan->n_graphs) * P, p, cs, s);
     dm->all_launches += 1;
@@ -256,7 +256,7 @@ int run(const qaoa_plan *plan, int64_t n_points, const double *params, double *e
             jpt = std::min<int64_t>(jpt, std::max<int64_t>(1, 12288 / row_bytes));
             L.jpt = int32_t(std::min<int64_t>(jpt, n_points));
         }
-        const size_t smem = size_t(kRegBlock / 32) * L.jpt * p * d->cmax1 * sizeof(float2);
+        const size_t smem = reg_smem_bytes(L.jpt, p, d->cmax1, grad != nullptr);
         const int64_t tasks_per = (n_points + L.jpt - 1) / L.jpt;
         L.cmax1 = d->cmax1;
         L.lut = lut;
@@ -507,7 +507,12 @@ extern "C" int qaoa_plan_info(const qaoa_plan *plan, qaoa_plan_info_t *info) {
         info->max_inner = std::max(info->max_inner, c.n_in);
         info->max_edges = std::max(info->max_edges, int32_t(c.ea.size()));
         info->amps_per_point += std::ldexp(1.0, c.n);
-        if (c.n_in > kRegMaxInner) info->n_big++;
+        if (c.n_in > kRegMaxInner) {
+            info->n_big++;
+            const bool general = (plan->flags & QAOA_BIG_GENERAL) != 0;
+            if (general || !split_ok(c.n_in, plan->p, c.k, false)) info->n_big_general_energy++;
+            if (general || !split_ok(c.n_in, plan->p, c.k, true)) info->n_big_general_grad++;
+        }
     }
     info->on_device = plan->dev ? 1 : 0;
     info->t_orbits_s = plan->t_orbits;

@@ -30,16 +30,16 @@
 //
 // Numerics: complex64 amplitudes and FP32 arithmetic; the phase table
 // exp(-i gamma c), tan and the kappa powers are computed in FP64 and rounded
-// once; lane partial sums are reduced across the warp in FP32 and
-// accumulated across warps, cones and orbits in FP64 (atomicAdd).
+// once; each lane's partial of an output is summed over the warp with
+// compensated FP32 additions (the shell blocks' derivative terms cancel), and
+// across warps, cones and orbits in FP64 (atomicAdd).
 #pragma once
 
+#include "dev_math.cuh"
 #include "device.cuh"
 
 namespace qaoa {
 namespace {
-
-constexpr unsigned kFull = 0xffffffffu;
 
 template <typename MT>
 __device__ __forceinline__ int popc_t(MT x);
@@ -134,14 +134,6 @@ struct CutWords {
     }
 };
 
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
-    return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
-}
-// Im(conj(a) b)
-__device__ __forceinline__ float imconj(float2 a, float2 b) { return a.x * b.y - a.y * b.x; }
 // u - i tau v
 __device__ __forceinline__ float2 bfly(float2 u, float2 v, float tau) {
     return make_float2(fmaf(tau, v.y, u.x), fmaf(-tau, v.x, u.y));
@@ -237,19 +229,6 @@ __device__ __forceinline__ bool seg_sum(float &v, int key) {
     return lane == 0 || prev != key;
 }
 
-// Adds v (summed over the warp in FP32) into base[(g*P + j)*stride + comp]
-// with one FP64 atomic per warp when every lane's graph is the same.
-__device__ __forceinline__ void add_gp(float v, double *base, int g, int64_t P, int64_t j, int stride, int comp) {
-    const int g0 = __shfl_sync(kFull, g, 0);
-    if (__all_sync(kFull, g == g0)) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-        if ((threadIdx.x & 31) == 0) atomicAdd(base + (int64_t(g0) * P + j) * stride + comp, double(v));
-    } else if (v != 0.f) {
-        atomicAdd(base + (int64_t(g) * P + j) * stride + comp, double(v));
-    }
-}
-
 // PC > 0: the depth p is the compile-time constant PC (layer loops unrolled);
 // PC = 0: p is read from the launch arguments.
 template <int R, typename MT, bool GRAD, int PC>
@@ -261,6 +240,14 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? kGradMinBlocks : kEnergyMinB
     const int p = PC > 0 ? PC : L.p;
     const int row = p * L.cmax1;  // one point's phase table
     float2 *my_tab = s_tab + (threadIdx.x >> 5) * (L.jpt * row);
+    // Reduction buffer: this lane's share of output c (0: energy, 1 + i:
+    // gradient component i) of point jj sits at [c][jj mod G][(lane + jj) mod
+    // 32] (the skew keeps the reads below free of bank conflicts).
+    constexpr int NOUT_C = PC > 0 ? reg_outputs(PC, GRAD) : 0;
+    constexpr int G_C = PC > 0 ? reg_group(PC, GRAD) : 0;
+    const int NOUT = PC > 0 ? NOUT_C : reg_outputs(p, GRAD);
+    const int G = PC > 0 ? G_C : reg_group(p, GRAD);
+    float2 *red = s_tab + (kRegBlock / 32) * (L.jpt * row) + (threadIdx.x >> 5) * (NOUT * G * 32);
     const int64_t gw = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
     const int64_t nblk = (L.n_points + L.jpt - 1) / L.jpt;
@@ -286,6 +273,8 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? kGradMinBlocks : kEnergyMinB
             n = 2;
         }
         const int g = C->graph;  // the same on every lane (padded work list)
+        const bool uni = __all_sync(kFull, g == __shfl_sync(kFull, g, 0));
+        if (!uni && lane == 0) atomicOr(L.status, 1);
         const int64_t t = active ? slot - W.start[ci] : 0;
         const float wgt = float(C->weight);
         CutWords<R, MT> cw;
@@ -302,6 +291,49 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? kGradMinBlocks : kEnergyMinB
             for (int e = lane; e < jn * row; e += 32) my_tab[e] = __ldg(src + e);
         }
         __syncwarp();
+        // output c of point jj: this lane's share (exact as hi + lo)
+        auto stash = [&](int c, int jj, Dfl v) {
+            if (uni) {
+                red[(c * G + (jj & (G - 1))) * 32 + ((lane + jj) & 31)] = make_float2(v.hi, v.lo);
+            } else {  // a warp over two graphs (never made by the planner): one atomic per lane
+                const int64_t gjj = int64_t(g) * L.n_points + j0 + jj;
+                double *dst = c == 0 ? L.energy + gjj : L.grad + gjj * 2 * p + (c - 1);
+                atomicAdd(dst, f2d(v.hi));
+                atomicAdd(dst, f2d(v.lo));
+            }
+        };
+        // Warp sums of the group of points ending at jj: lane = (part, point);
+        // each lane adds G lanes' shares of its point (compensated), the parts
+        // meet by shuffles, and lanes of part 0 issue the FP64 atomics (hi and
+        // lo each; no FP64 arithmetic).
+        auto flush = [&](int jj) {
+            __syncwarp();
+            if (uni) {
+                const int gn = (jj & (G - 1)) + 1, jf = jj + 1 - gn;
+                const int pt = lane & (G - 1), part = lane / G;
+                for (int c = 0; c < NOUT; ++c) {
+                    const float2 *src = red + (c * G + pt) * 32;
+                    Dfl acc{0.f, 0.f};
+                    for (int k = 0; k < G; ++k) {
+                        const float2 v = src[(part * G + k + jf + pt) & 31];
+                        dfl_add(acc, Dfl{v.x, v.y});
+                    }
+                    for (int o = G; o < 32; o <<= 1) {
+                        Dfl b;
+                        b.hi = __shfl_xor_sync(kFull, acc.hi, o);
+                        b.lo = __shfl_xor_sync(kFull, acc.lo, o);
+                        dfl_add(acc, b);
+                    }
+                    if (part == 0 && pt < gn) {
+                        const int64_t gjj = int64_t(g) * L.n_points + j0 + jf + pt;
+                        double *dst = c == 0 ? L.energy + gjj : L.grad + gjj * 2 * p + (c - 1);
+                        atomicAdd(dst, f2d(acc.hi));
+                        if (acc.lo != 0.f) atomicAdd(dst, f2d(acc.lo));
+                    }
+                }
+            }
+            __syncwarp();
+        };
         for (int jj = 0; jj < jn; ++jj) {
             const int64_t j = j0 + jj;
             const float2 *lut = my_tab + jj * row;
@@ -332,11 +364,10 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? kGradMinBlocks : kEnergyMinB
                 }
             }
             const float tl = zz_partial<R>(x, wk);
-            add_gp(-0.5f * wgt * sig * tl, L.energy, g, L.n_points, j, 1, 0);
+            stash(0, jj, Dfl{-0.5f * wgt * sig * tl, 0.f});
             if (L.terms) {
                 float tv = sig * tl;
-                if (seg_sum(tv, active ? ci : -1) && active)
-                    atomicAdd(L.terms + C->rep * L.n_points + j, double(tv));
+                if (seg_sum(tv, active ? ci : -1) && active) atomicAdd(L.terms + C->rep * L.n_points + j, f2d(tv));
             }
             if constexpr (!GRAD) {
                 cw.flip(fw);  // back to no flips for the next point
@@ -409,14 +440,16 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? kGradMinBlocks : kEnergyMinB
                             float e = 0.f;
 #pragma unroll
                             for (int kk = 0; kk < NA / 4; ++kk) e = fmaf(wk[kk], e4[kk], e);
-                            db += e * __ldg(kpl + Lb);
+                            db = fmaf(e, __ldg(kpl + Lb), db);
                         }
                     }
                     // undo the register-qubit butterflies (psi only above layer 1: below
                     // it psi is the layer-1 phase table itself, read back for d/d gamma_1)
                     if (l > 0) mix_reg<R>(x, kr, -tau);
                     mix_reg<R>(r, kr, -tau);
-                    add_gp(gw2 * sig * db, L.grad, g, L.n_points, j, 2 * p, p + l);
+                    // the blocks' terms cancel across lanes: from here on the sum is
+                    // compensated (exact product, then the grouped reduction)
+                    stash(1 + p + l, jj, dfl_scale(Dfl{db, 0.f}, gw2 * sig));
                     sig *= __ldg(kpl + k);
                     if (mx.y != 0.f) cw.flip(MT(C->pw[l]));
                     // d/d gamma_l = 2 sigma Im <r| C |s>; then undo the phase
@@ -443,9 +476,10 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? kGradMinBlocks : kEnergyMinB
                     float dgs = 0.f;
 #pragma unroll
                     for (int kk = 0; kk < NA / 4; ++kk) dgs = fmaf(wk[kk], dg4[kk], dgs);
-                    add_gp(gw2 * (l > 0 ? sig : sig_end) * dgs, L.grad, g, L.n_points, j, 2 * p, l);
+                    stash(1 + l, jj, dfl_scale(Dfl{dgs, 0.f}, gw2 * (l > 0 ? sig : sig_end)));
                 }
             }
+            if ((jj & (G - 1)) == G - 1 || jj == jn - 1) flush(jj);
         }
     }
 }

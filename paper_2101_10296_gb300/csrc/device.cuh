@@ -156,4 +156,21 @@ constexpr int kEnergyMinBlocks = 3;
 // largest inner part the register kernels take (both must fit)
 constexpr int kRegMaxInner = (kRegBitsEnergy < kRegBitsGrad ? kRegBitsEnergy : kRegBitsGrad) + kLaneBits;
 
+// The register kernels stage every lane's share of each output of a point
+// (the energy, and with the adjoint the 2p derivatives) in shared memory and
+// sum it over the warp for a group of points at once: per warp, outputs x
+// group points x 32 lanes float2 (hi, lo) partials.
+__host__ __device__ constexpr int reg_outputs(int p, bool grad) { return grad ? 1 + 2 * p : 1; }
+__host__ __device__ constexpr int reg_group(int p, bool grad) {
+    // at most 24 x 32 partials (6 KB) per warp, so that the phase tables and
+    // this buffer leave room for four blocks per SM
+    return reg_outputs(p, grad) * 8 <= 24 ? 8 : (reg_outputs(p, grad) * 4 <= 24 ? 4 : 2);
+}
+// Dynamic shared memory of a register-kernel block: per warp the phase
+// tables of jpt points and the reduction buffer.
+inline size_t reg_smem_bytes(int jpt, int p, int cmax1, bool grad) {
+    return size_t(kRegBlock / 32) *
+           (size_t(jpt) * p * cmax1 + size_t(reg_outputs(p, grad)) * reg_group(p, grad) * 32) * sizeof(float2);
+}
+
 }  // namespace qaoa

@@ -154,12 +154,8 @@ int reg_energy_grid(bool wide, size_t smem) {
     return wide ? occupancy_grid((const void *)reg_cone_kernel<kRegBitsEnergy, uint64_t, false, 0>, kRegBlock, smem)
                 : occupancy_grid((const void *)reg_cone_kernel<kRegBitsEnergy, uint32_t, false, 0>, kRegBlock, smem);
 }
-size_t reg_smem(const RegLaunch &a) {
-    return size_t(kRegBlock / 32) * a.jpt * a.p * a.cmax1 * sizeof(float2);
-}
-
 cudaError_t launch_reg_energy(const RegLaunch &a, bool wide, int grid, cudaStream_t s) {
-    const size_t sm = reg_smem(a);
+    const size_t sm = reg_smem_bytes(a.jpt, a.p, a.cmax1, false);
     if (wide)
         reg_cone_kernel<kRegBitsEnergy, uint64_t, false, 0><<<grid, kRegBlock, sm, s>>>(a);
     else

@@ -6,7 +6,6 @@
 namespace qaoa {
 
 int occupancy_grid(const void *fn, int block, size_t smem);
-size_t reg_smem(const RegLaunch &a);
 
 namespace {
 
@@ -47,7 +46,7 @@ int reg_grad_grid(bool wide, size_t smem, int p) {
 }
 
 cudaError_t launch_reg_grad(const RegLaunch &a, bool wide, int grid, cudaStream_t s) {
-    const size_t sm = reg_smem(a);
+    const size_t sm = reg_smem_bytes(a.jpt, a.p, a.cmax1, true);
     if (wide)
         launch_for<uint64_t>(a, grid, sm, s);
     else

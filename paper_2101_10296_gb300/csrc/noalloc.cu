@@ -95,7 +95,7 @@ extern "C" int qaoa_energy_noalloc(const qaoa_plan *plan, int64_t n_points, cons
     const size_t lut_b = align256(GP * p * d->cmax1 * sizeof(float2));
     const size_t mix_b = align256(GP * p * sizeof(float2));
     const size_t kpow_b = align256(GP * p * kKpow * sizeof(float));
-    const size_t cs_b = d->big.empty() ? 0 : align256(GP * p * sizeof(float2));
+    const size_t cs_b = d->big.empty() ? 0 : align256(GP * p * sizeof(float4));
     const size_t tables = lut_b + mix_b + kpow_b + cs_b;
     size_t largest_block = 0;
     for (const BigShape &bs : d->big)
@@ -113,7 +113,7 @@ extern "C" int qaoa_energy_noalloc(const qaoa_plan *plan, int64_t n_points, cons
     float2 *lut = reinterpret_cast<float2 *>(base);
     float2 *mix = reinterpret_cast<float2 *>(base + lut_b);
     float *kpow = reinterpret_cast<float *>(base + lut_b + mix_b);
-    float2 *cs = reinterpret_cast<float2 *>(base + lut_b + mix_b + kpow_b);
+    float4 *cs = reinterpret_cast<float4 *>(base + lut_b + mix_b + kpow_b);
     unsigned char *blocks = base + tables;
     const size_t block_room = kNoAllocBytes - tables;
     cudaStream_t s = (cudaStream_t)stream;
@@ -159,7 +159,7 @@ extern "C" int qaoa_energy_noalloc(const qaoa_plan *plan, int64_t n_points, cons
         L.terms = terms_dev;
         L.status = d->status;
         const bool wide = d->cmax1 - 1 > 32;
-        const size_t smem = size_t(kRegBlock / 32) * L.jpt * p * d->cmax1 * sizeof(float2);
+        const size_t smem = reg_smem_bytes(L.jpt, p, d->cmax1, false);
         const int64_t tasks = d->reg_e.warps * ((n_points + L.jpt - 1) / L.jpt);
         const int64_t grid = std::min<int64_t>(reg_energy_grid(wide, smem), (tasks + 3) / 4);
         e = launch_reg_energy(L, wide, int(std::max<int64_t>(grid, 1)), s);

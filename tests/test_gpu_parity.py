@@ -890,3 +890,106 @@ def test_injected_allocation_failure_is_reported_and_recoverable(q):
         q.inject_fault(q.FAULT_NONE, 0)
     e1, _ = plan.energy_grad(theta)
     assert np.allclose(e1.cpu().numpy(), e0, rtol=E_REL_TOL, atol=0) and plan.device_status() == 0
+
+
+# ------------------------------------- gradients where they are hardest
+
+def _golden(name):
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)
+    with open(path) as f:
+        return json.load(f)
+
+
+def _build(spec):
+    fn, args = spec
+    return getattr(I, fn)(*args)
+
+
+_NEAR = _golden("near_stationary.json")["rows"]
+# schedule name -> plan options; Q_d at p = 1 runs its pruned cones on the register
+# path and its full cones (QAOA_FULL_CONE) on either large-state schedule
+_SCHEDULES = {"register": {}, "core-tile": {"full_cone": True}, "general": {"full_cone": True, "big_general": True}}
+
+
+@pytest.mark.parametrize("case", sorted({r["case"] for r in _NEAR}))
+def test_gradient_at_near_stationary_points(q, case):
+    """Six points near a local maximum of E (|grad E| = 2e-4 |E|, where the
+    derivative sums cancel to ~1e-4 of their terms), FP64 oracle values from
+    tests/golden/near_stationary.json: energy and gradient of every schedule
+    that takes the case, at the unchanged tolerances.  C_30(1,2) at p = 4 and
+    K_{8,8} at p = 3 are default (pruned) plans whose later layers mix more
+    qubits than a core tile holds, so their gradient runs on the general
+    schedule."""
+    rows = [r for r in _NEAR if r["case"] == case]
+    graph = _build(rows[0]["graph"])
+    p = rows[0]["p"]
+    theta = np.array([r["theta"] for r in rows])
+    if case.startswith("Q"):
+        schedules = _SCHEDULES
+    else:
+        schedules = {"default": {}}
+    for name, kw in schedules.items():
+        plan = q.Plan(graph, p, **kw)
+        info = plan.info()
+        if name == "register":
+            assert info["n_big"] == 0
+        elif name == "core-tile":
+            assert info["n_big"] == 1 and info["n_big_general_grad"] == 0
+        else:
+            assert info["n_big"] >= 1 and info["n_big_general_grad"] == info["n_big"]
+        e, g = plan.energy_grad(_params(theta))
+        e, g = e.cpu().numpy()[0], g.cpu().numpy()[0]
+        for j, r in enumerate(rows):
+            assert abs(e[j] - r["energy"]) <= E_REL_TOL * abs(r["energy"]), (name, j)
+            try:
+                _check_grad(g[j], r["grad"])
+            except AssertionError:
+                err = np.linalg.norm(g[j] - r["grad"]) / np.linalg.norm(r["grad"])
+                raise AssertionError(f"{case} {name} point {j}: relative gradient error {err:.2e}")
+        assert plan.device_status() == 0
+
+
+def test_gradient_configuration_full_size_against_fp64(q):
+    """The gradient configuration at full size against FP64 oracle values
+    (tests/golden/full_size_gradient.json): four random 3-regular graphs with
+    n = 24 at p = 3, 128 points in one call (cones of up to 24 qubits, mostly
+    on the large-state path), energy and gradient of each graph at two points
+    and the terms of its two largest cones; the 6x6 torus at p = 3 (one orbit,
+    a 28-qubit cone with 18 inner qubits) at one point."""
+    gold = _golden("full_size_gradient.json")
+    P = gold["rr3_n24_p3"]["points_per_graph"]
+    seeds = (1, 2, 3, 4)
+    graphs = [I.random_regular(24, 3, s) for s in seeds]
+    theta = np.stack([I.draw_params(3, P, s) for s in seeds])
+    plan = q.Plan(graphs, 3)
+    assert plan.info()["n_big"] > 0
+    e, g, t = plan.energy_grad(_params(theta), terms=True)
+    e, g, t = e.cpu().numpy(), g.cpu().numpy(), t.cpu().numpy()
+    reps = plan.reps()
+    for row in gold["rr3_n24_p3"]["rows"]:
+        k, j = seeds.index(row["seed"]), row["point"]
+        assert abs(e[k, j] - row["energy"]) <= E_REL_TOL * abs(row["energy"])
+        _check_grad(g[k, j], row["grad"])
+        for cone in row["largest_cones"]:
+            r = np.nonzero((reps["graph"] == k) & (reps["edge"] == cone["edge"]))[0]
+            assert r.size == 1 and reps["n_qubits"][r[0]] == cone["qubits"]
+            # <Z_u Z_v> = 1 - 2 (cut probability)
+            assert abs(t[r[0], j] - (1 - 2 * cone["term_cut"])) <= 2 * TERM_TOL
+    assert plan.device_status() == 0
+
+    n, edges = I.torus(6, 6)
+    tor = gold["torus6_p3"]
+    theta = I.draw_params(3, tor["points"], tor["param_seed"])
+    plan = q.Plan((n, edges), 3)
+    info = plan.info()
+    assert info["n_reps"] == 1 and info["max_qubits"] == 28 and info["max_inner"] == 18
+    e, g = plan.energy_grad(_params(theta))
+    e_only = plan.energy(_params(theta))
+    for row in tor["rows"]:
+        j = row["point"]
+        assert abs(e[0, j].item() - row["energy"]) <= E_REL_TOL * abs(row["energy"])
+        assert abs(e_only[0, j].item() - row["energy"]) <= E_REL_TOL * abs(row["energy"])
+        _check_grad(g[0, j].cpu().numpy(), row["grad"])
+    assert plan.device_status() == 0

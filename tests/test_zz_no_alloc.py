@@ -89,8 +89,9 @@ def test_noalloc_rejects_bad_outputs_before_the_call(qlib):
         plan.energy_noalloc(params, out=torch.empty(1, 8, dtype=torch.float64, device="cuda")[:, ::2])
     with pytest.raises(ValueError):
         plan.energy_noalloc(params, out=torch.empty(1, 4, dtype=torch.float64))
+    assert plan.info()["n_reps"] == 1
     with pytest.raises(ValueError):
-        plan.energy_noalloc(params, terms=torch.empty(1, 4, dtype=torch.float64, device="cuda"))
+        plan.energy_noalloc(params, terms=torch.empty(2, 4, dtype=torch.float64, device="cuda"))
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch(qlib):
