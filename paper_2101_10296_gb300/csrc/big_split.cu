@@ -122,6 +122,16 @@ __device__ __forceinline__ FirstMix first_mix(const BigLaunch &L, int64_t gj, in
     return f;
 }
 
+// The same factored form for layer l mixing k qubits (kappa_l^(2k) in k2n).
+__device__ __forceinline__ FirstMix layer_mix(const BigLaunch &L, int64_t gj, int l, int k) {
+    const float2 m = __ldg(L.mix + gj * L.p + l);
+    FirstMix f;
+    f.b = m.y != 0.f;
+    f.a = f.b ? -m.x : m.x;
+    f.k2n = __ldg(L.kpow + (gj * L.p + l) * kKpow + k);
+    return f;
+}
+
 // exp(-i beta X) on register qubits [0, nbits) (nbits <= log2 NR).
 template <int NR>
 __device__ __forceinline__ void mix_regs(float2 (&x)[NR], int nbits, float4 cs) {
@@ -305,7 +315,7 @@ __global__ void __launch_bounds__(128, GRAD ? QAOA_SPLIT_GRAD_BLOCKS : 3) split_
         }
         const FirstMix f1 = first_mix(L, gj, nin);
         // |psi|^2 = 2^-n kappa_1^(2 n_in) |x|^2 (the first mixer's factored form)
-        const float sig = __int_as_float((127 - C->n) << 23) * f1.k2n;
+        float sig = __int_as_float((127 - C->n) << 23) * f1.k2n;
         // first mixer on the core qubits
         first_mix_regs<NR, false>(x, 0, RB, f1.a, f1.b);
         first_mix_lanes<NR, false>(x, 5, f1.a, f1.b);
@@ -313,10 +323,17 @@ __global__ void __launch_bounds__(128, GRAD ? QAOA_SPLIT_GRAD_BLOCKS : 3) split_
             const float2 *__restrict__ lt = lut + l * L.cmax1;
 #pragma unroll
             for (int i = 0; i < NR; ++i) x[i] = cmul(x[i], __ldg(lt + cut(i)));
-            const float4 c_s = __ldg(cs + l);
             const int kl = C->k[l];
-            mix_regs<NR>(x, kl < RB ? kl : RB, c_s);
-            if (kl > RB) mix_lanes<NR>(x, kl - RB, c_s);
+            if (GRAD) {  // the adjoint keeps exact rotations (its derivative terms need them)
+                const float4 c_s = __ldg(cs + l);
+                mix_regs<NR>(x, kl < RB ? kl : RB, c_s);
+                if (kl > RB) mix_lanes<NR>(x, kl - RB, c_s);
+            } else {  // the energy: the factored form, two FMAs per output, kappa^(2 k_l) into sigma
+                const FirstMix fl = layer_mix(L, gj, l, kl);
+                first_mix_regs<NR, false>(x, 0, kl < RB ? kl : RB, fl.a, fl.b);
+                if (kl > RB) first_mix_lanes<NR, false>(x, kl - RB, fl.a, fl.b);
+                sig *= fl.k2n;
+            }
         }
         float acc = 0.f;
 #pragma unroll

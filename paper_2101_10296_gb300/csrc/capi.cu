@@ -246,7 +246,8 @@ int run(const qaoa_plan *plan, int64_t n_points, const double *params, double *e
         // plans: more tasks of fewer points); a tuned value is held to the
         // 48 KB of shared memory of 4 warps
         {
-            const int64_t row_bytes = int64_t(p) * d->cmax1 * int64_t(sizeof(float2));
+            // one point's phase tables, mixer data and kappa powers
+            const int64_t row_bytes = int64_t(p) * ((d->cmax1 + 1) * int64_t(sizeof(float2)) + kRegKpow * int64_t(sizeof(float)));
             const int64_t warps = grad ? d->reg_g.warps : d->reg_e.warps;
             int64_t jpt = d->points_per_task;
             if (jpt <= 0) {
@@ -479,6 +480,7 @@ extern "C" int qaoa_plan_upload(qaoa_plan *plan) {
             rc = cuda_fail(e, "cudaMemset");
     }
     if (rc == QAOA_OK && !d->big.empty() && (e = split_prepare()) != cudaSuccess) rc = cuda_fail(e, "kernel attributes");
+    if (rc == QAOA_OK && (e = reg_prepare()) != cudaSuccess) rc = cuda_fail(e, "kernel attributes");
     // commit qaoa_energy_noalloc's static scratch on this device now, during set-up
     // (not fatal here: that entry point repeats the lookup and reports a failure)
     if (rc == QAOA_OK) {

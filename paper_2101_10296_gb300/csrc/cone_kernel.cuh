@@ -132,7 +132,24 @@ struct CutWords {
 #pragma unroll
         for (int i = 0; i < (1 << R); ++i) f(i, popc_t<MT>(lo[i & 3] ^ hi[i >> 2]));
     }
+    // C(z_i) of every register index, one byte each (a cone has < 256 cut bits)
+    __device__ __forceinline__ void pack(uint32_t (&pk)[1 << (R - 2)]) const {
+#pragma unroll
+        for (int k = 0; k < (1 << (R - 2)); ++k) {
+            uint32_t w = 0;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) w |= uint32_t(popc_t<MT>(lo[a] ^ hi[k])) << (8 * a);
+            pk[k] = w;
+        }
+    }
 };
+
+// f(i, c_i) from counts packed by CutWords::pack
+template <int R, class F>
+__device__ __forceinline__ void visit_packed(const uint32_t (&pk)[1 << (R - 2)], F &&f) {
+#pragma unroll
+    for (int i = 0; i < (1 << R); ++i) f(i, int((pk[i >> 2] >> (8 * (i & 3))) & 0xffu));
+}
 
 // u - i tau v
 __device__ __forceinline__ float2 bfly(float2 u, float2 v, float tau) {
@@ -239,15 +256,22 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? kGradMinBlocks : kEnergyMinB
     const RegWork &W = L.work;
     const int p = PC > 0 ? PC : L.p;
     const int row = p * L.cmax1;  // one point's phase table
-    float2 *my_tab = s_tab + (threadIdx.x >> 5) * (L.jpt * row);
-    // Reduction buffer: this lane's share of output c (0: energy, 1 + i:
-    // gradient component i) of point jj sits at [c][jj mod G][(lane + jj) mod
-    // 32] (the skew keeps the reads below free of bank conflicts).
+    // Per warp: the phase tables, mixer data (tau, flip) and kappa powers of
+    // the task's points, and the reduction buffer: this lane's share of output
+    // c (0: energy, 1 + i: gradient component i) of point jj sits at
+    // [c][jj mod G][(lane + jj) mod 32] (the skew keeps the reads below free
+    // of bank conflicts).
     constexpr int NOUT_C = PC > 0 ? reg_outputs(PC, GRAD) : 0;
     constexpr int G_C = PC > 0 ? reg_group(PC, GRAD) : 0;
     const int NOUT = PC > 0 ? NOUT_C : reg_outputs(p, GRAD);
     const int G = PC > 0 ? G_C : reg_group(p, GRAD);
-    float2 *red = s_tab + (kRegBlock / 32) * (L.jpt * row) + (threadIdx.x >> 5) * (NOUT * G * 32);
+    const int warp = threadIdx.x >> 5;
+    float2 *my_tab = s_tab + warp * (L.jpt * row);
+    float2 *my_mix = s_tab + (kRegBlock / 32) * (L.jpt * row) + warp * (L.jpt * p);
+    float *my_kp = reinterpret_cast<float *>(s_tab + (kRegBlock / 32) * (L.jpt * (row + p))) +
+                   warp * (L.jpt * p * kRegKpow);
+    float *red = reinterpret_cast<float *>(s_tab + (kRegBlock / 32) * (L.jpt * (row + p))) +
+                 (kRegBlock / 32) * (L.jpt * p * kRegKpow) + warp * (NOUT * G * 32);
     const int64_t gw = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
     const int64_t nblk = (L.n_points + L.jpt - 1) / L.jpt;
@@ -284,22 +308,35 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? kGradMinBlocks : kEnergyMinB
 #pragma unroll
             for (int k = 0; k < NA / 4; ++k) wk[k] = 0.f;
         }
+        // At p = 1 every phase lookup (the layer-1 table forward, and again for
+        // d/d gamma_1) uses the cut values without flips: count them once per task.
+        uint32_t pk[NA / 4];
+        if constexpr (PC == 1) cw.pack(pk);
+        auto visit = [&](auto &&f) {
+            if constexpr (PC == 1)
+                visit_packed<R>(pk, f);
+            else
+                cw.visit(f);
+        };
         // stage the phase tables of points j0 .. j0+jn-1 of graph g
         __syncwarp();
         {
             const float2 *__restrict__ src = L.lut + (int64_t(g) * L.n_points + j0) * row;
             for (int e = lane; e < jn * row; e += 32) my_tab[e] = __ldg(src + e);
+            const float2 *__restrict__ msrc = L.mix + (int64_t(g) * L.n_points + j0) * p;
+            for (int e = lane; e < jn * p; e += 32) my_mix[e] = __ldg(msrc + e);
+            const float *__restrict__ ksrc = L.kpow + (int64_t(g) * L.n_points + j0) * p * kKpow;
+            for (int e = lane; e < jn * p * kRegKpow; e += 32)
+                my_kp[e] = __ldg(ksrc + (e / kRegKpow) * kKpow + (e % kRegKpow));
         }
         __syncwarp();
-        // output c of point jj: this lane's share (exact as hi + lo)
-        auto stash = [&](int c, int jj, Dfl v) {
+        // output c of point jj: this lane's share
+        auto stash = [&](int c, int jj, float v) {
             if (uni) {
-                red[(c * G + (jj & (G - 1))) * 32 + ((lane + jj) & 31)] = make_float2(v.hi, v.lo);
+                red[(c * G + (jj & (G - 1))) * 32 + ((lane + jj) & 31)] = v;
             } else {  // a warp over two graphs (never made by the planner): one atomic per lane
                 const int64_t gjj = int64_t(g) * L.n_points + j0 + jj;
-                double *dst = c == 0 ? L.energy + gjj : L.grad + gjj * 2 * p + (c - 1);
-                atomicAdd(dst, f2d(v.hi));
-                atomicAdd(dst, f2d(v.lo));
+                atomicAdd(c == 0 ? L.energy + gjj : L.grad + gjj * 2 * p + (c - 1), f2d(v));
             }
         };
         // Warp sums of the group of points ending at jj: lane = (part, point);
@@ -312,12 +349,9 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? kGradMinBlocks : kEnergyMinB
                 const int gn = (jj & (G - 1)) + 1, jf = jj + 1 - gn;
                 const int pt = lane & (G - 1), part = lane / G;
                 for (int c = 0; c < NOUT; ++c) {
-                    const float2 *src = red + (c * G + pt) * 32;
+                    const float *src = red + (c * G + pt) * 32;
                     Dfl acc{0.f, 0.f};
-                    for (int k = 0; k < G; ++k) {
-                        const float2 v = src[(part * G + k + jf + pt) & 31];
-                        dfl_add(acc, Dfl{v.x, v.y});
-                    }
+                    for (int k = 0; k < G; ++k) dfl_add(acc, src[(part * G + k + jf + pt) & 31]);
                     for (int o = G; o < 32; o <<= 1) {
                         Dfl b;
                         b.hi = __shfl_xor_sync(kFull, acc.hi, o);
@@ -337,40 +371,39 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? kGradMinBlocks : kEnergyMinB
         for (int jj = 0; jj < jn; ++jj) {
             const int64_t j = j0 + jj;
             const float2 *lut = my_tab + jj * row;
-            const int64_t gj = int64_t(g) * L.n_points + j;
-            const float2 *__restrict__ mix = L.mix + gj * p;
-            const float *__restrict__ kp = L.kpow + gj * p * kKpow;
+            const float2 *mix = my_mix + jj * p;
+            const float *kp = my_kp + jj * p * kRegKpow;
 
             float2 x[NA];
             // layer 1 phase on |+>: amplitude exp(-i gamma_1 C(z)) (2^-n/2 kept in sigma)
-            cw.visit([&](int i, int c) { x[i] = lut[c]; });
+            visit([&](int i, int c) { x[i] = lut[c]; });
             float sig = __int_as_float((127 - n) << 23);  // 2^-n
             MT fw = 0;                                      // accumulated flip word
 #pragma unroll(PC > 0 ? PC : 1)
             for (int l = 0; l < p; ++l) {
                 if (l > 0) {
                     const float2 *lt = lut + l * L.cmax1;
-                    cw.visit([&](int i, int c) { x[i] = cmul(x[i], lt[c]); });
+                    visit([&](int i, int c) { x[i] = cmul(x[i], lt[c]); });
                 }
-                const float2 mx = __ldg(mix + l);
+                const float2 mx = mix[l];
                 const int k = C->k[l];
                 mix_reg<R>(x, k, mx.x);
                 mix_lane<R>(x, k, mx.x);
-                sig *= __ldg(kp + l * kKpow + k);
-                if (mx.y != 0.f) {
+                sig *= kp[l * kRegKpow + k];
+                if (PC != 1 && mx.y != 0.f) {  // (no lookup follows a flip at p = 1)
                     const MT f = MT(C->pw[l]);
                     cw.flip(f);
                     fw ^= f;
                 }
             }
             const float tl = zz_partial<R>(x, wk);
-            stash(0, jj, Dfl{-0.5f * wgt * sig * tl, 0.f});
+            stash(0, jj, -0.5f * wgt * sig * tl);
             if (L.terms) {
                 float tv = sig * tl;
                 if (seg_sum(tv, active ? ci : -1) && active) atomicAdd(L.terms + C->rep * L.n_points + j, f2d(tv));
             }
             if constexpr (!GRAD) {
-                cw.flip(fw);  // back to no flips for the next point
+                if (PC != 1) cw.flip(fw);  // back to no flips for the next point
             } else {
                 // co-state lambda = -1/2 Z_0 Z_1 psi, in the same stored form
                 float2 r[NA];
@@ -388,11 +421,11 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? kGradMinBlocks : kEnergyMinB
                 const float c0 = 0.5f * float(C->m);
 #pragma unroll(PC > 0 ? PC : 1)
                 for (int l = p - 1; l >= 0; --l) {
-                    const float2 mx = __ldg(mix + l);
+                    const float2 mx = mix[l];
                     const float tau = mx.x;
                     const int k = C->k[l];
                     const int kr = k < R ? k : R;
-                    const float *__restrict__ kpl = kp + l * kKpow;
+                    const float *kpl = kp + l * kRegKpow;
                     // d/d beta_l = 2 sigma Im <r| sum_q X_q |s>, register qubits
                     // on the untouched state first
                     float d[NA / 4];
@@ -440,25 +473,25 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? kGradMinBlocks : kEnergyMinB
                             float e = 0.f;
 #pragma unroll
                             for (int kk = 0; kk < NA / 4; ++kk) e = fmaf(wk[kk], e4[kk], e);
-                            db = fmaf(e, __ldg(kpl + Lb), db);
+                            db = fmaf(e, kpl[Lb], db);
                         }
                     }
                     // undo the register-qubit butterflies (psi only above layer 1: below
                     // it psi is the layer-1 phase table itself, read back for d/d gamma_1)
                     if (l > 0) mix_reg<R>(x, kr, -tau);
                     mix_reg<R>(r, kr, -tau);
-                    // the blocks' terms cancel across lanes: from here on the sum is
-                    // compensated (exact product, then the grouped reduction)
-                    stash(1 + p + l, jj, dfl_scale(Dfl{db, 0.f}, gw2 * sig));
-                    sig *= __ldg(kpl + k);
-                    if (mx.y != 0.f) cw.flip(MT(C->pw[l]));
+                    // the blocks' terms cancel across lanes: the grouped reduction
+                    // adds the lanes' shares with compensation
+                    stash(1 + p + l, jj, gw2 * sig * db);
+                    sig *= kpl[k];
+                    if (PC != 1 && mx.y != 0.f) cw.flip(MT(C->pw[l]));
                     // d/d gamma_l = 2 sigma Im <r| C |s>; then undo the phase
                     float dg4[NA / 4];
 #pragma unroll
                     for (int kk = 0; kk < NA / 4; ++kk) dg4[kk] = 0.f;
                     const float2 *lt = lut + l * L.cmax1;
                     if (l > 0) {
-                        cw.visit([&](int i, int cv) {
+                        visit([&](int i, int cv) {
                             dg4[i >> 2] = fmaf(float(cv) - c0, imconj(r[i], x[i]), dg4[i >> 2]);
                             const float2 ph = lt[cv];
                             x[i] = cmulc(x[i], ph);
@@ -469,14 +502,14 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? kGradMinBlocks : kEnergyMinB
                         // Lambda = prod_l (1 + tau_l^2)^k_l from the unnormalised inverse
                         // butterflies, and sigma * Lambda = sigma at the end of the forward
                         // sweep: use the table and that sigma.
-                        cw.visit([&](int i, int cv) {
+                        visit([&](int i, int cv) {
                             dg4[i >> 2] = fmaf(float(cv) - c0, imconj(r[i], lt[cv]), dg4[i >> 2]);
                         });
                     }
                     float dgs = 0.f;
 #pragma unroll
                     for (int kk = 0; kk < NA / 4; ++kk) dgs = fmaf(wk[kk], dg4[kk], dgs);
-                    stash(1 + l, jj, dfl_scale(Dfl{dgs, 0.f}, gw2 * (l > 0 ? sig : sig_end)));
+                    stash(1 + l, jj, gw2 * (l > 0 ? sig : sig_end) * dgs);
                 }
             }
             if ((jj & (G - 1)) == G - 1 || jj == jn - 1) flush(jj);

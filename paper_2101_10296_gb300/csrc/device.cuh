@@ -135,7 +135,11 @@ cudaError_t launch_cut_table(const DevCone *cone, uint8_t *out, int32_t n, int32
 int reg_energy_grid(bool wide, size_t smem);
 int sm_count();  // multiprocessors of the current device (cached)
 int reg_grad_grid(bool wide, size_t smem, int p);
+// Raises the register kernels' dynamic shared memory limit to kRegMaxSmem
+// (once per device; called at upload, outside any stream capture).
+cudaError_t reg_prepare();
 constexpr int kRegBlock = 128;
+constexpr int kRegMaxSmem = 96 * 1024;
 
 #ifndef QAOA_REG_BITS_ENERGY
 #define QAOA_REG_BITS_ENERGY 5
@@ -159,18 +163,24 @@ constexpr int kRegMaxInner = (kRegBitsEnergy < kRegBitsGrad ? kRegBitsEnergy : k
 // The register kernels stage every lane's share of each output of a point
 // (the energy, and with the adjoint the 2p derivatives) in shared memory and
 // sum it over the warp for a group of points at once: per warp, outputs x
-// group points x 32 lanes float2 (hi, lo) partials.
+// group points x 32 lanes FP32 partials.
 __host__ __device__ constexpr int reg_outputs(int p, bool grad) { return grad ? 1 + 2 * p : 1; }
 __host__ __device__ constexpr int reg_group(int p, bool grad) {
-    // at most 24 x 32 partials (6 KB) per warp, so that the phase tables and
+    // at most 24 x 32 partials (3 KB) per warp, so that the point tables and
     // this buffer leave room for four blocks per SM
-    return reg_outputs(p, grad) * 8 <= 24 ? 8 : (reg_outputs(p, grad) * 4 <= 24 ? 4 : 2);
+    return reg_outputs(p, grad) * 8 <= 24 ? 8
+           : reg_outputs(p, grad) * 4 <= 24 ? 4
+           : reg_outputs(p, grad) * 2 <= 24 ? 2 : 1;
 }
-// Dynamic shared memory of a register-kernel block: per warp the phase
-// tables of jpt points and the reduction buffer.
+// kappa powers a register kernel reads: kappa^(2k) for k <= its largest inner part
+constexpr int kRegKpow = 10;
+// Dynamic shared memory of a register-kernel block: per warp and point the
+// phase tables (p x cmax1 float2), the mixer data (p float2) and the kappa
+// powers (p x kRegKpow float) of jpt points, and the reduction buffer.
 inline size_t reg_smem_bytes(int jpt, int p, int cmax1, bool grad) {
     return size_t(kRegBlock / 32) *
-           (size_t(jpt) * p * cmax1 + size_t(reg_outputs(p, grad)) * reg_group(p, grad) * 32) * sizeof(float2);
+           (size_t(jpt) * p * (cmax1 + 1) * sizeof(float2) +
+            (size_t(jpt) * p * kRegKpow + size_t(reg_outputs(p, grad)) * reg_group(p, grad) * 32) * sizeof(float));
 }
 
 }  // namespace qaoa

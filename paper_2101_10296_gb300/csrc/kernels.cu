@@ -31,6 +31,7 @@
 // once; lane partial sums are reduced across the warp in FP32 and
 // accumulated across warps, cones and orbits in FP64 (atomicAdd).
 #include <map>
+#include <set>
 #include <mutex>
 #include <tuple>
 
@@ -154,6 +155,25 @@ int reg_energy_grid(bool wide, size_t smem) {
     return wide ? occupancy_grid((const void *)reg_cone_kernel<kRegBitsEnergy, uint64_t, false, 0>, kRegBlock, smem)
                 : occupancy_grid((const void *)reg_cone_kernel<kRegBitsEnergy, uint32_t, false, 0>, kRegBlock, smem);
 }
+cudaError_t reg_grad_prepare();  // kernels_grad.cu
+
+cudaError_t reg_prepare() {
+    static std::mutex mu;
+    static std::set<int> done;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.count(dev)) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute((const void *)reg_cone_kernel<kRegBitsEnergy, uint32_t, false, 0>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kRegMaxSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute((const void *)reg_cone_kernel<kRegBitsEnergy, uint64_t, false, 0>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kRegMaxSmem);
+    if (e == cudaSuccess) e = reg_grad_prepare();
+    if (e == cudaSuccess) done.insert(dev);
+    return e;
+}
+
 cudaError_t launch_reg_energy(const RegLaunch &a, bool wide, int grid, cudaStream_t s) {
     const size_t sm = reg_smem_bytes(a.jpt, a.p, a.cmax1, false);
     if (wide)

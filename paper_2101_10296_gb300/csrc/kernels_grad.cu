@@ -41,6 +41,16 @@ void launch_for(const RegLaunch &a, int grid, size_t sm, cudaStream_t s) {
 
 }  // namespace
 
+cudaError_t reg_grad_prepare() {
+    cudaError_t e = cudaSuccess;
+    for (int p = 0; p <= 3 && e == cudaSuccess; ++p) {
+        for (int w = 0; w < 2 && e == cudaSuccess; ++w)
+            e = cudaFuncSetAttribute(w ? grad_fn_for<uint64_t>(p) : grad_fn_for<uint32_t>(p),
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kRegMaxSmem);
+    }
+    return e;
+}
+
 int reg_grad_grid(bool wide, size_t smem, int p) {
     return occupancy_grid(wide ? grad_fn_for<uint64_t>(p) : grad_fn_for<uint32_t>(p), kRegBlock, smem);
 }

@@ -148,7 +148,7 @@ extern "C" int qaoa_energy_noalloc(const qaoa_plan *plan, int64_t n_points, cons
         L.work.warps = d->reg_e.warps;
         L.n_points = n_points;
         L.p = p;
-        const int64_t row_bytes = int64_t(p) * d->cmax1 * int64_t(sizeof(float2));
+        const int64_t row_bytes = int64_t(p) * ((d->cmax1 + 1) * int64_t(sizeof(float2)) + kRegKpow * int64_t(sizeof(float)));
         L.jpt = int32_t(std::min<int64_t>(std::min<int64_t>(8, std::max<int64_t>(1, 6144 / row_bytes)), n_points));
         L.cmax1 = d->cmax1;
         L.lut = lut;
