@@ -343,7 +343,10 @@ int qaoa_energy_noalloc(const qaoa_plan *plan, int64_t n_points,
 /*
  * Reads and clears the plan's device status word (synchronises the device).
  * *status = 0 if no kernel guard tripped since the last read; otherwise a
- * nonzero code (1: descriptor out of range, 2: non-finite result).
+ * nonzero code, the OR of 1: descriptor out of range, 2: non-finite result,
+ * 4: a tensor-memory-accelerator load into shared memory did not complete
+ * within its time limit (the block stopped; results of that call are
+ * incomplete).
  */
 int qaoa_device_status(const qaoa_plan *plan, int32_t *status);
 
@@ -359,12 +362,23 @@ int qaoa_device_status(const qaoa_plan *plan, int32_t *status);
  *   big_scratch_bytes scratch per call for large-state cones, which sets how
  *                    many state blocks a wave holds (default 1 GiB; a wave
  *                    that fits the 129 MB L2 keeps its passes on chip)
- * Errors: QAOA_E_INVALID for negative values.
+ *   reg_bits_grad    register qubits per thread of the adjoint register
+ *                    kernel, 4 (default) or 5: a tile of 2^(bits + 5)
+ *                    amplitudes per warp, 5 holding twice the amplitudes per
+ *                    thread at half the resident blocks
+ *   chunk_window     largest window of outer qubits a shared-memory chunk
+ *                    pass of the large-state path mixes, 6..10 (default 10):
+ *                    the 2^13-amplitude chunk is a window of w outer qubits
+ *                    over contiguous runs of 2^(13 - w) amplitudes
+ * Errors: QAOA_E_INVALID for negative values, reg_bits_grad other than
+ * 0, 4, 5, or chunk_window outside 6..10 (0 = default).
  */
 typedef struct qaoa_tuning_t {
     int32_t points_per_task;
     int32_t blocks_per_sm;
     int64_t big_scratch_bytes;
+    int32_t reg_bits_grad;
+    int32_t chunk_window;
 } qaoa_tuning_t;
 
 int qaoa_plan_set_tuning(qaoa_plan *plan, const qaoa_tuning_t *tuning);

@@ -1,13 +1,25 @@
 """Launch autotuner for a plan: times candidate tunings once and keeps the best.
 
-Candidates (see qaoa_tuning_t in include/qaoa.h): the number of parameter
-points a warp task of the register kernels evaluates (1, 2, 4, 8, 16 when the
-phase tables fit), the persistent grid's blocks per SM, and, when the plan
-has large-state cones, the scratch per call, i.e. how many state blocks a
-wave holds (waves that fit the L2 keep their passes on chip).  Each
-candidate is timed with the library's kernel events on real parameters; the
-winner is applied to the plan and cached in a JSON file keyed by device name
-and plan shape, so later plans of the same shape skip the search.
+Candidates (see qaoa_tuning_t in include/qaoa.h), searched one group at a
+time (coordinate descent, each group timed with the best values found for
+the groups before it):
+
+1. the number of parameter points a warp task of the register kernels
+   evaluates (1 .. 32 while the phase tables fit) and the persistent grid's
+   blocks per SM;
+2. with gradients and register-resident cones: the adjoint register kernel's
+   tile, 2^(bits + 5) amplitudes per warp with 4 or 5 register qubits per
+   thread;
+3. with large-state cones: the scratch per call, i.e. how many state blocks a
+   wave holds (waves that fit the L2 keep their passes on chip), and the
+   widest window of outer qubits a shared-memory chunk pass mixes (the chunk
+   tile: a window of w outer qubits over contiguous runs of 2^(13 - w)
+   amplitudes).
+
+Each candidate is timed with the library's kernel events on real parameters;
+the winner is applied to the plan and cached in a JSON file keyed by device
+name and plan shape, so later plans of the same shape skip the search.
+Results do not depend on the tuning (every candidate computes the same sums).
 """
 from __future__ import annotations
 
@@ -15,6 +27,7 @@ import json
 import os
 
 _DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_tuning_cache.json")
+_FIELDS = ("points_per_task", "blocks_per_sm", "big_scratch_bytes", "reg_bits_grad", "chunk_window")
 
 
 def _key(plan, n_points, grad):
@@ -39,19 +52,32 @@ def _time(plan, params, grad, reps):
     return ms / max(reps, 1)
 
 
-def candidates(plan, n_points):
+def candidate_groups(plan, n_points, grad):
+    """The groups of tuning values the search walks through, in order: a list
+    of lists of partial tunings (dicts over qaoa_tuning_t's fields)."""
     info = plan.info()
     row_bytes = info["p"] * (info["max_edges"] + 1) * 8
     jpts = [j for j in (1, 2, 4, 8, 16, 32) if j <= max(1, n_points) and j * row_bytes * 4 <= 48 * 1024]
-    bpsm = [0, 1, 2]
-    bigs = [0] if info["n_big"] == 0 else [0, 32 << 20, 96 << 20, 256 << 20]
-    return [(j, b, g) for j in jpts for b in bpsm for g in bigs]
+    groups = [[{"points_per_task": j, "blocks_per_sm": b} for j in jpts for b in (0, 1, 2)]]
+    has_reg = info["n_reps"] > info["n_big"]
+    if grad and has_reg:
+        groups.append([{"reg_bits_grad": r} for r in (4, 5)])
+    if info["n_big"] > 0:
+        groups.append([{"big_scratch_bytes": g, "chunk_window": w}
+                       for g in (0, 96 << 20, 256 << 20) for w in (8, 10)])
+    return groups
+
+
+def candidates(plan, n_points, grad=True):
+    """Every partial tuning the search may time (flattened groups)."""
+    return [c for grp in candidate_groups(plan, n_points, grad) for c in grp]
 
 
 def autotune(plan, params, grad=True, reps=2, cache_path=_DEFAULT_CACHE, use_cache=True):
-    """Times every candidate tuning on ``params`` and applies the fastest.
+    """Times the candidate tunings on ``params`` and applies the fastest.
 
-    Returns ``(best_tuning_dict, {candidate: ms})``.
+    Returns ``(best_tuning_dict, {candidate: ms})`` with candidates as tuples
+    of (field, value) pairs.
     """
     n_points = int(params.shape[-2])
     key = _key(plan, n_points, grad)
@@ -62,15 +88,20 @@ def autotune(plan, params, grad=True, reps=2, cache_path=_DEFAULT_CACHE, use_cac
         except Exception:
             cache = {}
     if use_cache and key in cache:
-        best = cache[key]
+        best = {k: cache[key].get(k, 0) for k in _FIELDS}
         plan.set_tuning(**best)
         return best, {}
+    best = {k: 0 for k in _FIELDS}
     results = {}
-    for j, b, g in candidates(plan, n_points):
-        plan.set_tuning(points_per_task=j, blocks_per_sm=b, big_scratch_bytes=g)
-        results[(j, b, g)] = _time(plan, params, grad, reps)
-    j, b, g = min(results, key=results.get)
-    best = {"points_per_task": j, "blocks_per_sm": b, "big_scratch_bytes": g}
+    for group in candidate_groups(plan, n_points, grad):
+        timed = []
+        for cand in group:
+            trial = dict(best, **cand)
+            plan.set_tuning(**trial)
+            ms = _time(plan, params, grad, reps)
+            results[tuple(sorted(trial.items()))] = ms
+            timed.append((ms, cand))
+        best.update(min(timed, key=lambda t: t[0])[1])
     plan.set_tuning(**best)
     if cache_path:
         cache[key] = best

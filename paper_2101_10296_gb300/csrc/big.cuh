@@ -85,6 +85,7 @@ bool split_ok(int n_in, int p, const int32_t *k, bool grad);
 // Per-device kernel attributes (shared memory of the chunk passes), set at
 // upload so that no attribute call falls inside a stream capture.
 cudaError_t split_prepare();
-cudaError_t launch_split_wave(BigLaunch B, bool grad, int64_t &launches, cudaStream_t s);
+// chunk_window: largest outer window of a shared-memory chunk pass (6..10)
+cudaError_t launch_split_wave(BigLaunch B, bool grad, int chunk_window, int64_t &launches, cudaStream_t s);
 
 }  // namespace qaoa

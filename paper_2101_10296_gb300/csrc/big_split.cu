@@ -31,6 +31,8 @@
 // often mixed qubits 0, 1 are register butterflies and <Z_0 Z_1>'s sign is a
 // compile-time function of the register.  Every load and store moves 256
 // contiguous bytes per warp instruction.
+#include <cuda.h>  // CUtensorMap and its enums (the encoder itself is fetched from the driver at run time)
+
 #include <mutex>
 #include <set>
 
@@ -505,7 +507,13 @@ __global__ void __launch_bounds__(128, MODE == kOuterGen ? 4 : 3) split_outer_ke
 // bits (contiguous runs of at least 64 bytes) and a window of w <=
 // kChunkMaxW outer qubits.  The window is mixed five qubits at a time by
 // register butterflies over amplitudes gathered from shared memory, so one
-// HBM round trip covers all of it.
+// HBM round trip covers all of it.  The chunk moves between HBM and shared
+// memory by the tensor memory accelerator: one cp.async.bulk.tensor per
+// chunk and direction, described by a tensor map of the block (the run, the
+// address bits between run and window, the window in two dimensions of at
+// most 256, the bits above it times the wave's items), completion of a load
+// tracked by an mbarrier.  The copies use the natural order (element e at
+// e); the rounds in between use a bank-swizzled order.
 constexpr int kChunkBits = 13;
 constexpr int kChunkMaxW = 10;
 constexpr int kChunkThreads = 256;
@@ -514,6 +522,68 @@ constexpr int kChunkThreads = 256;
 // 128-byte row) is flipped by the parity of the bits above it, so the four
 // 64-byte runs that a warp touches fall two in each half.
 __device__ __forceinline__ int swz(int s) { return s ^ ((__popc(s >> 4) & 1) << 3); }
+__device__ __forceinline__ int sidx(int s, bool swizzled) { return swizzled ? swz(s) : s; }
+
+// ---- tensor-memory-accelerator helpers (one thread issues, an mbarrier tracks loads)
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return uint32_t(__cvta_generic_to_shared(p)); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Orders this thread's earlier shared-memory accesses before later accesses
+// of the asynchronous (TMA) proxy.
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Load of one box into shared memory, completing on bar (issued by one thread).
+__device__ __forceinline__ void tma_load(const CUtensorMap *map, void *dst, uint64_t *bar, uint32_t bytes,
+                                         const int (&c)[5]) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
+        "%6}], [%7];" ::"r"(smem_addr(dst)),
+        "l"(map), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4]), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Store of one box from shared memory; returns once the box has been read
+// (issued by one thread, after every writer's fence_async_smem and a barrier).
+__device__ __forceinline__ void tma_store(const CUtensorMap *map, const void *src, const int (&c)[5]) {
+    asm volatile("cp.async.bulk.tensor.5d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3, %4, %5}], [%6];" ::"l"(
+                     map),
+                 "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4]), "r"(smem_addr(src))
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
+__device__ __forceinline__ void tma_store_drain() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits for phase `phase` of bar to complete, for at most limit_ns; false if
+// it has not.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t phase, uint64_t limit_ns) {
+    const uint32_t a = smem_addr(bar);
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(a), "r"(phase)
+            : "memory");
+        if (done) return true;
+        if (global_ns() - t0 > limit_ns) return false;
+    }
+}
+constexpr uint64_t kTmaWaitNs = 2000000000ull;  // 2 s: a load of 64 KB takes microseconds
 
 // slot with gn zero bits inserted at bit position pos
 __device__ __forceinline__ int spread_slot(int slot, int pos, int gn) {
@@ -543,7 +613,7 @@ __device__ __forceinline__ void slot_words(const DevCone *__restrict__ C, uint64
 template <int G, bool GEN>
 __device__ __forceinline__ void chunk_round(float2 *__restrict__ sm, int n_el, int pos, FirstMix f, bool inv,
                                             const DevCone *__restrict__ C, uint64_t cw, int lo_bits, int RB, int w0,
-                                            const float2 *__restrict__ lut) {
+                                            const float2 *__restrict__ lut, bool rd_swz, bool wr_swz) {
     constexpr int NR = 1 << G;
     for (int slot = threadIdx.x; slot < (n_el >> G); slot += kChunkThreads) {
         const int sb = spread_slot(slot, pos, G);
@@ -560,44 +630,46 @@ __device__ __forceinline__ void chunk_round(float2 *__restrict__ sm, int n_el, i
             for (int i = 0; i < NR; ++i) x[i] = __ldg(lut + __popcll(lo[i & 3] ^ hi[i >> 2]));
         } else {
 #pragma unroll
-            for (int i = 0; i < NR; ++i) x[i] = sm[swz(sb | (i << pos))];
+            for (int i = 0; i < NR; ++i) x[i] = sm[sidx(sb | (i << pos), rd_swz)];
         }
         if (inv)
             first_mix_regs<NR, true>(x, 0, G, f.a, f.b);
         else
             first_mix_regs<NR, false>(x, 0, G, f.a, f.b);
 #pragma unroll
-        for (int i = 0; i < NR; ++i) sm[swz(sb | (i << pos))] = x[i];
+        for (int i = 0; i < NR; ++i) sm[sidx(sb | (i << pos), wr_swz)] = x[i];
     }
 }
 
 template <bool GEN>
 __device__ __forceinline__ void chunk_round_any(int G, float2 *sm, int n_el, int pos, FirstMix f, bool inv,
                                                 const DevCone *C, uint64_t cw, int lo_bits, int RB, int w0,
-                                                const float2 *lut) {
+                                                const float2 *lut, bool rd_swz, bool wr_swz) {
     switch (G) {
-        case 1: chunk_round<1, GEN>(sm, n_el, pos, f, inv, C, cw, lo_bits, RB, w0, lut); break;
-        case 2: chunk_round<2, GEN>(sm, n_el, pos, f, inv, C, cw, lo_bits, RB, w0, lut); break;
-        case 3: chunk_round<3, GEN>(sm, n_el, pos, f, inv, C, cw, lo_bits, RB, w0, lut); break;
-        case 4: chunk_round<4, GEN>(sm, n_el, pos, f, inv, C, cw, lo_bits, RB, w0, lut); break;
-        default: chunk_round<5, GEN>(sm, n_el, pos, f, inv, C, cw, lo_bits, RB, w0, lut); break;
+        case 1: chunk_round<1, GEN>(sm, n_el, pos, f, inv, C, cw, lo_bits, RB, w0, lut, rd_swz, wr_swz); break;
+        case 2: chunk_round<2, GEN>(sm, n_el, pos, f, inv, C, cw, lo_bits, RB, w0, lut, rd_swz, wr_swz); break;
+        case 3: chunk_round<3, GEN>(sm, n_el, pos, f, inv, C, cw, lo_bits, RB, w0, lut, rd_swz, wr_swz); break;
+        case 4: chunk_round<4, GEN>(sm, n_el, pos, f, inv, C, cw, lo_bits, RB, w0, lut, rd_swz, wr_swz); break;
+        default: chunk_round<5, GEN>(sm, n_el, pos, f, inv, C, cw, lo_bits, RB, w0, lut, rd_swz, wr_swz); break;
     }
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kChunkThreads, 2) split_chunk_kernel(const __grid_constant__ BigLaunch L) {
-    extern __shared__ float4 sm4[];
-    float2 *sm = reinterpret_cast<float2 *>(sm4);
+__global__ void __launch_bounds__(kChunkThreads, 2)
+    split_chunk_kernel(const __grid_constant__ BigLaunch L, const __grid_constant__ CUtensorMap tmap) {
+    extern __shared__ __align__(1024) float2 sm[];
+    __shared__ uint64_t s_bar;  // completion of the chunk's load
     const int tid = threadIdx.x;
+    if (tid == 0) mbar_init(&s_bar);
+    __syncthreads();
+    uint32_t phase = 0;
     const int nin = L.n_in, RB = L.rb, w0 = L.w0, w = L.w1 - L.w0;
     const int lo_bits = kChunkBits - w;  // lowest address bits of the chunk (w0 >= lo_bits)
     const int n_el = 1 << kChunkBits;
     const int p = L.p;
     const int64_t chunks = int64_t(1) << (nin - kChunkBits);
     const int64_t ntask = L.n_items * chunks;
-    const int64_t block_amps = int64_t(1) << nin;
     const int64_t lowmask = (int64_t(1) << (w0 - lo_bits)) - 1;
-    const int runmask = (1 << lo_bits) - 1;
     for (int64_t task = blockIdx.x; task < ntask; task += gridDim.x) {
         const int64_t it = task / chunks;
         const int64_t ch = task - it * chunks;
@@ -612,15 +684,14 @@ __global__ void __launch_bounds__(kChunkThreads, 2) split_chunk_kernel(const __g
         const int64_t gj = int64_t(C->graph) * L.P + j;
         const FirstMix f1 = first_mix(L, gj, nin);
         const bool inv = MODE == kOuterFirst || (MODE == kOuterMix && L.sign < 0);
-        // element e of the chunk <-> address xb + (e & runmask) + ((e >> lo_bits) << w0);
-        // pairs of elements (2e', 2e'+1) are adjacent in both places and move as one float4
+        // element e of the chunk <-> address xb + (e & runmask) + ((e >> lo_bits) << w0) of
+        // item it; tensor coordinates: run, middle bits, window (two dimensions), high bits x item
         const int64_t xb = ((ch & lowmask) << lo_bits) | ((ch >> (w0 - lo_bits)) << (w0 + w));
-        float2 *__restrict__ gp = L.psi + it * block_amps + xb;
-        if (MODE != kOuterGen) {
-            for (int e2 = tid; e2 < (n_el >> 1); e2 += kChunkThreads) {
-                const int e = e2 << 1;
-                sm4[swz(e) >> 1] = *reinterpret_cast<const float4 *>(gp + (e & runmask) + (int64_t(e >> lo_bits) << w0));
-            }
+        const int crd[5] = {0, int(ch & lowmask), 0, 0,
+                            int(it * (int64_t(1) << (nin - w0 - w)) + (ch >> (w0 - lo_bits)))};
+        if (MODE != kOuterGen && tid == 0) {
+            fence_async_smem();  // the previous task's accesses come before the copy's writes
+            tma_load(&tmap, sm, &s_bar, uint32_t(n_el * sizeof(float2)), crd);
         }
         // cut word of the chunk's fixed bits (shell block and address bits outside the chunk)
         float mult = 1.f;
@@ -631,13 +702,27 @@ __global__ void __launch_bounds__(kChunkThreads, 2) split_chunk_kernel(const __g
             for (int a = lo_bits; a < nin; ++a)
                 if ((a < w0 || a >= w0 + w) && ((xb >> a) & 1)) cw ^= C->col[qubit_of(a, RB)];
         }
+        if (MODE != kOuterGen) {
+            // bounded wait; should it ever run out (never expected), record it,
+            // give the copy the same time again to land, and stop this block
+            const bool ok = mbar_wait(&s_bar, phase, kTmaWaitNs);
+            if (__syncthreads_or(!ok)) {
+                if (tid == 0) atomicOr(L.status, 4);
+                mbar_wait(&s_bar, phase, kTmaWaitNs);
+                return;
+            }
+            phase ^= 1u;
+        }
         __syncthreads();
         for (int g0 = 0; g0 < w; g0 += 5) {
             const int gn = min(5, w - g0);  // this round's qubits: chunk bits lo_bits + g0 ..
+            // the copies use the natural order, the rounds between them the swizzled one
+            const bool rd_swz = g0 > 0, wr_swz = g0 + gn < w || MODE == kOuterFirst;
             if (MODE == kOuterGen && g0 == 0)
-                chunk_round_any<true>(gn, sm, n_el, lo_bits, f1, false, C, cw, lo_bits, RB, w0, lut);
+                chunk_round_any<true>(gn, sm, n_el, lo_bits, f1, false, C, cw, lo_bits, RB, w0, lut, rd_swz, wr_swz);
             else
-                chunk_round_any<false>(gn, sm, n_el, lo_bits + g0, f1, inv, C, cw, lo_bits, RB, w0, lut);
+                chunk_round_any<false>(gn, sm, n_el, lo_bits + g0, f1, inv, C, cw, lo_bits, RB, w0, lut, rd_swz,
+                                       wr_swz);
             __syncthreads();
         }
         if (MODE == kOuterFirst) {
@@ -691,13 +776,52 @@ __global__ void __launch_bounds__(kChunkThreads, 2) split_chunk_kernel(const __g
             add_gp(dg, wgt2, L.grad, gj * 2 * p);
             if (outer_terms) add_gp(db, wgt2, L.grad, gj * 2 * p + p);
         } else {
-            for (int e2 = tid; e2 < (n_el >> 1); e2 += kChunkThreads) {
-                const int e = e2 << 1;
-                *reinterpret_cast<float4 *>(gp + (e & runmask) + (int64_t(e >> lo_bits) << w0)) = sm4[swz(e) >> 1];
-            }
+            fence_async_smem();  // every thread's writes, before the copy reads them
+            __syncthreads();
+            if (tid == 0) tma_store(&tmap, sm, crd);
         }
         __syncthreads();  // the next task reuses the shared chunk
     }
+    if (tid == 0) tma_store_drain();
+}
+
+// Tensor map of a wave's blocks as the chunk passes of window [w0, w0 + w) see
+// them (8-byte elements): the run of the lo = 13 - w lowest address bits,
+// the bits between run and window, the window in two dimensions of at most 2^8,
+// the bits above it times the items.  Dense: every stride is the previous one
+// times the previous extent.
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encoder() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(ptr);
+    });
+    return fn;
+}
+
+cudaError_t chunk_map(const BigLaunch &B, int w0, int w, CUtensorMap *map) {
+    EncodeTiledFn enc = encoder();
+    if (!enc) return cudaErrorNotSupported;
+    const int nin = B.n_in, lo = kChunkBits - w, wa = w < 8 ? w : 8;
+    const cuuint64_t dim[5] = {cuuint64_t(1) << lo, cuuint64_t(1) << (w0 - lo), cuuint64_t(1) << wa,
+                               cuuint64_t(1) << (w - wa), cuuint64_t(B.n_items) << (nin - w0 - w)};
+    const cuuint64_t stride[4] = {cuuint64_t(8) << lo, cuuint64_t(8) << w0, cuuint64_t(8) << (w0 + wa),
+                                  cuuint64_t(8) << (w0 + w)};
+    const cuuint32_t box[5] = {1u << lo, 1u, 1u << wa, 1u << (w - wa), 1u};
+    const cuuint32_t estride[5] = {1u, 1u, 1u, 1u, 1u};
+    const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 5, B.psi, dim, stride, box, estride,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 }  // namespace
@@ -735,7 +859,8 @@ cudaError_t split_prepare() {
     return e;
 }
 
-cudaError_t launch_split_wave(BigLaunch B, bool grad, int64_t &launches, cudaStream_t s) {
+cudaError_t launch_split_wave(BigLaunch B, bool grad, int chunk_window, int64_t &launches, cudaStream_t s) {
+    const int cw_max = chunk_window < 6 ? 6 : (chunk_window > kChunkMaxW ? kChunkMaxW : chunk_window);
     const int RB = grad ? kSplitRbGrad : kSplitRbEnergy, T = RB + 5;
     const int nin = B.n_in;
     B.rb = RB;
@@ -748,7 +873,7 @@ cudaError_t launch_split_wave(BigLaunch B, bool grad, int64_t &launches, cudaStr
     std::vector<Win> win;
     for (int w0 = T; w0 < nin;) {
         const int left = nin - w0;
-        const int n = left > 5 ? std::min(left, kChunkMaxW) : left;
+        const int n = left > 5 ? std::min(left, cw_max) : left;
         win.push_back({w0, w0 + n, left > 5});
         w0 += n;
     }
@@ -766,6 +891,8 @@ cudaError_t launch_split_wave(BigLaunch B, bool grad, int64_t &launches, cudaStr
         B.sign = sign;
         if (win[w].chunk) {
             const size_t smem = size_t(sizeof(float2)) << kChunkBits;
+            CUtensorMap map;
+            if (cudaError_t e = chunk_map(B, B.w0, B.w1 - B.w0, &map); e != cudaSuccess) return e;
             const int64_t tasks = B.n_items << (nin - kChunkBits);
             const void *fn = mode == kOuterGen   ? (const void *)split_chunk_kernel<kOuterGen>
                              : mode == kOuterMix ? (const void *)split_chunk_kernel<kOuterMix>
@@ -773,11 +900,11 @@ cudaError_t launch_split_wave(BigLaunch B, bool grad, int64_t &launches, cudaStr
             if (cudaError_t e = allow_chunk_smem(fn, mode); e != cudaSuccess) return e;
             const int grid = int(std::min<int64_t>(occupancy_grid(fn, kChunkThreads, smem), std::max<int64_t>(tasks, 1)));
             if (mode == kOuterGen)
-                split_chunk_kernel<kOuterGen><<<grid, kChunkThreads, smem, s>>>(B);
+                split_chunk_kernel<kOuterGen><<<grid, kChunkThreads, smem, s>>>(B, map);
             else if (mode == kOuterMix)
-                split_chunk_kernel<kOuterMix><<<grid, kChunkThreads, smem, s>>>(B);
+                split_chunk_kernel<kOuterMix><<<grid, kChunkThreads, smem, s>>>(B, map);
             else
-                split_chunk_kernel<kOuterFirst><<<grid, kChunkThreads, smem, s>>>(B);
+                split_chunk_kernel<kOuterFirst><<<grid, kChunkThreads, smem, s>>>(B, map);
         } else {
             const int64_t tasks = B.n_items << (nin - 10);
             if (mode == kOuterGen) {

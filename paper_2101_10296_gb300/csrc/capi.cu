@@ -168,7 +168,7 @@ cudaError_t run_big(const qaoa_device_plan *d, const qaoa_plan *plan, int64_t P,
             B.item0 = i0;
             B.n_items = std::min(wave, items - i0);
             if (split) {
-                e = launch_split_wave(B, g, dm->all_launches, s);
+                e = launch_split_wave(B, g, d->chunk_window, dm->all_launches, s);
                 continue;
             }
             for (const BigPass &ps : passes) {
@@ -248,7 +248,8 @@ int run(const qaoa_plan *plan, int64_t n_points, const double *params, double *e
         {
             // one point's phase tables, mixer data and kappa powers
             const int64_t row_bytes = int64_t(p) * ((d->cmax1 + 1) * int64_t(sizeof(float2)) + kRegKpow * int64_t(sizeof(float)));
-            const int64_t warps = grad ? d->reg_g.warps : d->reg_e.warps;
+            const int rgi = d->reg_bits_grad == 5 ? 1 : 0;
+            const int64_t warps = grad ? d->reg_g[rgi].warps : d->reg_e.warps;
             int64_t jpt = d->points_per_task;
             if (jpt <= 0) {
                 jpt = std::min<int64_t>(32, std::max<int64_t>(1, 8192 / row_bytes));
@@ -268,10 +269,12 @@ int run(const qaoa_plan *plan, int64_t n_points, const double *params, double *e
         L.terms = terms;
         L.status = d->status;
         if (grad) {
-            L.work = as_reg(d, d->reg_g);
+            const int rg = d->reg_bits_grad == 5 ? 5 : 4;
+            L.work = as_reg(d, d->reg_g[rg - 4]);
             if (L.work.warps > 0) {
-                int64_t grid = std::min<int64_t>(tuned_grid(d, reg_grad_grid(wide, smem, p)), (L.work.warps * tasks_per + 3) / 4);
-                e = launch_reg_grad(L, wide, int(std::max<int64_t>(grid, 1)), s);
+                int64_t grid = std::min<int64_t>(tuned_grid(d, reg_grad_grid(wide, smem, p, rg)),
+                                                 (L.work.warps * tasks_per + 3) / 4);
+                e = launch_reg_grad(L, wide, rg, int(std::max<int64_t>(grid, 1)), s);
             }
         } else {
             L.work = as_reg(d, d->reg_e);
@@ -304,7 +307,8 @@ extern "C" void qaoa_device_release(qaoa_plan *plan) {
     if (d->device >= 0) cudaSetDevice(d->device);
     cudaFree(d->cones);
     free_work(d->reg_e);
-    free_work(d->reg_g);
+    free_work(d->reg_g[0]);
+    free_work(d->reg_g[1]);
     for (auto &bs : d->big) {
         cudaFree(bs.d_cones);
         cudaFree(bs.d_ystart);
@@ -464,7 +468,8 @@ extern "C" int qaoa_plan_upload(qaoa_plan *plan) {
             cudaMemcpy(d->shell, shell_tab.data(), shell_tab.size() * sizeof(uint64_t), cudaMemcpyHostToDevice);
     }
     if (rc == QAOA_OK) rc = build_work(hc, reg_idx, kRegBitsEnergy, d->reg_e);
-    if (rc == QAOA_OK) rc = build_work(hc, reg_idx, kRegBitsGrad, d->reg_g);
+    if (rc == QAOA_OK) rc = build_work(hc, reg_idx, 4, d->reg_g[0]);
+    if (rc == QAOA_OK) rc = build_work(hc, reg_idx, 5, d->reg_g[1]);
     if (rc == QAOA_OK) {
         std::vector<double> half(size_t(plan->n_graphs));
         for (int32_t g = 0; g < plan->n_graphs; ++g) half[g] = 0.5 * double(plan->weight_sum[g]);
@@ -611,7 +616,9 @@ extern "C" int qaoa_kernel_time(qaoa_plan *plan, double *ms, int64_t *launches, 
 }
 
 extern "C" int qaoa_plan_set_tuning(qaoa_plan *plan, const qaoa_tuning_t *t) {
-    if (!plan || !t || t->points_per_task < 0 || t->blocks_per_sm < 0 || t->big_scratch_bytes < 0) {
+    if (!plan || !t || t->points_per_task < 0 || t->blocks_per_sm < 0 || t->big_scratch_bytes < 0 ||
+        (t->reg_bits_grad != 0 && t->reg_bits_grad != 4 && t->reg_bits_grad != 5) ||
+        (t->chunk_window != 0 && (t->chunk_window < 6 || t->chunk_window > 10))) {
         set_error("bad plan or tuning values");
         return QAOA_E_INVALID;
     }
@@ -620,6 +627,8 @@ extern "C" int qaoa_plan_set_tuning(qaoa_plan *plan, const qaoa_tuning_t *t) {
     plan->dev->points_per_task = t->points_per_task;
     plan->dev->blocks_per_sm = t->blocks_per_sm;
     plan->dev->big_budget = t->big_scratch_bytes > 0 ? size_t(t->big_scratch_bytes) : size_t(1) << 30;
+    plan->dev->reg_bits_grad = t->reg_bits_grad == 5 ? 5 : 4;
+    plan->dev->chunk_window = t->chunk_window > 0 ? t->chunk_window : 10;
     return QAOA_OK;
 }
 
@@ -631,6 +640,8 @@ extern "C" int qaoa_plan_get_tuning(const qaoa_plan *plan, qaoa_tuning_t *t) {
     t->points_per_task = plan->dev ? plan->dev->points_per_task : 0;
     t->blocks_per_sm = plan->dev ? plan->dev->blocks_per_sm : 0;
     t->big_scratch_bytes = plan->dev ? int64_t(plan->dev->big_budget) : int64_t(1) << 30;
+    t->reg_bits_grad = plan->dev ? plan->dev->reg_bits_grad : 4;
+    t->chunk_window = plan->dev ? plan->dev->chunk_window : 10;
     return QAOA_OK;
 }
 

@@ -249,7 +249,8 @@ __device__ __forceinline__ bool seg_sum(float &v, int key) {
 // PC > 0: the depth p is the compile-time constant PC (layer loops unrolled);
 // PC = 0: p is read from the launch arguments.
 template <int R, typename MT, bool GRAD, int PC>
-__global__ void __launch_bounds__(kRegBlock, GRAD ? kGradMinBlocks : kEnergyMinBlocks) reg_cone_kernel(const RegLaunch L) {
+__global__ void __launch_bounds__(kRegBlock, GRAD ? (R <= 4 ? kGradMinBlocks : kGradMinBlocks5) : kEnergyMinBlocks)
+    reg_cone_kernel(const RegLaunch L) {
     constexpr int NA = 1 << R;
     extern __shared__ float2 s_tab[];
     const int lane = threadIdx.x & 31;

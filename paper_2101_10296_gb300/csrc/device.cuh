@@ -129,12 +129,14 @@ cudaError_t launch_prep(const PrepArgs &a, cudaStream_t s);
 // wide = some cone has more than 32 edges (64-bit cut words).  Dynamic
 // shared memory: 4 warps x jpt x p x cmax1 float2 (phase tables).
 cudaError_t launch_reg_energy(const RegLaunch &a, bool wide, int grid, cudaStream_t s);
-cudaError_t launch_reg_grad(const RegLaunch &a, bool wide, int grid, cudaStream_t s);
+// rg: register qubits per thread of the adjoint kernel (4 or 5)
+cudaError_t launch_reg_grad(const RegLaunch &a, bool wide, int rg, int grid, cudaStream_t s);
 cudaError_t launch_cut_table(const DevCone *cone, uint8_t *out, int32_t n, int32_t *status, cudaStream_t s);
 // occupancy-sized persistent grids for a given dynamic shared memory size
 int reg_energy_grid(bool wide, size_t smem);
 int sm_count();  // multiprocessors of the current device (cached)
-int reg_grad_grid(bool wide, size_t smem, int p);
+int reg_grad_grid(bool wide, size_t smem, int p, int rg);
+cudaError_t reg_grad_prepare();
 // Raises the register kernels' dynamic shared memory limit to kRegMaxSmem
 // (once per device; called at upload, outside any stream capture).
 cudaError_t reg_prepare();
@@ -152,10 +154,13 @@ constexpr int kRegBitsEnergy = QAOA_REG_BITS_ENERGY;
 constexpr int kRegBitsGrad = QAOA_REG_BITS_GRAD;
 constexpr int kLaneBits = 5;
 // resident 128-thread blocks per SM the register allocation is sized for
+// (the adjoint with four register qubits; with five it holds twice the
+// amplitudes and is sized for two)
 #ifndef QAOA_GRAD_MIN_BLOCKS
 #define QAOA_GRAD_MIN_BLOCKS 4
 #endif
 constexpr int kGradMinBlocks = QAOA_GRAD_MIN_BLOCKS;
+constexpr int kGradMinBlocks5 = 2;
 constexpr int kEnergyMinBlocks = 3;
 // largest inner part the register kernels take (both must fit)
 constexpr int kRegMaxInner = (kRegBitsEnergy < kRegBitsGrad ? kRegBitsEnergy : kRegBitsGrad) + kLaneBits;

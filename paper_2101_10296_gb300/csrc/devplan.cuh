@@ -33,7 +33,8 @@ struct qaoa_device_plan {
     int device = -1;
     qaoa::DevCone *cones = nullptr;
     int64_t n_cones = 0;
-    DevWork reg_e, reg_g;  // work lists of the energy and the adjoint kernels
+    DevWork reg_e;       // work list of the energy kernels
+    DevWork reg_g[2];    // of the adjoint kernels with 4 and 5 register qubits
     std::vector<BigShape> big;
     size_t big_budget = size_t(1) << 30;  // scratch bytes per call for big cones
     double *half_edges = nullptr;
@@ -43,6 +44,8 @@ struct qaoa_device_plan {
     int64_t n_big = 0;
     int32_t points_per_task = 0;  // 0: default (see qaoa_tuning_t)
     int32_t blocks_per_sm = 0;
+    int32_t reg_bits_grad = 4;    // adjoint register qubits (4 or 5)
+    int32_t chunk_window = 10;    // largest outer window of a shared-memory chunk pass (6..10)
     bool timing = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
     int64_t all_launches = 0;

@@ -155,8 +155,6 @@ int reg_energy_grid(bool wide, size_t smem) {
     return wide ? occupancy_grid((const void *)reg_cone_kernel<kRegBitsEnergy, uint64_t, false, 0>, kRegBlock, smem)
                 : occupancy_grid((const void *)reg_cone_kernel<kRegBitsEnergy, uint32_t, false, 0>, kRegBlock, smem);
 }
-cudaError_t reg_grad_prepare();  // kernels_grad.cu
-
 cudaError_t reg_prepare() {
     static std::mutex mu;
     static std::set<int> done;

@@ -1,67 +1,29 @@
-// Adjoint instantiations of the register-resident cone kernel: the depth p
-// is a compile-time constant for p = 1, 2, 3 (layer loops fully unrolled),
-// read at run time otherwise.
-#include "cone_kernel.cuh"
+// Adjoint register kernels with four register qubits per thread (the
+// default width), and the dispatch over the widths.
+#include "kernels_grad_impl.cuh"
 
 namespace qaoa {
 
-int occupancy_grid(const void *fn, int block, size_t smem);
+template cudaError_t reg_grad_prepare_r<4>();
+template int reg_grad_grid_r<4>(bool, size_t, int);
+template cudaError_t launch_reg_grad_r<4>(const RegLaunch &, bool, int, cudaStream_t);
 
-namespace {
-
-template <typename MT, int PC>
-const void *grad_fn() {
-    return (const void *)reg_cone_kernel<kRegBitsGrad, MT, true, PC>;
-}
-
-template <typename MT>
-const void *grad_fn_for(int p) {
-    switch (p) {
-        case 1: return grad_fn<MT, 1>();
-        case 2: return grad_fn<MT, 2>();
-        case 3: return grad_fn<MT, 3>();
-        default: return grad_fn<MT, 0>();
-    }
-}
-
-template <typename MT, int PC>
-void launch(const RegLaunch &a, int grid, size_t sm, cudaStream_t s) {
-    reg_cone_kernel<kRegBitsGrad, MT, true, PC><<<grid, kRegBlock, sm, s>>>(a);
-}
-
-template <typename MT>
-void launch_for(const RegLaunch &a, int grid, size_t sm, cudaStream_t s) {
-    switch (a.p) {
-        case 1: launch<MT, 1>(a, grid, sm, s); break;
-        case 2: launch<MT, 2>(a, grid, sm, s); break;
-        case 3: launch<MT, 3>(a, grid, sm, s); break;
-        default: launch<MT, 0>(a, grid, sm, s); break;
-    }
-}
-
-}  // namespace
+// instantiated in kernels_grad5.cu
+extern template cudaError_t reg_grad_prepare_r<5>();
+extern template int reg_grad_grid_r<5>(bool, size_t, int);
+extern template cudaError_t launch_reg_grad_r<5>(const RegLaunch &, bool, int, cudaStream_t);
 
 cudaError_t reg_grad_prepare() {
-    cudaError_t e = cudaSuccess;
-    for (int p = 0; p <= 3 && e == cudaSuccess; ++p) {
-        for (int w = 0; w < 2 && e == cudaSuccess; ++w)
-            e = cudaFuncSetAttribute(w ? grad_fn_for<uint64_t>(p) : grad_fn_for<uint32_t>(p),
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kRegMaxSmem);
-    }
-    return e;
+    cudaError_t e = reg_grad_prepare_r<4>();
+    return e == cudaSuccess ? reg_grad_prepare_r<5>() : e;
 }
 
-int reg_grad_grid(bool wide, size_t smem, int p) {
-    return occupancy_grid(wide ? grad_fn_for<uint64_t>(p) : grad_fn_for<uint32_t>(p), kRegBlock, smem);
+int reg_grad_grid(bool wide, size_t smem, int p, int rg) {
+    return rg == 5 ? reg_grad_grid_r<5>(wide, smem, p) : reg_grad_grid_r<4>(wide, smem, p);
 }
 
-cudaError_t launch_reg_grad(const RegLaunch &a, bool wide, int grid, cudaStream_t s) {
-    const size_t sm = reg_smem_bytes(a.jpt, a.p, a.cmax1, true);
-    if (wide)
-        launch_for<uint64_t>(a, grid, sm, s);
-    else
-        launch_for<uint32_t>(a, grid, sm, s);
-    return cudaGetLastError();
+cudaError_t launch_reg_grad(const RegLaunch &a, bool wide, int rg, int grid, cudaStream_t s) {
+    return rg == 5 ? launch_reg_grad_r<5>(a, wide, grid, s) : launch_reg_grad_r<4>(a, wide, grid, s);
 }
 
 }  // namespace qaoa

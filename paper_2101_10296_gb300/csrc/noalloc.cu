@@ -198,7 +198,7 @@ extern "C" int qaoa_energy_noalloc(const qaoa_plan *plan, int64_t n_points, cons
                 B.item0 = i0;
                 B.n_items = std::min(wave, items - i0);
                 if (bs.split_e) {
-                    e = launch_split_wave(B, false, launches, s);
+                    e = launch_split_wave(B, false, d->chunk_window, launches, s);
                     continue;
                 }
                 for (const BigPass &ps : bs.fwd) {

@@ -38,7 +38,8 @@ class QAOAError(RuntimeError):
 
 
 class Tuning(C.Structure):
-    _fields_ = [("points_per_task", C.c_int32), ("blocks_per_sm", C.c_int32), ("big_scratch_bytes", C.c_int64)]
+    _fields_ = [("points_per_task", C.c_int32), ("blocks_per_sm", C.c_int32), ("big_scratch_bytes", C.c_int64),
+                ("reg_bits_grad", C.c_int32), ("chunk_window", C.c_int32)]
 
 
 class PlanInfo(C.Structure):
@@ -357,9 +358,9 @@ class Plan:
                                       _stream_handle(stream)))
         return (e, g, t) if terms else (e, g)
 
-    def set_tuning(self, points_per_task=0, blocks_per_sm=0, big_scratch_bytes=0):
+    def set_tuning(self, points_per_task=0, blocks_per_sm=0, big_scratch_bytes=0, reg_bits_grad=0, chunk_window=0):
         """Launch tuning for later calls (0 = default); see qaoa_tuning_t."""
-        t = Tuning(points_per_task, blocks_per_sm, big_scratch_bytes)
+        t = Tuning(points_per_task, blocks_per_sm, big_scratch_bytes, reg_bits_grad, chunk_window)
         _check(lib().qaoa_plan_set_tuning(self._h, C.byref(t)))
 
     def get_tuning(self):

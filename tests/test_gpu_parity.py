@@ -679,7 +679,8 @@ def test_tuning_leaves_results_unchanged(q):
     th = _params(np.stack([I.draw_params(3, 7, 30 + g) for g in range(G)]))
     e0, g0 = plan.energy_grad(th)
     for tune in ({"points_per_task": 1}, {"points_per_task": 3, "blocks_per_sm": 1},
-                 {"points_per_task": 16, "big_scratch_bytes": 1 << 20}):
+                 {"points_per_task": 16, "big_scratch_bytes": 1 << 20}, {"reg_bits_grad": 5},
+                 {"reg_bits_grad": 5, "points_per_task": 2, "chunk_window": 6}, {"chunk_window": 8}):
         plan.set_tuning(**tune)
         assert all(plan.get_tuning()[k] == v for k, v in tune.items())
         e1, g1 = plan.energy_grad(th)
@@ -709,6 +710,34 @@ def test_autotune_picks_and_caches(q, tmp_path):
     e = plan.energy(th)
     plan.set_tuning()
     assert np.allclose(e.cpu().numpy(), plan.energy(th).cpu().numpy(), rtol=E_REL_TOL, atol=0)
+
+
+def test_autotune_searches_tile_shapes_per_plan_shape(q, tmp_path):
+    """The tile-shape search depends on the plan: a plan of small cones only
+    (register kernels) tries both adjoint register tiles and no chunk windows;
+    one with large-state cones also tries chunk windows and wave sizes.  Both
+    searches pick a tuning under which the results are the ones the default
+    gives, and the two plan shapes are cached under different keys."""
+    from paper_2101_10296_gb300 import autotune
+    small = q.Plan([I.random_regular(200, 3, s) for s in (1, 2)], 2)
+    large = q.Plan(I.torus(6, 6), 3)
+    c_small = autotune.candidates(small, 16, grad=True)
+    c_large = autotune.candidates(large, 16, grad=True)
+    assert {c.get("reg_bits_grad") for c in c_small} >= {4, 5}
+    assert not any("chunk_window" in c for c in c_small)
+    assert {c.get("chunk_window") for c in c_large} >= {8, 10}
+    cache = str(tmp_path / "tune.json")
+    for plan, G, p, P in ((small, 2, 2, 16), (large, 1, 3, 4)):
+        th = _params(np.stack([I.draw_params(p, P, 60 + g) for g in range(G)]))
+        e0, g0 = plan.energy_grad(th)
+        best, results = autotune.autotune(plan, th, grad=True, reps=1, cache_path=cache)
+        assert results and all(v > 0 for v in results.values())
+        e1, g1 = plan.energy_grad(th)
+        assert np.allclose(e1.cpu().numpy(), e0.cpu().numpy(), rtol=E_REL_TOL, atol=0)
+        assert np.allclose(g1.cpu().numpy(), g0.cpu().numpy(), rtol=2 * G_REL_TOL, atol=1e-6)
+        assert plan.device_status() == 0
+    import json
+    assert len(json.load(open(cache))) == 2
 
 
 # -------------------------------------- full-size configurations, sampled
