@@ -518,9 +518,12 @@ constexpr int kChunkBits = 13;
 constexpr int kChunkMaxW = 10;
 constexpr int kChunkThreads = 256;
 
-// Bank swizzle: bit 3 of the shared-memory index (which 64-byte half of a
-// 128-byte row) is flipped by the parity of the bits above it, so the four
-// 64-byte runs that a warp touches fall two in each half.
+// Bank swizzle for runs of eight amplitudes (a window of ten): bit 3 of the
+// shared-memory index (which 64-byte half of a 128-byte row) is flipped by
+// the parity of the bits above it, so the four 64-byte runs that a warp
+// touches fall two in each half.  With runs of 16 or more the rounds' lanes
+// read 16 consecutive amplitudes per half-warp, free of conflicts as they
+// are, and no swizzle is applied.
 __device__ __forceinline__ int swz(int s) { return s ^ ((__popc(s >> 4) & 1) << 3); }
 __device__ __forceinline__ int sidx(int s, bool swizzled) { return swizzled ? swz(s) : s; }
 
@@ -717,7 +720,8 @@ __global__ void __launch_bounds__(kChunkThreads, 2)
         for (int g0 = 0; g0 < w; g0 += 5) {
             const int gn = min(5, w - g0);  // this round's qubits: chunk bits lo_bits + g0 ..
             // the copies use the natural order, the rounds between them the swizzled one
-            const bool rd_swz = g0 > 0, wr_swz = g0 + gn < w || MODE == kOuterFirst;
+            const bool swz_on = lo_bits < 4;
+            const bool rd_swz = swz_on && g0 > 0, wr_swz = swz_on && (g0 + gn < w || MODE == kOuterFirst);
             if (MODE == kOuterGen && g0 == 0)
                 chunk_round_any<true>(gn, sm, n_el, lo_bits, f1, false, C, cw, lo_bits, RB, w0, lut, rd_swz, wr_swz);
             else
@@ -737,7 +741,8 @@ __global__ void __launch_bounds__(kChunkThreads, 2)
                 const int sb = spread_slot(slot, lo_bits, gn);
                 float2 x[32];
 #pragma unroll
-                for (int i = 0; i < 32; ++i) x[i] = i < nreg ? sm[swz(sb | (i << lo_bits))] : make_float2(0.f, 0.f);
+                for (int i = 0; i < 32; ++i)
+                    x[i] = i < nreg ? sm[sidx(sb | (i << lo_bits), lo_bits < 4)] : make_float2(0.f, 0.f);
                 uint64_t base = cw;
                 for (int b = 0; b < lo_bits; ++b)
                     if ((sb >> b) & 1) base ^= C->col[qubit_of(b, RB)];

@@ -156,6 +156,13 @@ __device__ __forceinline__ float2 bfly(float2 u, float2 v, float tau) {
     return make_float2(fmaf(tau, v.y, u.x), fmaf(-tau, v.x, u.y));
 }
 
+// d += Im(conj(a) b) as two FMAs (written out: the compiler may not contract
+// a separate product and sum)
+__device__ __forceinline__ void acc_imconj(float &d, float2 a, float2 b) {
+    d = fmaf(a.x, b.y, d);
+    d = fmaf(-a.y, b.x, d);
+}
+
 // (I - i tau X_q) on register qubits q < KQ (compile-time count)
 template <int R, int KQ>
 __device__ __forceinline__ void mix_reg_fixed(float2 (&x)[1 << R], float tau) {
@@ -245,6 +252,13 @@ __device__ __forceinline__ bool seg_sum(float &v, int key) {
     const int prev = __shfl_up_sync(kFull, key, 1);
     return lane == 0 || prev != key;
 }
+
+// Outputs reduced per unrolled copy of the reduction loop (1 keeps one copy of
+// its code: the adjoint body is large enough for instruction fetch to stall).
+#ifndef QAOA_FLUSH_UNROLL
+#define QAOA_FLUSH_UNROLL 1
+#endif
+constexpr int kFlushUnroll = QAOA_FLUSH_UNROLL;
 
 // PC > 0: the depth p is the compile-time constant PC (layer loops unrolled);
 // PC = 0: p is read from the launch arguments.
@@ -349,6 +363,7 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? (R <= 4 ? kGradMinBlocks : k
             if (uni) {
                 const int gn = (jj & (G - 1)) + 1, jf = jj + 1 - gn;
                 const int pt = lane & (G - 1), part = lane / G;
+#pragma unroll(kFlushUnroll)
                 for (int c = 0; c < NOUT; ++c) {
                     const float *src = red + (c * G + pt) * 32;
                     Dfl acc{0.f, 0.f};
@@ -406,14 +421,12 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? (R <= 4 ? kGradMinBlocks : k
             if constexpr (!GRAD) {
                 if (PC != 1) cw.flip(fw);  // back to no flips for the next point
             } else {
-                // co-state lambda = -1/2 Z_0 Z_1 psi, in the same stored form
+                // co-state lambda = -1/2 Z_0 Z_1 psi, in the same stored form; r
+                // holds Z_0 Z_1 psi (signs only) and the -1/2 goes into the weight
                 float2 r[NA];
 #pragma unroll
-                for (int i = 0; i < NA; ++i) {
-                    const float sg = ((i ^ (i >> 1)) & 1) ? 0.5f : -0.5f;
-                    r[i] = make_float2(sg * x[i].x, sg * x[i].y);
-                }
-                const float gw2 = active ? 2.f * wgt : 0.f;
+                for (int i = 0; i < NA; ++i) r[i] = ((i ^ (i >> 1)) & 1) ? make_float2(-x[i].x, -x[i].y) : x[i];
+                const float gw2 = active ? -wgt : 0.f;  // 2 x (-1/2) x orbit weight
                 const float sig_end = sig;
                 // Im<lambda|psi> = <psi_end|O|psi_end> is real at every point of
                 // the sweep (and within every shell block), so C may be replaced
@@ -439,7 +452,8 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? (R <= 4 ? kGradMinBlocks : k
                             for (int i = 0; i < NA; ++i) {
                                 if (i & (1 << q)) continue;
                                 const int i2 = i | (1 << q);
-                                d[i >> 2] += imconj(r[i], x[i2]) + imconj(r[i2], x[i]);
+                                acc_imconj(d[i >> 2], r[i], x[i2]);
+                                acc_imconj(d[i >> 2], r[i2], x[i]);
                             }
                         }
                     }
@@ -465,7 +479,7 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? (R <= 4 ? kGradMinBlocks : k
                             ro.x = __shfl_xor_sync(kFull, r[i].x, m);
                             ro.y = __shfl_xor_sync(kFull, r[i].y, m);
                             if (mine) {
-                                e4[i >> 2] += imconj(r[i], xo);
+                                acc_imconj(e4[i >> 2], r[i], xo);
                                 x[i] = bfly(x[i], xo, -tau);
                                 r[i] = bfly(r[i], ro, -tau);
                             }
