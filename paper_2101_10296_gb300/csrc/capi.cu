@@ -29,6 +29,8 @@ void free_work(DevWork &w) {
     cudaFree(w.order);
     cudaFree(w.prefix);
     cudaFree(w.warp_first);
+    cudaFree(w.slot_cone);
+    cudaFree(w.warp_graph);
     w = DevWork{};
 }
 
@@ -60,10 +62,20 @@ int build_work(const std::vector<DevCone> &hc, const std::vector<int32_t> &idx, 
     const int64_t slots = pos;
     const int64_t warps = slots / 32;
     std::vector<int32_t> first(size_t(std::max<int64_t>(warps, 1)), 0);
+    std::vector<int32_t> wgraph(first.size(), 0);
     size_t ci = 0;
     for (int64_t wi = 0; wi < warps; ++wi) {
         while (ci + 1 < order.size() && start[ci + 1] <= wi * 32) ++ci;
         first[wi] = int32_t(ci);
+        wgraph[wi] = order.empty() ? 0 : hc[order[ci]].graph;
+    }
+    // the cone owning each slot (the last cone starting at or before it), so that
+    // a kernel finds it with one load instead of a walk along the start list
+    std::vector<int32_t> scone(size_t(std::max<int64_t>(slots, 1)), 0);
+    ci = 0;
+    for (int64_t sl = 0; sl < slots; ++sl) {
+        while (ci + 1 < order.size() && start[ci + 1] <= sl) ++ci;
+        scone[size_t(sl)] = int32_t(ci);
     }
     w.slots = slots;
     w.warps = warps;
@@ -74,6 +86,12 @@ int build_work(const std::vector<DevCone> &hc, const std::vector<int32_t> &idx, 
     if ((e = cudaMalloc(&w.prefix, start.size() * sizeof(int64_t))) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
     if ((e = cudaMalloc(&w.warp_first, first.size() * sizeof(int32_t))) != cudaSuccess)
         return cuda_fail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&w.slot_cone, scone.size() * sizeof(int32_t))) != cudaSuccess)
+        return cuda_fail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&w.warp_graph, wgraph.size() * sizeof(int32_t))) != cudaSuccess)
+        return cuda_fail(e, "cudaMalloc");
+    cudaMemcpy(w.slot_cone, scone.data(), scone.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    cudaMemcpy(w.warp_graph, wgraph.data(), wgraph.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
     cudaMemcpy(w.order, order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
     cudaMemcpy(w.prefix, start.data(), start.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
     if ((e = cudaMemcpy(w.warp_first, first.data(), first.size() * sizeof(int32_t), cudaMemcpyHostToDevice)) !=
@@ -89,6 +107,8 @@ RegWork as_reg(const qaoa_device_plan *d, const DevWork &w) {
     r.order = w.order;
     r.start = w.prefix;
     r.warp_first = w.warp_first;
+    r.slot_cone = w.slot_cone;
+    r.warp_graph = w.warp_graph;
     r.n_cones = w.n;
     r.slots = w.slots;
     r.warps = w.warps;
@@ -112,13 +132,12 @@ int ensure_uploaded(const qaoa_plan *plan) {
     return check_device(plan);
 }
 
-// Register qubits per thread of the adjoint kernel: the tuned value, else 4
-// at p = 1 (cones of two inner qubits: more blocks per SM win) and 5 above
-// (one lane qubit fewer to shuffle; measured 6% faster on random cubic
-// graphs at p = 2, 25% slower on the p = 1 benchmark mix).
-int reg_bits_for(const qaoa_device_plan *d, int p) {
-    if (d->reg_bits_grad == 4 || d->reg_bits_grad == 5) return d->reg_bits_grad;
-    return p == 1 ? 4 : 5;
+// Register qubits per thread of the adjoint kernel: the tuned value, else 4.
+// Which width wins depends on the plan (measured: 5 is 6% faster on random
+// cubic graphs at p = 2, whose cones have six inner qubits, but 14-25%
+// slower on tori with eight and on the p = 1 mix), so the autotuner picks it.
+int reg_bits_for(const qaoa_device_plan *d, int) {
+    return d->reg_bits_grad == 5 ? 5 : 4;
 }
 
 // Persistent grid: the occupancy-sized grid, or blocks_per_sm per SM if tuned

@@ -297,9 +297,21 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? (R <= 4 ? kGradMinBlocks : k
         const int64_t j0 = jb * L.jpt;
         const int jn = int(L.n_points - j0 < L.jpt ? L.n_points - j0 : L.jpt);
         const int64_t slot = w * 32 + lane;
-        int ci = W.warp_first[w];
-        if (slot < W.slots)
-            while (W.start[ci + 1] <= slot) ++ci;
+        // Stage the phase tables, mixer data and kappa powers of points j0 ..
+        // j0+jn-1 of the warp's graph first: they depend on nothing else, so
+        // their loads overlap the cone descriptor's.
+        const int gwarp = __ldg(W.warp_graph + w);
+        __syncwarp();  // the previous task's reads of the tables are done
+        {
+            const float2 *__restrict__ src = L.lut + (int64_t(gwarp) * L.n_points + j0) * row;
+            for (int e = lane; e < jn * row; e += 32) my_tab[e] = __ldg(src + e);
+            const float2 *__restrict__ msrc = L.mix + (int64_t(gwarp) * L.n_points + j0) * p;
+            for (int e = lane; e < jn * p; e += 32) my_mix[e] = __ldg(msrc + e);
+            const float *__restrict__ ksrc = L.kpow + (int64_t(gwarp) * L.n_points + j0) * p * kKpow;
+            for (int e = lane; e < jn * p * kRegKpow; e += 32)
+                my_kp[e] = __ldg(ksrc + (e / kRegKpow) * kKpow + (e % kRegKpow));
+        }
+        const int ci = slot < W.slots ? __ldg(W.slot_cone + slot) : __ldg(W.warp_first + w);
         const DevCone *__restrict__ C = W.cones + W.order[ci];
         int n = C->n;
         const int gbits = C->n_in > R ? C->n_in - R : 0;
@@ -311,8 +323,8 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? (R <= 4 ? kGradMinBlocks : k
             active = false;
             n = 2;
         }
-        const int g = C->graph;  // the same on every lane (padded work list)
-        const bool uni = __all_sync(kFull, g == __shfl_sync(kFull, g, 0));
+        const int g = C->graph;  // the warp's graph on every lane (padded work list)
+        const bool uni = __all_sync(kFull, g == gwarp);
         if (!uni && lane == 0) atomicOr(L.status, 1);
         const int64_t t = active ? slot - W.start[ci] : 0;
         const float wgt = float(C->weight);
@@ -333,18 +345,7 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? (R <= 4 ? kGradMinBlocks : k
             else
                 cw.visit(f);
         };
-        // stage the phase tables of points j0 .. j0+jn-1 of graph g
-        __syncwarp();
-        {
-            const float2 *__restrict__ src = L.lut + (int64_t(g) * L.n_points + j0) * row;
-            for (int e = lane; e < jn * row; e += 32) my_tab[e] = __ldg(src + e);
-            const float2 *__restrict__ msrc = L.mix + (int64_t(g) * L.n_points + j0) * p;
-            for (int e = lane; e < jn * p; e += 32) my_mix[e] = __ldg(msrc + e);
-            const float *__restrict__ ksrc = L.kpow + (int64_t(g) * L.n_points + j0) * p * kKpow;
-            for (int e = lane; e < jn * p * kRegKpow; e += 32)
-                my_kp[e] = __ldg(ksrc + (e / kRegKpow) * kKpow + (e % kRegKpow));
-        }
-        __syncwarp();
+        __syncwarp();  // the point tables staged above are complete
         // output c of point jj: this lane's share
         auto stash = [&](int c, int jj, float v) {
             if (uni) {

@@ -82,6 +82,8 @@ struct RegWork {
     const int32_t *order = nullptr;     // sorted position -> plan index
     const int64_t *start = nullptr;     // [n+1] first slot of each sorted cone
     const int32_t *warp_first = nullptr;  // sorted index of the cone at slot 32*w
+    const int32_t *slot_cone = nullptr;   // sorted index of the cone owning each slot
+    const int32_t *warp_graph = nullptr;  // the graph of each warp's slots
     const uint64_t *shell = nullptr;    // shell table
     int32_t n_cones = 0;
     int64_t slots = 0;                  // slots per point (with padding)

@@ -12,6 +12,8 @@ struct DevWork {
     int32_t *order = nullptr;
     int64_t *prefix = nullptr;
     int32_t *warp_first = nullptr;
+    int32_t *slot_cone = nullptr;   // sorted cone index of every slot
+    int32_t *warp_graph = nullptr;  // graph of every warp's slots
     int64_t slots = 0, warps = 0;
     int32_t n = 0;
 };
@@ -44,7 +46,7 @@ struct qaoa_device_plan {
     int64_t n_big = 0;
     int32_t points_per_task = 0;  // 0: default (see qaoa_tuning_t)
     int32_t blocks_per_sm = 0;
-    int32_t reg_bits_grad = 0;    // adjoint register qubits (4 or 5; 0: 4 at p = 1, else 5)
+    int32_t reg_bits_grad = 0;    // adjoint register qubits (4 or 5; 0: 4)
     int32_t chunk_window = 10;    // largest outer window of a shared-memory chunk pass (6..10)
     bool timing = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;

@@ -142,6 +142,8 @@ extern "C" int qaoa_energy_noalloc(const qaoa_plan *plan, int64_t n_points, cons
         L.work.order = d->reg_e.order;
         L.work.start = d->reg_e.prefix;
         L.work.warp_first = d->reg_e.warp_first;
+        L.work.slot_cone = d->reg_e.slot_cone;
+        L.work.warp_graph = d->reg_e.warp_graph;
         L.work.shell = d->shell;
         L.work.n_cones = d->reg_e.n;
         L.work.slots = d->reg_e.slots;

@@ -415,8 +415,17 @@ class PlanGraph:
         self._h = h
 
     def run(self, params=None, stream=None):
+        """Replays the graph; ``params`` (optional) is copied into its buffer
+        first: a CUDA float64 tensor, or a host float64 tensor of the same
+        shape (pinned, for an asynchronous copy)."""
         if params is not None:
-            self.params.copy_(self.plan._params(params))
+            import torch
+            if isinstance(params, torch.Tensor) and not params.is_cuda:
+                if params.dtype != torch.float64 or params.numel() != self.params.numel():
+                    raise ValueError(f"params must be float64 with {self.params.numel()} elements")
+                self.params.copy_(params.reshape(self.params.shape), non_blocking=True)
+            else:
+                self.params.copy_(self.plan._params(params))
         _check(lib().qaoa_graph_launch(self._h, _stream_handle(stream)))
         return (self.energy, self.grad) if self.grad is not None else self.energy
 
