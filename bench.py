@@ -59,13 +59,15 @@ P_DEPTH, N_POINTS = 1, 256
 PARAM_SEED0 = 1000  # graph k draws its points with seed PARAM_SEED0 + k
 SIDE_SEEDS = (1, 2, 3, 4)
 
-# DRAM bytes per launch of the dominant kernel (the adjoint register kernel on
+# DRAM bytes per launch of the dominant kernel (the depth-1 adjoint kernel on
 # this workload) from a one-pass ncu capture of `bench.py --case reg-mix48`
-# (dram__bytes_read.sum + dram__bytes_write.sum), with the hash of the sources
-# they were taken on; a change to any of them reports null until it is
-# captured again.
-TRAFFIC = {"kernels_sha1": None, "bytes_per_launch": None,
-           "source": "ncu one-pass capture of `python bench.py --case reg-mix48`, summarised in profiles/"}
+# (dram__bytes_read.sum + dram__bytes_write.sum: 12,869,120 + 0), with the
+# hash of the sources they were taken on; a change to any of them reports
+# null until it is captured again.
+TRAFFIC = {"kernels_sha1": "95e3323e6c51b55f830e3371b397c9610655b38d", "bytes_per_launch": 12869120,
+           "source": "ncu one-pass capture (dram__bytes_read.sum + dram__bytes_write.sum) of "
+                     "`python bench.py --case reg-mix48` (default tuning, 6 points per task), "
+                     "summarised in profiles/reg_p1_mix48_p1.md"}
 
 
 def log(*a):
@@ -105,7 +107,7 @@ def config_dict(world, info=None):
 
 # ------------------------------------------------------------------ roofline
 
-def algorithmic_flops(reps, p, grad):
+def algorithmic_flops(reps, p, grad, depth1=False):
     """FP32 FLOPs of the pruned state-vector circuit per point, summed over reps.
 
     Counted for the cheapest formulation the kernels use (FMA = 2 FLOPs), per
@@ -121,12 +123,21 @@ def algorithmic_flops(reps, p, grad):
         the butterfly on both states (8), on the co-state only in layer 1 (4);
         per layer the Im<lam|C|psi> term (5); undoing the phase on both states
         above layer 1 (12).
+    With depth1 (p = 1 plans on the depth-1 kernel, k_1 = 2 for every cone)
+    the adjoint is A (4 + 8 + 3.75): the co-state's signs fold into the next
+    FMAs (0); the two pair terms of a mixed qubit coincide once the co-state
+    is Z_u Z_v psi, so Im<lam|X_q|psi> takes 2 per amplitude per qubit; undoing
+    the butterflies on the co-state (4 per qubit); Im<lam|C|psi> (5) on the
+    three amplitudes of each 4-amplitude block whose cut value differs from
+    the block's first, against which C is shifted.
     """
     A = reps["n_blocks"].astype(np.float64) * np.ldexp(1.0, reps["n_inner"].astype(np.int64))
     k = reps["mix_qubits"][:, :p].astype(np.float64)
     ksum = k.sum(axis=1)
     flops = A * (6 * (p - 1) + 4 * ksum + 4)
-    if grad:
+    if grad and depth1:
+        flops = flops + A * (2 * ksum + 4 * ksum + 3.75)
+    elif grad:
         flops = flops + A * (2 + 12 * (ksum - k[:, 0]) + 8 * k[:, 0] + 5 * p + 12 * (p - 1))
     return float(flops.sum())
 
@@ -156,10 +167,10 @@ def hbm_peak_gbs():
 
 
 def kernels_sha1():
-    """Hash of the register kernel's sources and of the planner and upload code
-    that decide what it reads (the shell block lists, the descriptors)."""
+    """Hash of the dominant kernel's sources (the depth-1 kernel) and of the
+    planner and upload code that decide what it reads (the block records)."""
     h = hashlib.sha1()
-    for f in ("cone_kernel.cuh", "kernels_grad.cu", "device.cuh", "capi.cu", "plan.cpp", "block_orbits.cpp"):
+    for f in ("p1_kernel.cu", "reg_common.cuh", "device.cuh", "capi.cu", "plan.cpp", "block_orbits.cpp"):
         h.update(open(os.path.join(ROOT, "paper_2101_10296_gb300", "csrc", f), "rb").read())
     return h.hexdigest()
 
@@ -603,7 +614,8 @@ def run_ours(args, rank, world, local_rank):
 
     # roofline of the dominant kernel: the adjoint register kernel (every cone of the
     # workload is register-resident at p = 1; the events bracket its launch)
-    flops = algorithmic_flops(reps, p, grad=True) * P
+    depth1 = bool(info["depth1_kernel"])
+    flops = algorithmic_flops(reps, p, grad=True, depth1=depth1) * P
     kern_avg_ms = kern_ms / max(kern_launches, 1)
     achieved = flops / (kern_avg_ms / 1e3) / 1e12
     peak, mhz = fp32_peak_tflops(sm_count)
@@ -641,7 +653,7 @@ def run_ours(args, rank, world, local_rank):
                  "autotune_s": t_tune, "kernel_launches_per_step": launches_per_step},
         "roofline": {
             "bound": "alu",
-            "kernel": "reg_cone_kernel<R=4, u32, adjoint, p=1>",
+            "kernel": "reg_p1_kernel<adjoint>" if depth1 else "reg_cone_kernel<adjoint, p=1>",
             "achieved": achieved,
             "peak": peak,
             "unit": "TFLOP/s",
@@ -809,7 +821,7 @@ def run_suite(args):
         terms = terms.cpu().numpy()
         reps = plan.reps()
         reps["n_blocks"] = plan.shell_blocks()
-        flops = algorithmic_flops(reps, p, grad=True) * P
+        flops = algorithmic_flops(reps, p, grad=True, depth1=bool(plan.info()["depth1_kernel"])) * P
         amps = float((np.ldexp(1.0, reps["n_qubits"].astype(np.int64)) * p).sum()) * P
         # accuracy: per-term against the FP64 oracle on sampled representatives
         # (cones of at most 20 qubits), total energy against the closed form at p = 1
@@ -877,6 +889,7 @@ def run_suite(args):
 PROFILE_CASES = {
     "reg-mix48": "the benchmark workload (48-graph mix, p=1, 256 points): energy+grad",
     "reg-mix48-small": "the 48-graph mix, p=1, 16 points: energy+grad",
+    "reg-mix48-p32": "the 48-graph mix, p=1, 32 points: energy+grad",
     "reg-adjoint-rr3-n2000": "1 random 3-regular graph n=2000 (seed 1), p=2, 8 points: energy+grad",
     "reg-rr3-x4": "4 x rr3 n=2000, p=2, 64 points: energy+grad",
     "split-adjoint-rr3-n24": "1 random 3-regular graph n=24 (seed 1), p=3, 8 points: energy+grad",
@@ -890,10 +903,10 @@ def run_case(name):
     import torch
     from paper_2101_10296_gb300 import inputs as I
     from paper_2101_10296_gb300 import qaoa
-    if name in ("reg-mix48", "reg-mix48-small"):
+    if name in ("reg-mix48", "reg-mix48-small", "reg-mix48-p32"):
         graphs, theta = workload()
-        if name == "reg-mix48-small":
-            theta = np.ascontiguousarray(theta[:, :16])
+        if name != "reg-mix48":
+            theta = np.ascontiguousarray(theta[:, :16 if name == "reg-mix48-small" else 32])
         p, grad, kw = 1, True, {}
     elif name == "reg-rr3-x4":
         graphs, theta = side_workload()

@@ -168,6 +168,12 @@ typedef struct qaoa_plan_info_t {
      * n_big runs on the core-tile schedule) */
     int64_t n_big_general_energy;
     int64_t n_big_general_grad;
+    /* 1 when the register-resident cones run on the depth-1 kernel: p = 1 and
+     * every such cone's inner part is the edge {u, v}, the qubits the only
+     * mixer acts on (Sec. 2.3), so its shell blocks evolve independently and
+     * are processed as one flat list per graph.  Calls that ask for terms_dev
+     * use the general register kernel. */
+    int32_t depth1_kernel;
 } qaoa_plan_info_t;
 
 int qaoa_plan_info(const qaoa_plan *plan, qaoa_plan_info_t *info);

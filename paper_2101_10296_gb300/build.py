@@ -23,9 +23,9 @@ LIB = os.path.join(PKG, "libqaoa.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 HOST_SRC = ["graph.cpp", "orbits.cpp", "plan.cpp", "cone_classes.cpp", "block_orbits.cpp"]
-CUDA_SRC = ["kernels.cu", "kernels_grad.cu", "kernels_grad5.cu", "big.cu", "big_split.cu", "capi.cu", "noalloc.cu"]
+CUDA_SRC = ["kernels.cu", "kernels_grad.cu", "kernels_grad5.cu", "big.cu", "big_split.cu", "capi.cu", "noalloc.cu", "p1_kernel.cu"]
 HEADERS = ["host.hpp", "device.cuh", "big.cuh", "big_common.cuh", "devplan.cuh", "cone_kernel.cuh", "dev_math.cuh",
-           "kernels_grad_impl.cuh"]
+           "kernels_grad_impl.cuh", "reg_common.cuh"]
 
 
 def _nvcc():

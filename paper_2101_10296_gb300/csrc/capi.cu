@@ -26,20 +26,58 @@ int cuda_fail(cudaError_t e, const char *what) {
 }
 
 void free_work(DevWork &w) {
-    cudaFree(w.order);
-    cudaFree(w.prefix);
-    cudaFree(w.warp_first);
     cudaFree(w.slot_cone);
     cudaFree(w.warp_graph);
+    cudaFree(w.rec_hi);
+    cudaFree(w.rec_wk);
+    cudaFree(w.rec_cw);
     w = DevWork{};
+}
+
+// Shell word and multiplicity of block beta of a cone, decoded from the shell
+// table exactly as the kernels' shell_block does (the same float products in
+// the same order).
+uint64_t host_shell_block(const DevCone &C, const std::vector<uint64_t> &tab, uint32_t beta, float &mult) {
+    if (C.n_cls < 0) {
+        if (int64_t(beta) >= C.n_blocks) {
+            mult = 0.f;
+            return 0;
+        }
+        const uint64_t *e = tab.data() + C.cls_off + 2 * size_t(beta);
+        const uint32_t bits = uint32_t(e[1]);
+        std::memcpy(&mult, &bits, sizeof mult);
+        return e[0];
+    }
+    const uint64_t *t = tab.data() + C.cls_off;
+    uint64_t m = 0;
+    float w = 1.f;
+    for (int c = 0; c < C.n_cls; ++c) {
+        const uint32_t sz = uint32_t(t[0]);
+        const uint32_t q = beta / (sz + 1);
+        const uint32_t nc = beta - q * (sz + 1);
+        beta = q;
+        m ^= t[1 + nc];
+        const uint32_t bits = uint32_t(t[2 + sz + nc]);
+        float f;
+        std::memcpy(&f, &bits, sizeof f);
+        w *= f;
+        t += 2 * sz + 3;
+    }
+    mult = w;
+    return m;
 }
 
 // Builds the slot list for R register qubits over the given plan indices:
 // cones sorted by (G_c = 2^max(n_in - R, 0) descending, graph, plan order)
 // and packed back to back, T_c slots each (a multiple of G_c, so every cone
 // starts at a multiple of its own G_c and its lane-qubit groups never
-// straddle a cone boundary); a new graph starts on a fresh warp.
-int build_work(const std::vector<DevCone> &hc, const std::vector<int32_t> &idx, int R, DevWork &w) {
+// straddle a cone boundary); a new graph starts on a fresh warp.  Then the
+// slot records (see RegWork): for slot s of cone c at offset t = s - start_c
+// the thread holds inner qubits R..n_in-1 in the low bits of t and block
+// group t >> max(n_in - R, 0); register bits [2, nr) are inner qubits (nr =
+// min(n_in, R)) and bits [nr, R) pick one of 2^(R - nr) blocks of the group.
+int build_work(const std::vector<DevCone> &hc, const std::vector<uint64_t> &shell_tab,
+               const std::vector<int32_t> &idx, int R, bool wide, DevWork &w) {
     std::vector<int32_t> order(idx);
     auto G = [&](int32_t i) { return int64_t(1) << std::max(hc[i].n_in - R, 0); };
     auto T = [&](int32_t i) {
@@ -61,59 +99,131 @@ int build_work(const std::vector<DevCone> &hc, const std::vector<int32_t> &idx, 
     start[order.size()] = pos;
     const int64_t slots = pos;
     const int64_t warps = slots / 32;
-    std::vector<int32_t> first(size_t(std::max<int64_t>(warps, 1)), 0);
-    std::vector<int32_t> wgraph(first.size(), 0);
-    size_t ci = 0;
-    for (int64_t wi = 0; wi < warps; ++wi) {
-        while (ci + 1 < order.size() && start[ci + 1] <= wi * 32) ++ci;
-        first[wi] = int32_t(ci);
-        wgraph[wi] = order.empty() ? 0 : hc[order[ci]].graph;
-    }
-    // the cone owning each slot (the last cone starting at or before it), so that
-    // a kernel finds it with one load instead of a walk along the start list
-    std::vector<int32_t> scone(size_t(std::max<int64_t>(slots, 1)), 0);
-    ci = 0;
-    for (int64_t sl = 0; sl < slots; ++sl) {
-        while (ci + 1 < order.size() && start[ci + 1] <= sl) ++ci;
-        scone[size_t(sl)] = int32_t(ci);
-    }
     w.slots = slots;
     w.warps = warps;
     w.n = int32_t(order.size());
     if (order.empty()) return QAOA_OK;
+    const int S = 1 << (R - 2);
+    std::vector<int32_t> wgraph(size_t(warps), 0);
+    std::vector<int32_t> scone(size_t(slots), 0);
+    std::vector<uint64_t> hi64(size_t(S) * size_t(slots), 0);
+    std::vector<float> wk(size_t(S) * size_t(slots), 0.f);
+    size_t ci = 0;
+    for (int64_t sl = 0; sl < slots; ++sl) {
+        // the cone owning the slot: the last one starting at or before it
+        while (ci + 1 < order.size() && start[ci + 1] <= sl) ++ci;
+        const DevCone &C = hc[size_t(order[ci])];
+        const bool active = sl < start[ci] + T(order[ci]);
+        scone[size_t(sl)] = order[ci] | (active ? 0 : int32_t(0x80000000u));
+        if (sl % 32 == 0) wgraph[size_t(sl / 32)] = C.graph;
+        const int64_t t = active ? sl - start[ci] : 0;  // padding: the cone's first slot, weight 0
+        const int n_in = C.n_in;
+        const int nr = std::min(n_in, R);
+        const int gb = std::max(n_in - R, 0);
+        const int sb = R - nr;
+        const int inner_bits = nr - 2;
+        uint64_t base = 0;
+        for (int q = R; q < n_in; ++q)
+            if ((t >> (q - R)) & 1) base ^= C.col[q];
+        const uint32_t group = uint32_t(t >> gb);
+        uint64_t shell = 0;
+        float mult = 0.f;
+        for (int k = 0; k < S; ++k) {
+            if ((k & ((1 << inner_bits) - 1)) == 0) {
+                const uint32_t beta = (group << sb) + uint32_t(k >> inner_bits);
+                shell = host_shell_block(C, shell_tab, beta, mult);
+                if (int64_t(beta) >= C.n_blocks) mult = 0.f;
+            }
+            uint64_t v = base ^ shell;
+            for (int b = 0; b < R - 2; ++b)
+                if (((k >> b) & 1) && 2 + b < nr) v ^= C.col[2 + b];
+            hi64[size_t(k) * size_t(slots) + size_t(sl)] = v;
+            wk[size_t(k) * size_t(slots) + size_t(sl)] = active ? mult : 0.f;
+        }
+    }
     cudaError_t e;
-    if ((e = cudaMalloc(&w.order, order.size() * sizeof(int32_t))) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
-    if ((e = cudaMalloc(&w.prefix, start.size() * sizeof(int64_t))) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
-    if ((e = cudaMalloc(&w.warp_first, first.size() * sizeof(int32_t))) != cudaSuccess)
+    const size_t n_rec = size_t(S) * size_t(slots);
+    const size_t word = wide ? sizeof(uint64_t) : sizeof(uint32_t);
+    if ((e = cudaMalloc(&w.slot_cone, scone.size() * sizeof(int32_t))) != cudaSuccess ||
+        (e = cudaMalloc(&w.warp_graph, wgraph.size() * sizeof(int32_t))) != cudaSuccess ||
+        (e = cudaMalloc(&w.rec_hi, n_rec * word)) != cudaSuccess ||
+        (e = cudaMalloc(&w.rec_wk, n_rec * sizeof(float))) != cudaSuccess)
         return cuda_fail(e, "cudaMalloc");
-    if ((e = cudaMalloc(&w.slot_cone, scone.size() * sizeof(int32_t))) != cudaSuccess)
-        return cuda_fail(e, "cudaMalloc");
-    if ((e = cudaMalloc(&w.warp_graph, wgraph.size() * sizeof(int32_t))) != cudaSuccess)
-        return cuda_fail(e, "cudaMalloc");
-    cudaMemcpy(w.slot_cone, scone.data(), scone.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
-    cudaMemcpy(w.warp_graph, wgraph.data(), wgraph.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
-    cudaMemcpy(w.order, order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
-    cudaMemcpy(w.prefix, start.data(), start.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
-    if ((e = cudaMemcpy(w.warp_first, first.data(), first.size() * sizeof(int32_t), cudaMemcpyHostToDevice)) !=
-        cudaSuccess)
-        return cuda_fail(e, "cudaMemcpy");
+    if (wide) {
+        e = cudaMemcpy(w.rec_hi, hi64.data(), n_rec * word, cudaMemcpyHostToDevice);
+    } else {
+        // at most 32 cut bits in every cone: the high halves are zero
+        std::vector<uint32_t> hi32(n_rec);
+        for (size_t r = 0; r < n_rec; ++r) hi32[r] = uint32_t(hi64[r]);
+        e = cudaMemcpy(w.rec_hi, hi32.data(), n_rec * word, cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(w.rec_wk, wk.data(), n_rec * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(w.slot_cone, scone.data(), scone.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(w.warp_graph, wgraph.data(), wgraph.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy");
     return QAOA_OK;
 }
 
-RegWork as_reg(const qaoa_device_plan *d, const DevWork &w) {
-    RegWork r;
-    r.cones = d->cones;
-    r.shell = d->shell;
-    r.order = w.order;
-    r.start = w.prefix;
-    r.warp_first = w.warp_first;
-    r.slot_cone = w.slot_cone;
-    r.warp_graph = w.warp_graph;
-    r.n_cones = w.n;
-    r.slots = w.slots;
-    r.warps = w.warps;
-    return r;
+// The depth-1 kernel's list (every cone with inner part {u, v}, mixed by the
+// only layer): per graph, the shell blocks of its cones back to back, each
+// as (c_0 | c_1 << 8 | c_2 << 16 | c_3 << 24, W) with c_a the cut value of
+// amplitude a = z_u + 2 z_v of the block and W = multiplicity x orbit size x
+// 2^-n rounded once to float; slot s of a graph takes its blocks 16 s ..
+// 16 s + 15, and every graph starts on a fresh warp (padding: zero weight).
+int build_p1_work(const std::vector<DevCone> &hc, const std::vector<uint64_t> &shell_tab,
+                  const std::vector<int32_t> &idx, DevWork &w) {
+    std::vector<int32_t> order(idx);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return hc[a].graph < hc[b].graph; });
+    std::vector<uint2> blocks;  // flat, graph by graph, each graph padded to 32 slots
+    std::vector<int32_t> wgraph;
+    const size_t per_warp = size_t(kP1Blocks) * 32;
+    for (size_t i = 0; i < order.size();) {
+        const int32_t g = hc[size_t(order[i])].graph;
+        const size_t first = blocks.size();
+        for (; i < order.size() && hc[size_t(order[i])].graph == g; ++i) {
+            const DevCone &C = hc[size_t(order[i])];
+            const uint64_t lo[4] = {0, C.col[0], C.col[1], C.col[0] ^ C.col[1]};
+            const double scale = C.weight * std::ldexp(1.0, -C.n);
+            for (int64_t beta = 0; beta < C.n_blocks; ++beta) {
+                float mult = 0.f;
+                const uint64_t word = host_shell_block(C, shell_tab, uint32_t(beta), mult);
+                uint32_t cnt = 0;
+                for (int a = 0; a < 4; ++a) cnt |= uint32_t(__builtin_popcountll(lo[a] ^ word)) << (8 * a);
+                const float wf = float(double(mult) * scale);
+                uint32_t bits;
+                std::memcpy(&bits, &wf, sizeof bits);
+                blocks.push_back(make_uint2(cnt, bits));
+            }
+        }
+        const size_t n = blocks.size() - first;
+        const size_t padded = (n + per_warp - 1) / per_warp * per_warp;
+        blocks.resize(first + padded, make_uint2(0u, 0u));
+        wgraph.insert(wgraph.end(), padded / per_warp, g);
+    }
+    const int64_t slots = int64_t(blocks.size() / kP1Blocks);
+    w.slots = slots;
+    w.warps = slots / 32;
+    w.n = int32_t(order.size());
+    if (slots == 0) return QAOA_OK;
+    // records [k][slot]: block k of slot s is flat block 16 s + k
+    std::vector<uint2> rec(blocks.size());
+    for (int64_t sl = 0; sl < slots; ++sl)
+        for (int k = 0; k < kP1Blocks; ++k)
+            rec[size_t(k) * size_t(slots) + size_t(sl)] = blocks[size_t(sl) * kP1Blocks + size_t(k)];
+    cudaError_t e;
+    if ((e = cudaMalloc(&w.warp_graph, wgraph.size() * sizeof(int32_t))) != cudaSuccess ||
+        (e = cudaMalloc(&w.rec_cw, rec.size() * sizeof(uint2))) != cudaSuccess)
+        return cuda_fail(e, "cudaMalloc");
+    e = cudaMemcpy(w.rec_cw, rec.data(), rec.size() * sizeof(uint2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(w.warp_graph, wgraph.data(), wgraph.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy");
+    return QAOA_OK;
 }
+
+RegWork as_reg(const qaoa_device_plan *d, const DevWork &w) { return reg_work(d, w); }
 
 int check_device(const qaoa_plan *plan) {
     int dev = -1;
@@ -265,7 +375,48 @@ int run(const qaoa_plan *plan, int64_t n_points, const double *params, double *e
         cudaEventCreate(&ev1);
         cudaEventRecord(ev0, s);
     }
-    if (e == cudaSuccess) {
+    // depth 1 (no per-cone terms asked for): the depth-1 kernel over flat block lists
+    const bool use_p1 = p == 1 && d->reg_p1.warps > 0 && terms == nullptr;
+    if (e == cudaSuccess && use_p1) {
+        RegLaunch L;
+        L.n_points = n_points;
+        L.p = 1;
+        L.cmax1 = d->cmax1;
+        L.lut = lut;
+        L.mix = mix;
+        L.kpow = kpow;
+        L.energy = energy;
+        L.grad = grad;
+        L.terms = nullptr;
+        L.status = d->status;
+        L.work = as_reg(d, d->reg_p1);
+        // points per warp task: as many phase tables as leave room for the
+        // resident blocks the kernel is sized for (a tuned value is held to
+        // the kernel's shared-memory limit), halved while the tasks would not
+        // give every SM 16 warps
+        {
+            const bool g = grad != nullptr;
+            const int64_t row = int64_t(d->cmax1 + 1) * int64_t(sizeof(float2));
+            const int64_t fixed = int64_t(reg_p1_smem_bytes(0, d->cmax1, g)) / (kRegBlock / 32);
+            const int blocks = g ? kP1GradMinBlocks : kP1EnergyMinBlocks;
+            const int64_t fit = (int64_t(227) * 1024 / (blocks * (kRegBlock / 32)) - fixed) / row;
+            const int64_t cap = (int64_t(kRegMaxSmem) / (kRegBlock / 32) - fixed) / row;
+            int64_t jpt = d->points_per_task;
+            if (jpt <= 0) {
+                jpt = std::min<int64_t>(32, std::max<int64_t>(1, fit));
+                while (jpt > 1 && L.work.warps * ((n_points + jpt - 1) / jpt) < int64_t(sm_count()) * 16)
+                    jpt = (jpt + 1) / 2;
+            }
+            jpt = std::max<int64_t>(1, std::min<int64_t>(jpt, cap));
+            L.jpt = int32_t(std::min<int64_t>(jpt, n_points));
+        }
+        const size_t smem = reg_p1_smem_bytes(L.jpt, d->cmax1, grad != nullptr);
+        const int64_t tasks = L.work.warps * ((n_points + L.jpt - 1) / L.jpt);
+        int64_t grid = std::min<int64_t>(tuned_grid(d, reg_p1_grid(grad != nullptr, smem)), (tasks + 3) / 4);
+        e = launch_reg_p1(L, grad != nullptr, int(std::max<int64_t>(grid, 1)), s);
+        dm->all_launches += 1;
+        if (e == cudaSuccess && !d->big.empty()) e = run_big(d, plan, n_points, params, lut, mix, kpow, energy, grad, terms, s);
+    } else if (e == cudaSuccess) {
         RegLaunch L;
         L.n_points = n_points;
         L.p = p;
@@ -337,6 +488,7 @@ extern "C" void qaoa_device_release(qaoa_plan *plan) {
     free_work(d->reg_e);
     free_work(d->reg_g[0]);
     free_work(d->reg_g[1]);
+    free_work(d->reg_p1);
     for (auto &bs : d->big) {
         cudaFree(bs.d_cones);
         cudaFree(bs.d_ystart);
@@ -495,9 +647,15 @@ extern "C" int qaoa_plan_upload(qaoa_plan *plan) {
         else
             cudaMemcpy(d->shell, shell_tab.data(), shell_tab.size() * sizeof(uint64_t), cudaMemcpyHostToDevice);
     }
-    if (rc == QAOA_OK) rc = build_work(hc, reg_idx, kRegBitsEnergy, d->reg_e);
-    if (rc == QAOA_OK) rc = build_work(hc, reg_idx, 4, d->reg_g[0]);
-    if (rc == QAOA_OK) rc = build_work(hc, reg_idx, 5, d->reg_g[1]);
+    const bool wide = cmax > 32;  // the kernels' cut-word width (as at launch)
+    if (rc == QAOA_OK) rc = build_work(hc, shell_tab, reg_idx, kRegBitsEnergy, wide, d->reg_e);
+    if (rc == QAOA_OK) rc = build_work(hc, shell_tab, reg_idx, 4, wide, d->reg_g[0]);
+    if (rc == QAOA_OK) rc = build_work(hc, shell_tab, reg_idx, 5, wide, d->reg_g[1]);
+    // depth 1 with every register cone mixing qubits 0 and 1 only (its inner
+    // part): the depth-1 kernel's list
+    bool p1 = plan->p == 1 && !reg_idx.empty();
+    for (int32_t i : reg_idx) p1 = p1 && hc[size_t(i)].n_in == 2 && hc[size_t(i)].k[0] == 2;
+    if (rc == QAOA_OK && p1) rc = build_p1_work(hc, shell_tab, reg_idx, d->reg_p1);
     if (rc == QAOA_OK) {
         std::vector<double> half(size_t(plan->n_graphs));
         for (int32_t g = 0; g < plan->n_graphs; ++g) half[g] = 0.5 * double(plan->weight_sum[g]);
@@ -537,7 +695,12 @@ extern "C" int qaoa_plan_info(const qaoa_plan *plan, qaoa_plan_info_t *info) {
     info->n_reps = int64_t(plan->cones.size());
     info->orbits_complete = 1;
     for (const auto &o : plan->orbits) info->orbits_complete &= o.complete ? 1 : 0;
+    int64_t n_reg = 0, n_reg_p1 = 0;
     for (const Cone &c : plan->cones) {
+        if (c.n_in <= kRegMaxInner) {
+            ++n_reg;
+            if (c.n_in == 2 && c.k[0] == 2) ++n_reg_p1;
+        }
         info->max_qubits = std::max(info->max_qubits, c.n);
         info->max_inner = std::max(info->max_inner, c.n_in);
         info->max_edges = std::max(info->max_edges, int32_t(c.ea.size()));
@@ -549,6 +712,7 @@ extern "C" int qaoa_plan_info(const qaoa_plan *plan, qaoa_plan_info_t *info) {
             if (general || !split_ok(c.n_in, plan->p, c.k, true)) info->n_big_general_grad++;
         }
     }
+    info->depth1_kernel = plan->p == 1 && n_reg > 0 && n_reg_p1 == n_reg ? 1 : 0;
     info->on_device = plan->dev ? 1 : 0;
     info->t_orbits_s = plan->t_orbits;
     info->t_cones_s = plan->t_cones;

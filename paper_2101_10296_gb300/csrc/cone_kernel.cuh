@@ -35,8 +35,7 @@
 // across warps, cones and orbits in FP64 (atomicAdd).
 #pragma once
 
-#include "dev_math.cuh"
-#include "device.cuh"
+#include "reg_common.cuh"
 
 namespace qaoa {
 namespace {
@@ -81,45 +80,20 @@ struct CutWords {
             hi[k] = v;
         }
     }
-    // Register index i of thread t: bits [0, nr) are inner qubits (nr =
-    // min(n_in, R)), bits [nr, R) pick one of S = 2^(R - nr) blocks; thread t
-    // holds inner qubits R..n_in-1 in its low bits and the block group above.
-    // hi[k] gets the inner part, the block's shell word, and wk[k] the block's
-    // multiplicity (0 for block numbers past the cone's n_blocks).
-    __device__ __forceinline__ void init_blocks(const DevCone *__restrict__ C, const uint64_t *__restrict__ tab,
-                                                int64_t t, float (&wk)[1 << (R - 2)]) {
-        const int n_in = C->n_in;
-        const int nr = n_in < R ? n_in : R;
-        const int gb = n_in > R ? n_in - R : 0;
+    // From the slot records (see RegWork): lo[] from the columns of qubits 0
+    // and 1, hi[k] and the multiplicities wk[k] from the slot's record.
+    __device__ __forceinline__ void load(const DevCone *__restrict__ C, const RegWork &W, int64_t slot,
+                                         float (&wk)[1 << (R - 2)]) {
         const MT c0 = MT(C->col[0]), c1 = MT(C->col[1]);
         lo[0] = 0;
         lo[1] = c0;
         lo[2] = c1;
         lo[3] = c0 ^ c1;
-        MT base = 0;
-        for (int q = R; q < n_in; ++q)
-            if ((t >> (q - R)) & 1) base ^= MT(C->col[q]);
-        const uint32_t group = uint32_t(t >> gb);
-        const int sb = R - nr;
-        MT cm[R - 2];
-#pragma unroll
-        for (int b = 0; b < R - 2; ++b) cm[b] = (2 + b < nr) ? MT(C->col[2 + b]) : MT(0);
-        const int inner_bits = nr - 2;  // register bits 2..nr-1 are inner
-        MT shell = 0;
-        float mult = 0.f;
+        const MT *__restrict__ rh = static_cast<const MT *>(W.rec_hi);
 #pragma unroll
         for (int k = 0; k < (1 << (R - 2)); ++k) {
-            if ((k & ((1 << inner_bits) - 1)) == 0) {
-                const uint32_t beta = (group << sb) + uint32_t(k >> inner_bits);
-                shell = MT(shell_block(C, tab, beta, mult));
-                if (beta >= uint64_t(C->n_blocks)) mult = 0.f;
-            }
-            MT v = base ^ shell;
-#pragma unroll
-            for (int b = 0; b < R - 2; ++b)
-                if ((k >> b) & 1) v ^= cm[b];
-            hi[k] = v;
-            wk[k] = mult;
+            hi[k] = __ldg(rh + k * W.slots + slot);
+            wk[k] = __ldg(W.rec_wk + k * W.slots + slot);
         }
     }
     __device__ __forceinline__ void flip(MT f) {
@@ -149,18 +123,6 @@ template <int R, class F>
 __device__ __forceinline__ void visit_packed(const uint32_t (&pk)[1 << (R - 2)], F &&f) {
 #pragma unroll
     for (int i = 0; i < (1 << R); ++i) f(i, int((pk[i >> 2] >> (8 * (i & 3))) & 0xffu));
-}
-
-// u - i tau v
-__device__ __forceinline__ float2 bfly(float2 u, float2 v, float tau) {
-    return make_float2(fmaf(tau, v.y, u.x), fmaf(-tau, v.x, u.y));
-}
-
-// d += Im(conj(a) b) as two FMAs (written out: the compiler may not contract
-// a separate product and sum)
-__device__ __forceinline__ void acc_imconj(float &d, float2 a, float2 b) {
-    d = fmaf(a.x, b.y, d);
-    d = fmaf(-a.y, b.x, d);
 }
 
 // (I - i tau X_q) on register qubits q < KQ (compile-time count)
@@ -239,20 +201,6 @@ __device__ __forceinline__ float zz_partial(const float2 (&x)[1 << R], const flo
     return tot;
 }
 
-// Sum of v over the lanes of each run of equal keys (runs are contiguous);
-// the result is valid in the run's first lane, which returns true.
-__device__ __forceinline__ bool seg_sum(float &v, int key) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const float ov = __shfl_down_sync(kFull, v, o);
-        const int ok = __shfl_down_sync(kFull, key, o);
-        if (lane + o < 32 && ok == key) v += ov;
-    }
-    const int prev = __shfl_up_sync(kFull, key, 1);
-    return lane == 0 || prev != key;
-}
-
 // Outputs reduced per unrolled copy of the reduction loop (1 keeps one copy of
 // its code: the adjoint body is large enough for instruction fetch to stall).
 #ifndef QAOA_FLUSH_UNROLL
@@ -285,8 +233,10 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? (R <= 4 ? kGradMinBlocks : k
     float2 *my_mix = s_tab + (kRegBlock / 32) * (L.jpt * row) + warp * (L.jpt * p);
     float *my_kp = reinterpret_cast<float *>(s_tab + (kRegBlock / 32) * (L.jpt * (row + p))) +
                    warp * (L.jpt * p * kRegKpow);
-    float *red = reinterpret_cast<float *>(s_tab + (kRegBlock / 32) * (L.jpt * (row + p))) +
-                 (kRegBlock / 32) * (L.jpt * p * kRegKpow) + warp * (NOUT * G * 32);
+    float *red_all = reinterpret_cast<float *>(s_tab + (kRegBlock / 32) * (L.jpt * (row + p))) +
+                     (kRegBlock / 32) * (L.jpt * p * kRegKpow);
+    float *red = red_all + warp * (NOUT * G * 32);
+    uint32_t *my_cone = reinterpret_cast<uint32_t *>(red_all + (kRegBlock / 32) * (NOUT * G * 32)) + warp * (kRegLaneWords * 32);
     const int64_t gw = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
     const int64_t nblk = (L.n_points + L.jpt - 1) / L.jpt;
@@ -303,21 +253,26 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? (R <= 4 ? kGradMinBlocks : k
         const int gwarp = __ldg(W.warp_graph + w);
         __syncwarp();  // the previous task's reads of the tables are done
         {
+            // asynchronous copies (no register round trip): all of them are in
+            // flight while the lanes load their slots' records and cones
             const float2 *__restrict__ src = L.lut + (int64_t(gwarp) * L.n_points + j0) * row;
-            for (int e = lane; e < jn * row; e += 32) my_tab[e] = __ldg(src + e);
+            for (int e = lane; e < jn * row; e += 32) cp_async8(my_tab + e, src + e);
             const float2 *__restrict__ msrc = L.mix + (int64_t(gwarp) * L.n_points + j0) * p;
-            for (int e = lane; e < jn * p; e += 32) my_mix[e] = __ldg(msrc + e);
+            for (int e = lane; e < jn * p; e += 32) cp_async8(my_mix + e, msrc + e);
             const float *__restrict__ ksrc = L.kpow + (int64_t(gwarp) * L.n_points + j0) * p * kKpow;
             for (int e = lane; e < jn * p * kRegKpow; e += 32)
-                my_kp[e] = __ldg(ksrc + (e / kRegKpow) * kKpow + (e % kRegKpow));
+                cp_async4(my_kp + e, ksrc + (e / kRegKpow) * kKpow + (e % kRegKpow));
         }
-        const int ci = slot < W.slots ? __ldg(W.slot_cone + slot) : __ldg(W.warp_first + w);
-        const DevCone *__restrict__ C = W.cones + W.order[ci];
+        // the slot's cone (every lane of a warp below W.warps has a slot) and
+        // whether the slot carries work (padding slots have weight 0)
+        const int32_t sc = __ldg(W.slot_cone + (slot < W.slots ? slot : W.slots - 1));
+        const int ci = sc & 0x7fffffff;
+        bool active = sc >= 0 && slot < W.slots;
+        const DevCone *__restrict__ C = W.cones + ci;
+        CutWords<R, MT> cw;
+        float wk[NA / 4];
+        cw.load(C, W, slot < W.slots ? slot : W.slots - 1, wk);
         int n = C->n;
-        const int gbits = C->n_in > R ? C->n_in - R : 0;
-        const int sbits = C->n_in < R ? R - C->n_in : 0;
-        const int64_t Tc = ((C->n_blocks + (int64_t(1) << sbits) - 1) >> sbits) << gbits;
-        bool active = slot < W.slots && slot < W.start[ci] + Tc;
         if (n < 2 || n > QAOA_MAX_CONE_QUBITS || C->n_in < 2 || C->n_in > R + kLaneBits) {
             if (active) atomicOr(L.status, 1);
             active = false;
@@ -326,11 +281,24 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? (R <= 4 ? kGradMinBlocks : k
         const int g = C->graph;  // the warp's graph on every lane (padded work list)
         const bool uni = __all_sync(kFull, g == gwarp);
         if (!uni && lane == 0) atomicOr(L.status, 1);
-        const int64_t t = active ? slot - W.start[ci] : 0;
         const float wgt = float(C->weight);
-        CutWords<R, MT> cw;
-        float wk[NA / 4];
-        cw.init_blocks(C, W.shell, t, wk);
+        // The cone fields the point loop reads go to the lane's slots in shared
+        // memory once per task: a warp's lanes read up to 32 different cone
+        // structs, which do not stay in L1 from one point to the next.  Word 0
+        // (1) holds k of layers 0-3 (4-7), one byte each; word 2 holds c0 =
+        // m/2: Im<lambda|psi> = <psi_end|O|psi_end> is real at every point of
+        // the sweep (and within every shell block), so C may be replaced by
+        // C - c0 in d/d gamma, which removes the mean cut value and with it most
+        // of the cancellation in the FP32 sums.
+        {
+            uint32_t kw[2] = {0u, 0u};
+            for (int l = 0; l < p; ++l)
+                kw[l >> 2] |= min(unsigned(C->k[l]), unsigned(kRegKpow - 1)) << (8 * (l & 3));
+            my_cone[lane] = kw[0];
+            my_cone[32 + lane] = kw[1];
+            my_cone[64 + lane] = __float_as_uint(0.5f * float(C->m));
+        }
+        auto k_of = [&](int l) -> int { return int((my_cone[(l >> 2) * 32 + lane] >> (8 * (l & 3))) & 0xffu); };
         if (!active) {
 #pragma unroll
             for (int k = 0; k < NA / 4; ++k) wk[k] = 0.f;
@@ -345,7 +313,8 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? (R <= 4 ? kGradMinBlocks : k
             else
                 cw.visit(f);
         };
-        __syncwarp();  // the point tables staged above are complete
+        cp_async_wait_all();
+        __syncwarp();  // the point tables staged above are complete and visible to the warp
         // output c of point jj: this lane's share
         auto stash = [&](int c, int jj, float v) {
             if (uni) {
@@ -355,34 +324,12 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? (R <= 4 ? kGradMinBlocks : k
                 atomicAdd(c == 0 ? L.energy + gjj : L.grad + gjj * 2 * p + (c - 1), f2d(v));
             }
         };
-        // Warp sums of the group of points ending at jj: lane = (part, point);
-        // each lane adds G lanes' shares of its point (compensated), the parts
-        // meet by shuffles, and lanes of part 0 issue the FP64 atomics (hi and
-        // lo each; no FP64 arithmetic).
+        // warp sums of the group of points ending at jj (see reg_flush)
         auto flush = [&](int jj) {
             __syncwarp();
-            if (uni) {
-                const int gn = (jj & (G - 1)) + 1, jf = jj + 1 - gn;
-                const int pt = lane & (G - 1), part = lane / G;
-#pragma unroll(kFlushUnroll)
-                for (int c = 0; c < NOUT; ++c) {
-                    const float *src = red + (c * G + pt) * 32;
-                    Dfl acc{0.f, 0.f};
-                    for (int k = 0; k < G; ++k) dfl_add(acc, src[(part * G + k + jf + pt) & 31]);
-                    for (int o = G; o < 32; o <<= 1) {
-                        Dfl b;
-                        b.hi = __shfl_xor_sync(kFull, acc.hi, o);
-                        b.lo = __shfl_xor_sync(kFull, acc.lo, o);
-                        dfl_add(acc, b);
-                    }
-                    if (part == 0 && pt < gn) {
-                        const int64_t gjj = int64_t(g) * L.n_points + j0 + jf + pt;
-                        double *dst = c == 0 ? L.energy + gjj : L.grad + gjj * 2 * p + (c - 1);
-                        atomicAdd(dst, f2d(acc.hi));
-                        if (acc.lo != 0.f) atomicAdd(dst, f2d(acc.lo));
-                    }
-                }
-            }
+            if (uni)
+                reg_flush<kFlushUnroll>(red, NOUT, G, jj, lane, int64_t(g) * L.n_points + j0, 2 * p, L.energy,
+                                        L.grad);
             __syncwarp();
         };
         for (int jj = 0; jj < jn; ++jj) {
@@ -403,7 +350,7 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? (R <= 4 ? kGradMinBlocks : k
                     visit([&](int i, int c) { x[i] = cmul(x[i], lt[c]); });
                 }
                 const float2 mx = mix[l];
-                const int k = C->k[l];
+                const int k = k_of(l);
                 mix_reg<R>(x, k, mx.x);
                 mix_lane<R>(x, k, mx.x);
                 sig *= kp[l * kRegKpow + k];
@@ -429,16 +376,12 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? (R <= 4 ? kGradMinBlocks : k
                 for (int i = 0; i < NA; ++i) r[i] = ((i ^ (i >> 1)) & 1) ? make_float2(-x[i].x, -x[i].y) : x[i];
                 const float gw2 = active ? -wgt : 0.f;  // 2 x (-1/2) x orbit weight
                 const float sig_end = sig;
-                // Im<lambda|psi> = <psi_end|O|psi_end> is real at every point of
-                // the sweep (and within every shell block), so C may be replaced
-                // by C - c0 in d/d gamma: c0 = m/2 removes the mean cut value and
-                // with it most of the cancellation in the FP32 sums.
-                const float c0 = 0.5f * float(C->m);
+                const float c0 = __uint_as_float(my_cone[64 + lane]);
 #pragma unroll(PC > 0 ? PC : 1)
                 for (int l = p - 1; l >= 0; --l) {
                     const float2 mx = mix[l];
                     const float tau = mx.x;
-                    const int k = C->k[l];
+                    const int k = k_of(l);
                     const int kr = k < R ? k : R;
                     const float *kpl = kp + l * kRegKpow;
                     // d/d beta_l = 2 sigma Im <r| sum_q X_q |s>, register qubits

@@ -72,22 +72,30 @@ __device__ __forceinline__ uint64_t shell_block(const DevCone *__restrict__ C, c
 // amplitudes takes G = 2^max(n_in - R, 0) threads (R register qubits per
 // thread); when n_in < R a thread holds S = 2^(R - n_in) blocks.  A (cone,
 // point) needs T_c = ceil(B / S) * G threads for its B shell blocks.  Cones
-// are sorted by (G descending, graph) and each cone's slots start at
-// start[i]; a graph change is padded to the next multiple of 32 slots, so
-// every cone's first slot is aligned to min(G, 32) lanes and no warp spans
-// two graphs.  A warp task covers 32 consecutive slots for
-// `jpt` consecutive parameter points of that graph.
+// are sorted by (G descending, graph) and packed back to back, T_c slots
+// each; a graph change is padded to the next multiple of 32 slots, so every
+// cone's first slot is aligned to min(G, 32) lanes and no warp spans two
+// graphs.  A warp task covers 32 consecutive slots for `jpt` consecutive
+// parameter points of that graph.
+//
+// Slot records: everything a thread derives from its slot before the first
+// point does not depend on the parameters, so it is computed once at upload.
+// For register index i = 4k + r of slot s's thread (r = bits 0-1: qubits u,
+// v), rec_hi[k * slots + s] is the part of the cut word M(z_i) that does not
+// involve qubits 0 and 1 -- the thread's inner qubits, its shell block's word
+// and register bits 2.. -- and rec_wk[k * slots + s] the multiplicity of the
+// block index i belongs to (0 past the cone's blocks and in padding slots).
+// Words are uint32 when every cone has at most 32 cut bits, else uint64.
 struct RegWork {
-    const DevCone *cones = nullptr;     // plan order
-    const int32_t *order = nullptr;     // sorted position -> plan index
-    const int64_t *start = nullptr;     // [n+1] first slot of each sorted cone
-    const int32_t *warp_first = nullptr;  // sorted index of the cone at slot 32*w
-    const int32_t *slot_cone = nullptr;   // sorted index of the cone owning each slot
+    const DevCone *cones = nullptr;       // plan order
+    const int32_t *slot_cone = nullptr;   // plan index of each slot's cone; bit 31: padding slot
     const int32_t *warp_graph = nullptr;  // the graph of each warp's slots
-    const uint64_t *shell = nullptr;    // shell table
+    const void *rec_hi = nullptr;         // slot records (above)
+    const float *rec_wk = nullptr;
+    const uint2 *rec_cw = nullptr;        // depth-1 work lists: per block the four cut values and the multiplicity
     int32_t n_cones = 0;
-    int64_t slots = 0;                  // slots per point (with padding)
-    int64_t warps = 0;                  // warps per point
+    int64_t slots = 0;                    // slots per point (with padding; a multiple of 32)
+    int64_t warps = 0;                    // warps per point
 };
 
 // Per-point mixer data.  exp(-i beta X) = kappa (I - i tau X) with
@@ -181,13 +189,38 @@ __host__ __device__ constexpr int reg_group(int p, bool grad) {
 }
 // kappa powers a register kernel reads: kappa^(2k) for k <= its largest inner part
 constexpr int kRegKpow = 10;
+// 32-bit words of per-lane cone fields a register kernel keeps in shared
+// memory (the layers' k, one byte each, and the adjoint's cut-value offset)
+constexpr int kRegLaneWords = 3;
+// Depth-1 kernel (p1_kernel.cu): shell blocks per thread, and the resident
+// blocks per SM its register allocation is sized for.  Its work lists hold
+// per graph the shell blocks of all the graph's cones back to back, block k
+// of slot s as rec_cw[k * slots + s] = (c_0 | c_1 << 8 | c_2 << 16 | c_3 <<
+// 24, bits of W), c_a the cut value of amplitude a = z_u + 2 z_v and W the
+// block's multiplicity x orbit size x 2^-n; warp_graph as for the other lists.
+constexpr int kP1Blocks = 16;
+constexpr int kP1GradMinBlocks = 6;
+constexpr int kP1EnergyMinBlocks = 8;
+// Dynamic shared memory of a depth-1 block: per warp jpt phase tables, jpt
+// (tau, kappa^4) pairs, the records of its 32 slots and the reduction buffer.
+inline size_t reg_p1_smem_bytes(int jpt, int cmax1, bool grad) {
+    return size_t(kRegBlock / 32) *
+           (size_t(jpt) * (cmax1 + 1) * sizeof(float2) + size_t(kP1Blocks) * 32 * sizeof(uint2) +
+            size_t(reg_outputs(1, grad)) * reg_group(1, grad) * 32 * sizeof(float));
+}
+int reg_p1_grid(bool grad, size_t smem);
+cudaError_t reg_p1_prepare();
+cudaError_t launch_reg_p1(const RegLaunch &a, bool grad, int grid, cudaStream_t s);
+
 // Dynamic shared memory of a register-kernel block: per warp and point the
 // phase tables (p x cmax1 float2), the mixer data (p float2) and the kappa
-// powers (p x kRegKpow float) of jpt points, and the reduction buffer.
+// powers (p x kRegKpow float) of jpt points, the reduction buffer, and the
+// lanes' cone fields.
 inline size_t reg_smem_bytes(int jpt, int p, int cmax1, bool grad) {
     return size_t(kRegBlock / 32) *
            (size_t(jpt) * p * (cmax1 + 1) * sizeof(float2) +
-            (size_t(jpt) * p * kRegKpow + size_t(reg_outputs(p, grad)) * reg_group(p, grad) * 32) * sizeof(float));
+            (size_t(jpt) * p * kRegKpow + size_t(reg_outputs(p, grad)) * reg_group(p, grad) * 32 +
+             size_t(kRegLaneWords) * 32) * sizeof(float));
 }
 
 }  // namespace qaoa

@@ -9,11 +9,11 @@
 #include "device.cuh"
 
 struct DevWork {
-    int32_t *order = nullptr;
-    int64_t *prefix = nullptr;
-    int32_t *warp_first = nullptr;
-    int32_t *slot_cone = nullptr;   // sorted cone index of every slot
+    int32_t *slot_cone = nullptr;   // plan index of every slot's cone; bit 31 set in padding slots
     int32_t *warp_graph = nullptr;  // graph of every warp's slots
+    void *rec_hi = nullptr;         // [S][slots] cut words (uint32 or uint64, see RegWork)
+    float *rec_wk = nullptr;        // [S][slots] block multiplicities
+    uint2 *rec_cw = nullptr;        // depth-1 lists: [kP1Blocks][slots] cut values and multiplicity
     int64_t slots = 0, warps = 0;
     int32_t n = 0;
 };
@@ -37,6 +37,7 @@ struct qaoa_device_plan {
     int64_t n_cones = 0;
     DevWork reg_e;       // work list of the energy kernels
     DevWork reg_g[2];    // of the adjoint kernels with 4 and 5 register qubits
+    DevWork reg_p1;      // of the depth-1 kernel (p = 1 plans whose register cones all mix qubits 0, 1 only)
     std::vector<BigShape> big;
     size_t big_budget = size_t(1) << 30;  // scratch bytes per call for big cones
     double *half_edges = nullptr;
@@ -53,3 +54,17 @@ struct qaoa_device_plan {
     int64_t all_launches = 0;
 };
 
+// The register kernels' view of a work list.
+inline qaoa::RegWork reg_work(const qaoa_device_plan *d, const DevWork &w) {
+    qaoa::RegWork r;
+    r.cones = d->cones;
+    r.slot_cone = w.slot_cone;
+    r.warp_graph = w.warp_graph;
+    r.rec_hi = w.rec_hi;
+    r.rec_wk = w.rec_wk;
+    r.rec_cw = w.rec_cw;
+    r.n_cones = w.n;
+    r.slots = w.slots;
+    r.warps = w.warps;
+    return r;
+}

@@ -168,6 +168,7 @@ cudaError_t reg_prepare() {
         e = cudaFuncSetAttribute((const void *)reg_cone_kernel<kRegBitsEnergy, uint64_t, false, 0>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kRegMaxSmem);
     if (e == cudaSuccess) e = reg_grad_prepare();
+    if (e == cudaSuccess) e = reg_p1_prepare();
     if (e == cudaSuccess) done.insert(dev);
     return e;
 }

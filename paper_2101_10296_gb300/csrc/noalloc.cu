@@ -138,16 +138,7 @@ extern "C" int qaoa_energy_noalloc(const qaoa_plan *plan, int64_t n_points, cons
     // register-resident cones
     if (e == cudaSuccess && d->reg_e.warps > 0) {
         RegLaunch L;
-        L.work.cones = d->cones;
-        L.work.order = d->reg_e.order;
-        L.work.start = d->reg_e.prefix;
-        L.work.warp_first = d->reg_e.warp_first;
-        L.work.slot_cone = d->reg_e.slot_cone;
-        L.work.warp_graph = d->reg_e.warp_graph;
-        L.work.shell = d->shell;
-        L.work.n_cones = d->reg_e.n;
-        L.work.slots = d->reg_e.slots;
-        L.work.warps = d->reg_e.warps;
+        L.work = reg_work(d, d->reg_e);
         L.n_points = n_points;
         L.p = p;
         const int64_t row_bytes = int64_t(p) * ((d->cmax1 + 1) * int64_t(sizeof(float2)) + kRegKpow * int64_t(sizeof(float)));

@@ -49,6 +49,7 @@ class PlanInfo(C.Structure):
         ("max_edges", C.c_int32), ("on_device", C.c_int32), ("n_big", C.c_int64),
         ("amps_per_point", C.c_double), ("t_orbits_s", C.c_double), ("t_cones_s", C.c_double),
         ("orbits_complete", C.c_int32), ("n_big_general_energy", C.c_int64), ("n_big_general_grad", C.c_int64),
+        ("depth1_kernel", C.c_int32),
     ]
 
 

@@ -34,15 +34,20 @@ def _params(theta, G=1):
     return torch.tensor(np.ascontiguousarray(t), device="cuda")
 
 
-def _check_grad(g, gref, scale=1.0):
+def _check_grad(g, gref, scale=1.0, energy=None):
     """Norm-wise relative error <= G_REL_TOL and per-component error <= 1e-4 of
     the largest component; scale = 2 when gref is itself an FP32 result (each
-    side within the tolerance of the exact value)."""
+    side within the tolerance of the exact value).  With the point's energy
+    given, errors are measured against at least 1e-3 |E|: below |grad E| =
+    1e-3 |E| the derivative sums cancel to less than 1e-3 of their terms and
+    the FP32 state's own rounding sets the error (the near-stationary tests
+    pin the kernels at |grad E| = 1e-3 |E|)."""
     g = np.asarray(g, dtype=np.float64)
     gref = np.asarray(gref, dtype=np.float64)
-    nrm = np.linalg.norm(gref)
-    assert np.linalg.norm(g - gref) <= scale * G_REL_TOL * max(nrm, 1e-12)
-    assert np.max(np.abs(g - gref)) <= scale * 1e-4 * max(np.max(np.abs(gref)), 1e-12)
+    floor = 1e-12 if energy is None else 1e-3 * abs(float(energy))
+    nrm = max(np.linalg.norm(gref), floor)
+    assert np.linalg.norm(g - gref) <= scale * G_REL_TOL * nrm
+    assert np.max(np.abs(g - gref)) <= scale * 1e-4 * max(np.max(np.abs(gref)), floor)
 
 
 # ------------------------------------------------------------- cut tables
@@ -204,6 +209,59 @@ def test_gradient_matches_oracle_adjoint(q, graph, p, P):
         assert abs(e_only[j] - eref) <= E_REL_TOL * abs(eref)
         _check_grad(g[j], gref)
     assert plan.device_status() == 0
+
+
+@pytest.mark.parametrize("graphs,weights", [
+    ([I.random_regular(50, 3, s) for s in (1, 2, 3)] + [I.torus(6, 6), I.hypercube(7), I.star(9)], None),
+    ([I.erdos_renyi(40, 0.12, 3), I.complete(9)], (1, -1, 2)),
+])
+def test_depth1_kernel_matches_oracle_and_general_kernel(q, graphs, weights):
+    """p = 1 plans run on the depth-1 kernel (flat per-graph block lists, 16
+    blocks per thread, several cones per warp and per thread, graphs padded
+    to whole warps): energies and gradients against the FP64 oracle on
+    sampled graphs and points, and against the general register kernel (the
+    path of calls that ask for terms) on every graph and point; energy-only
+    calls as well.  Weighted case: random weights 1, -1, 2 (negative edges and
+    two-bit cut-word entries).  (Point 14 of Q_7 lies next to the trivial
+    point E = |E|/2, at |grad E| = 2e-5 |E|: there both kernels sit at the
+    FP32 floor, ~3e-3 of the gradient from the FP64 value.)"""
+    P = 20
+    w = None if weights is None else [np.random.default_rng(5 + k).choice(weights, len(e))
+                                      for k, (_, e) in enumerate(graphs)]
+    theta = np.stack([I.draw_params(1, P, 300 + k) for k in range(len(graphs))])
+    plan = q.Plan(graphs, 1, weights=w)
+    info = plan.info()
+    assert info["depth1_kernel"] == 1 and info["n_big"] == 0
+    e, g = plan.energy_grad(_params(theta))
+    e_only = plan.energy(_params(theta))
+    e2, g2, _ = plan.energy_grad(_params(theta), terms=True)
+    e, g, e_only, e2, g2 = (x.cpu().numpy() for x in (e, g, e_only, e2, g2))
+    for k in range(len(graphs)):
+        for j in range(P):
+            assert abs(e[k, j] - e2[k, j]) <= 2 * E_REL_TOL * abs(e2[k, j])
+            assert abs(e_only[k, j] - e2[k, j]) <= 2 * E_REL_TOL * abs(e2[k, j])
+            _check_grad(g[k, j], g2[k, j], scale=2.0, energy=e2[k, j])
+    rng = np.random.default_rng(11)
+    for k in range(len(graphs)):
+        n, edges = graphs[k]
+        if n > 60:
+            continue
+        every_edge = np.arange(len(edges))
+        adj = O.adjacency(n, edges)
+        for j in rng.choice(P, 2, replace=False):
+            eref, gref = O.orbit_grad_adjoint(n, edges, theta[k, j], 1, every_edge, adj,
+                                              weights=None if w is None else w[k])
+            assert abs(e[k, j] - eref) <= E_REL_TOL * max(abs(eref), 1.0)
+            _check_grad(g[k, j], gref, energy=eref)
+    assert plan.device_status() == 0
+
+
+def test_depth1_kernel_routing(q):
+    """The depth-1 kernel takes p = 1 plans whose register cones all have the
+    inner part {u, v}; deeper plans and full cones keep the general kernels."""
+    assert q.Plan(I.random_regular(30, 3, 1), 1).info()["depth1_kernel"] == 1
+    assert q.Plan(I.random_regular(30, 3, 1), 2).info()["depth1_kernel"] == 0
+    assert q.Plan(I.cycle(12), 1, full_cone=True).info()["depth1_kernel"] == 0
 
 
 def test_gradient_matches_finite_differences(q):
@@ -976,15 +1034,21 @@ def test_gradient_at_near_stationary_points(q, case):
             assert info["n_big"] == 1 and info["n_big_general_grad"] == 0
         else:
             assert info["n_big"] >= 1 and info["n_big_general_grad"] == info["n_big"]
-        e, g = plan.energy_grad(_params(theta))
-        e, g = e.cpu().numpy()[0], g.cpu().numpy()[0]
-        for j, r in enumerate(rows):
-            assert abs(e[j] - r["energy"]) <= E_REL_TOL * abs(r["energy"]), (name, j)
-            try:
-                _check_grad(g[j], r["grad"])
-            except AssertionError:
-                err = np.linalg.norm(g[j] - r["grad"]) / np.linalg.norm(r["grad"])
-                raise AssertionError(f"{case} {name} point {j}: relative gradient error {err:.2e}")
+        runs = {name: plan.energy_grad(_params(theta))}
+        if name == "register" and p == 1:
+            # the depth-1 kernel, and the general register kernel (which calls
+            # asking for terms use)
+            assert info["depth1_kernel"] == 1
+            runs["register-general"] = plan.energy_grad(_params(theta), terms=True)[:2]
+        for run, (e, g) in runs.items():
+            e, g = e.cpu().numpy()[0], g.cpu().numpy()[0]
+            for j, r in enumerate(rows):
+                assert abs(e[j] - r["energy"]) <= E_REL_TOL * abs(r["energy"]), (run, j)
+                try:
+                    _check_grad(g[j], r["grad"])
+                except AssertionError:
+                    err = np.linalg.norm(g[j] - r["grad"]) / np.linalg.norm(r["grad"])
+                    raise AssertionError(f"{case} {run} point {j}: relative gradient error {err:.2e}")
         assert plan.device_status() == 0
 
 
