@@ -2,6 +2,7 @@
 // cut tables, device status.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 #include <string>
@@ -169,9 +170,10 @@ int build_work(const std::vector<DevCone> &hc, const std::vector<uint64_t> &shel
 // The depth-1 kernel's list (every cone with inner part {u, v}, mixed by the
 // only layer): per graph, the shell blocks of its cones back to back, each
 // as (c_0 | c_1 << 8 | c_2 << 16 | c_3 << 24, W) with c_a the cut value of
-// amplitude a = z_u + 2 z_v of the block and W = multiplicity x orbit size x
-// 2^-n rounded once to float; slot s of a graph takes its blocks 16 s ..
-// 16 s + 15, and every graph starts on a fresh warp (padding: zero weight).
+// amplitude a = z_u + 2 z_v of the block (up to the relabelling below) and
+// W = +-multiplicity x orbit size x 2^-n rounded once to float; slot s of a
+// graph takes its blocks 16 s .. 16 s + 15, and every graph starts on a
+// fresh warp (padding: zero weight).
 int build_p1_work(const std::vector<DevCone> &hc, const std::vector<uint64_t> &shell_tab,
                   const std::vector<int32_t> &idx, DevWork &w) {
     std::vector<int32_t> order(idx);
@@ -189,9 +191,24 @@ int build_p1_work(const std::vector<DevCone> &hc, const std::vector<uint64_t> &s
             for (int64_t beta = 0; beta < C.n_blocks; ++beta) {
                 float mult = 0.f;
                 const uint64_t word = host_shell_block(C, shell_tab, uint32_t(beta), mult);
+                int c[4];
+                for (int a = 0; a < 4; ++a) c[a] = __builtin_popcountll(lo[a] ^ word);
+                // amplitude order: relabel by f in {X_u, X_v, X_u X_v} (index a -> a
+                // xor f) so that the first cut value, against which the kernel
+                // shifts C in d/dgamma, is the one nearest the middle of the four;
+                // a single flip turns Z_u Z_v into -Z_u Z_v, so W changes sign
+                int f = 0, spread = 1 << 30;
+                for (int r = 0; r < 4; ++r) {
+                    int dev = 0;
+                    for (int a = 0; a < 4; ++a) dev = std::max(dev, std::abs(c[a] - c[r]));
+                    if (dev < spread) {
+                        spread = dev;
+                        f = r;
+                    }
+                }
                 uint32_t cnt = 0;
-                for (int a = 0; a < 4; ++a) cnt |= uint32_t(__builtin_popcountll(lo[a] ^ word)) << (8 * a);
-                const float wf = float(double(mult) * scale);
+                for (int a = 0; a < 4; ++a) cnt |= uint32_t(c[a ^ f]) << (8 * a);
+                const float wf = float(double(mult) * scale) * ((f == 1 || f == 2) ? -1.f : 1.f);
                 uint32_t bits;
                 std::memcpy(&bits, &wf, sizeof bits);
                 blocks.push_back(make_uint2(cnt, bits));

@@ -197,7 +197,9 @@ constexpr int kRegLaneWords = 3;
 // per graph the shell blocks of all the graph's cones back to back, block k
 // of slot s as rec_cw[k * slots + s] = (c_0 | c_1 << 8 | c_2 << 16 | c_3 <<
 // 24, bits of W), c_a the cut value of amplitude a = z_u + 2 z_v and W the
-// block's multiplicity x orbit size x 2^-n; warp_graph as for the other lists.
+// block's multiplicity x orbit size x 2^-n; the amplitudes may be relabelled
+// by X_u, X_v or both (a -> a xor f), with W negated for a single flip, so
+// that c_0 is the middle one of the four; warp_graph as for the other lists.
 constexpr int kP1Blocks = 16;
 constexpr int kP1GradMinBlocks = 6;
 constexpr int kP1EnergyMinBlocks = 8;

@@ -27,9 +27,14 @@
 //     (half the products of the general form);
 //   dE/dgamma = 2 Im<lambda|C|s> with the mixer undone on r.  Im<r|s> is
 //     zero within every block (it equals <x|Z_u Z_v|x>, which is real), so C
-//     may be replaced by C - c_0, the block's own first cut value: the
-//     differences c_a - c_0 are small integers, which removes most of the
-//     cancellation of the FP32 sums and one of the four terms.
+//     may be shifted by any per-block constant: the block's first cut value
+//     c_0, which drops one of the four terms.  The upload orders each block's
+//     amplitudes so that c_0 is the one of its four cut values nearest their
+//     middle (relabelling by X_u, X_v or both, which leave |+> and the mixers
+//     unchanged and turn Z_u Z_v into -Z_u Z_v, +Z_u Z_v: the weight W takes
+//     the sign).  That keeps the weights c_a - c_0 within about half the
+//     block's spread, which limits how much of the FP32 state's rounding the
+//     cancelling sum keeps.
 // The block terms are accumulated per thread in four partial sums (blocks
 // mod 4) and the lanes' shares of each point are summed with compensation
 // (reg_flush).
