@@ -874,6 +874,9 @@ def run_suite(args):
     # re-planning every round, enumeration of the last eight vertices
     from paper_2101_10296_gb300 import rqaoa
     n, edges = I.random_regular(60, 3, 1)
+    # untimed warm-up: the first use of the optimiser's and reductions' kernels
+    # on a fresh device loads them (seconds)
+    rqaoa.rqaoa(*I.random_regular(20, 3, 2), p=1, n_brute=8, steps=3, points=8, seed=1)
     t0 = time.perf_counter()
     out = rqaoa.rqaoa(n, edges, p=1, n_brute=8, steps=100, points=8, seed=1)
     secs = time.perf_counter() - t0
