@@ -236,7 +236,8 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? (R <= 4 ? kGradMinBlocks : k
     float *red_all = reinterpret_cast<float *>(s_tab + (kRegBlock / 32) * (L.jpt * (row + p))) +
                      (kRegBlock / 32) * (L.jpt * p * kRegKpow);
     float *red = red_all + warp * (NOUT * G * 32);
-    uint32_t *my_cone = reinterpret_cast<uint32_t *>(red_all + (kRegBlock / 32) * (NOUT * G * 32)) + warp * (kRegLaneWords * 32);
+    uint32_t *my_cone =
+        reinterpret_cast<uint32_t *>(red_all + (kRegBlock / 32) * (NOUT * G * 32)) + warp * (reg_lane_words(p) * 32);
     const int64_t gw = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
     const int64_t nblk = (L.n_points + L.jpt - 1) / L.jpt;
@@ -285,7 +286,8 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? (R <= 4 ? kGradMinBlocks : k
         // The cone fields the point loop reads go to the lane's slots in shared
         // memory once per task: a warp's lanes read up to 32 different cone
         // structs, which do not stay in L1 from one point to the next.  Word 0
-        // (1) holds k of layers 0-3 (4-7), one byte each; word 2 holds c0 =
+        // (1) holds k of layers 0-3 (4-7), one byte each; words 3 + 2l and
+        // 4 + 2l the flip word of layer l; word 2 holds c0 =
         // m/2: Im<lambda|psi> = <psi_end|O|psi_end> is real at every point of
         // the sweep (and within every shell block), so C may be replaced by
         // C - c0 in d/d gamma, which removes the mean cut value and with it most
@@ -297,8 +299,20 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? (R <= 4 ? kGradMinBlocks : k
             my_cone[lane] = kw[0];
             my_cone[32 + lane] = kw[1];
             my_cone[64 + lane] = __float_as_uint(0.5f * float(C->m));
+            if (PC != 1) {
+                for (int l = 0; l < p; ++l) {
+                    const uint64_t f = C->pw[l];
+                    my_cone[(3 + 2 * l) * 32 + lane] = uint32_t(f);
+                    my_cone[(4 + 2 * l) * 32 + lane] = uint32_t(f >> 32);
+                }
+            }
         }
         auto k_of = [&](int l) -> int { return int((my_cone[(l >> 2) * 32 + lane] >> (8 * (l & 3))) & 0xffu); };
+        auto pw_of = [&](int l) -> MT {
+            MT f = MT(my_cone[(3 + 2 * l) * 32 + lane]);
+            if constexpr (sizeof(MT) == 8) f |= MT(my_cone[(4 + 2 * l) * 32 + lane]) << 32;
+            return f;
+        };
         if (!active) {
 #pragma unroll
             for (int k = 0; k < NA / 4; ++k) wk[k] = 0.f;
@@ -355,7 +369,7 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? (R <= 4 ? kGradMinBlocks : k
                 mix_lane<R>(x, k, mx.x);
                 sig *= kp[l * kRegKpow + k];
                 if (PC != 1 && mx.y != 0.f) {  // (no lookup follows a flip at p = 1)
-                    const MT f = MT(C->pw[l]);
+                    const MT f = pw_of(l);
                     cw.flip(f);
                     fw ^= f;
                 }
@@ -443,7 +457,7 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? (R <= 4 ? kGradMinBlocks : k
                     // adds the lanes' shares with compensation
                     stash(1 + p + l, jj, gw2 * sig * db);
                     sig *= kpl[k];
-                    if (PC != 1 && mx.y != 0.f) cw.flip(MT(C->pw[l]));
+                    if (PC != 1 && mx.y != 0.f) cw.flip(pw_of(l));
                     // d/d gamma_l = 2 sigma Im <r| C |s>; then undo the phase
                     float dg4[NA / 4];
 #pragma unroll

@@ -190,8 +190,9 @@ __host__ __device__ constexpr int reg_group(int p, bool grad) {
 // kappa powers a register kernel reads: kappa^(2k) for k <= its largest inner part
 constexpr int kRegKpow = 10;
 // 32-bit words of per-lane cone fields a register kernel keeps in shared
-// memory (the layers' k, one byte each, and the adjoint's cut-value offset)
-constexpr int kRegLaneWords = 3;
+// memory: the layers' k (one byte each, two words), the adjoint's cut-value
+// offset, and per layer the flip word M(F_l) as two words
+__host__ __device__ constexpr int reg_lane_words(int p) { return 3 + 2 * p; }
 // Depth-1 kernel (p1_kernel.cu): shell blocks per thread, and the resident
 // blocks per SM its register allocation is sized for.  Its work lists hold
 // per graph the shell blocks of all the graph's cones back to back, block k
@@ -217,12 +218,12 @@ cudaError_t launch_reg_p1(const RegLaunch &a, bool grad, int grid, cudaStream_t 
 // Dynamic shared memory of a register-kernel block: per warp and point the
 // phase tables (p x cmax1 float2), the mixer data (p float2) and the kappa
 // powers (p x kRegKpow float) of jpt points, the reduction buffer, and the
-// lanes' cone fields.
+// lanes' cone fields (reg_lane_words).
 inline size_t reg_smem_bytes(int jpt, int p, int cmax1, bool grad) {
     return size_t(kRegBlock / 32) *
            (size_t(jpt) * p * (cmax1 + 1) * sizeof(float2) +
             (size_t(jpt) * p * kRegKpow + size_t(reg_outputs(p, grad)) * reg_group(p, grad) * 32 +
-             size_t(kRegLaneWords) * 32) * sizeof(float));
+             size_t(reg_lane_words(p)) * 32) * sizeof(float));
 }
 
 }  // namespace qaoa
