@@ -135,8 +135,30 @@ extern "C" int qaoa_energy_noalloc(const qaoa_plan *plan, int64_t n_points, cons
     pa.terms = terms_dev;
     pa.n_reps = d->n_cones;
     e = launch_prep(pa, s);
-    // register-resident cones
-    if (e == cudaSuccess && d->reg_e.warps > 0) {
+    // register-resident cones: the depth-1 kernel where the plan has its list
+    // (p = 1, no per-cone terms asked for), else the general register kernel
+    if (e == cudaSuccess && p == 1 && d->reg_p1.warps > 0 && terms_dev == nullptr) {
+        RegLaunch L;
+        L.work = reg_work(d, d->reg_p1);
+        L.n_points = n_points;
+        L.p = 1;
+        const int64_t row = int64_t(d->cmax1 + 1) * int64_t(sizeof(float2));
+        const int64_t fixed = int64_t(reg_p1_smem_bytes(0, d->cmax1, false)) / (kRegBlock / 32);
+        const int64_t fit = (int64_t(kRegMaxSmem) / (kRegBlock / 32) - fixed) / row;
+        L.jpt = int32_t(std::min<int64_t>(std::min<int64_t>(8, std::max<int64_t>(1, fit)), n_points));
+        L.cmax1 = d->cmax1;
+        L.lut = lut;
+        L.mix = mix;
+        L.kpow = kpow;
+        L.energy = energy_dev;
+        L.grad = nullptr;
+        L.terms = nullptr;
+        L.status = d->status;
+        const size_t smem = reg_p1_smem_bytes(L.jpt, d->cmax1, false);
+        const int64_t tasks = L.work.warps * ((n_points + L.jpt - 1) / L.jpt);
+        const int64_t grid = std::min<int64_t>(reg_p1_grid(false, smem), (tasks + 3) / 4);
+        e = launch_reg_p1(L, false, int(std::max<int64_t>(grid, 1)), s);
+    } else if (e == cudaSuccess && d->reg_e.warps > 0) {
         RegLaunch L;
         L.work = reg_work(d, d->reg_e);
         L.n_points = n_points;

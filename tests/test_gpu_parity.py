@@ -256,6 +256,40 @@ def test_depth1_kernel_matches_oracle_and_general_kernel(q, graphs, weights):
     assert plan.device_status() == 0
 
 
+@pytest.mark.parametrize("P", [1, 13])
+def test_depth1_kernel_edge_cases(q, P):
+    """Depth-1 lists at their edges, against the FP64 oracle summed over every
+    edge: an edgeless graph inside a batch (no blocks, energy 0), a single
+    edge (one cone of one block: the graph's warp is almost all padding), a
+    path, isolated vertices, and a weighted star whose cones carry 54 cut-word
+    bits (weights 9: counts beyond one 32-bit word, up to 54 per byte);
+    1 point, and 13 points (a ragged last task)."""
+    graphs = [(5, np.zeros((0, 2), dtype=np.int64)), (2, np.array([[0, 1]])), I.path(6),
+              (9, np.array([[0, 1], [1, 2], [6, 7]])), I.star(6)]
+    weights = [np.ones(len(e), dtype=np.int64) for _, e in graphs[:-1]] + [np.full(6, 9, dtype=np.int64)]
+    # seeds whose points all have |grad E| > 0.02 |E| (seed 70 puts a point of the
+    # weighted star at 9 gamma = pi mod 2 pi, a stationary point, where the FP32
+    # floor of the near-stationary tests applies instead)
+    theta = np.stack([I.draw_params(1, P, 80 + k) for k in range(len(graphs))])
+    plan = q.Plan(graphs, 1, weights=weights)
+    info = plan.info()
+    assert info["depth1_kernel"] == 1 and info["max_edges"] == 6
+    e, g = plan.energy_grad(_params(theta))
+    e_only = plan.energy(_params(theta)).cpu().numpy()
+    e, g = e.cpu().numpy(), g.cpu().numpy()
+    for k, (n, edges) in enumerate(graphs):
+        for j in range(P):
+            if len(edges) == 0:
+                assert e[k, j] == 0.0 and e_only[k, j] == 0.0 and np.all(g[k, j] == 0.0)
+                continue
+            eref, gref = O.orbit_grad_adjoint(n, edges, theta[k, j], 1, np.arange(len(edges)),
+                                              weights=weights[k])
+            assert abs(e[k, j] - eref) <= E_REL_TOL * max(abs(eref), 1.0), (k, j)
+            assert abs(e_only[k, j] - eref) <= E_REL_TOL * max(abs(eref), 1.0), (k, j)
+            _check_grad(g[k, j], gref, energy=eref)
+    assert plan.device_status() == 0
+
+
 def test_depth1_kernel_routing(q):
     """The depth-1 kernel takes p = 1 plans whose register cones all have the
     inner part {u, v}; deeper plans and full cones keep the general kernels."""

@@ -75,6 +75,33 @@ def test_noalloc_calls_leave_device_memory_unchanged(qlib):
     assert plan.device_status() == 0
 
 
+def test_noalloc_depth1_matches_and_allocates_nothing(qlib):
+    """At p = 1 (a depth-1 plan: every cone's inner part is its edge) the
+    allocation-free call takes the depth-1 kernel, like qaoa_energy: the same
+    energies, and no device memory taken after the upload."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    graphs = [I.hypercube(7), I.torus(6, 6), I.cycle(30), I.random_regular(40, 3, 2)]
+    plan = qlib.Plan(graphs, 1)
+    plan.upload()
+    assert plan.info()["depth1_kernel"] == 1
+    theta = np.stack([I.draw_params(1, 20, 40 + g) for g in range(len(graphs))])
+    params = torch.tensor(theta, device="cuda")
+    e_ref = plan.energy(params).cpu().numpy()
+    out = torch.full((len(graphs), 20), float("nan"), dtype=torch.float64, device="cuda")
+    plan.energy_noalloc(params, out=out)
+    gc.collect()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    used0 = torch.cuda.memory_allocated()
+    plan.energy_noalloc(params, out=out)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0 and torch.cuda.memory_allocated() == used0
+    assert np.allclose(out.cpu().numpy(), e_ref, rtol=E_REL_TOL, atol=0)
+    assert plan.device_status() == 0
+
+
 def test_noalloc_rejects_bad_outputs_before_the_call(qlib):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
