@@ -894,6 +894,7 @@ PROFILE_CASES = {
     "reg-mix48-small": "the 48-graph mix, p=1, 16 points: energy+grad",
     "reg-mix48-p32": "the 48-graph mix, p=1, 32 points: energy+grad",
     "reg-adjoint-rr3-n2000": "1 random 3-regular graph n=2000 (seed 1), p=2, 8 points: energy+grad",
+    "reg-adjoint-rr3-n2000-p64": "1 random 3-regular graph n=2000 (seed 1), p=2, 64 points: energy+grad",
     "reg-rr3-x4": "4 x rr3 n=2000, p=2, 64 points: energy+grad",
     "split-adjoint-rr3-n24": "1 random 3-regular graph n=24 (seed 1), p=3, 8 points: energy+grad",
     "split-adjoint-torus6": "6x6 torus, p=3, 2 points: energy+grad",
@@ -916,6 +917,7 @@ def run_case(name):
         p, grad, kw = 2, True, {}
     else:
         spec = {"reg-adjoint-rr3-n2000": ([I.random_regular(2000, 3, 1)], 2, 8, True, {}),
+                "reg-adjoint-rr3-n2000-p64": ([I.random_regular(2000, 3, 1)], 2, 64, True, {}),
                 "split-adjoint-rr3-n24": ([I.random_regular(24, 3, 1)], 3, 8, True, {}),
                 "split-adjoint-torus6": ([I.torus(6, 6)], 3, 2, True, {}),
                 "split-energy-torus6": ([I.torus(6, 6)], 3, 4, False, {}),
