@@ -304,6 +304,19 @@ int qaoa_energy(const qaoa_plan *plan, int64_t n_points, const double *params_de
                 double *energy_dev, double *terms_dev, qaoa_stream_t stream);
 
 /*
+ * State norms: the forward sweep of qaoa_energy with the identity in place of
+ * Z_u Z_v, so that norms_dev receives sum_z |psi_z|^2 of every representative's
+ * cone state at every point (exactly 1 for the unitary evolution of Sec. 2.2;
+ * the departure from 1 is the FP32 state's accumulated rounding).  The
+ * energies are not renormalised by it: this is a diagnostic.
+ *   norms_dev   device float64[n_reps][n_points], overwritten
+ * Other arguments and errors as qaoa_energy; allocates one stream-ordered
+ * float64[n_graphs][n_points] scratch for the unused energies.
+ */
+int qaoa_norms(const qaoa_plan *plan, int64_t n_points, const double *params_dev,
+               double *norms_dev, qaoa_stream_t stream);
+
+/*
  * Energies and their gradients dE/d(gamma_1..gamma_p, beta_1..beta_p) by the
  * adjoint method: after the forward sweep, the state psi and the co-state
  * lambda = -1/2 Z_u Z_v psi are taken back through the inverse gates; each

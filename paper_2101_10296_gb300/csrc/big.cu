@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(128) big_pass_kernel(const __grid_constant__ B
                     break;
                 }
                 case kOpReduce: {
-                    const float sg = ((lane ^ (lane >> 1)) & 1) ? -1.f : 1.f;
+                    const float sg = ((lane ^ (lane >> 1)) & 1) && !L.norm ? -1.f : 1.f;
                     float acc = 0.f;
 #pragma unroll
                     for (int i = 0; i < NR; ++i) acc = fmaf(x[i].x, x[i].x, fmaf(x[i].y, x[i].y, acc));

@@ -62,6 +62,7 @@ struct BigLaunch {
     float2 *psi, *lam;        // scratch: n_items blocks of 2^n_in
     double *energy, *grad, *terms;
     int32_t *status;
+    int32_t norm;             // 1: the observable is the identity (terms = sum |psi|^2, energy unused)
     BigPass pass;             // general schedule: the pass to run
     // core-tile schedule
     int32_t rb;               // register qubits of a core tile

@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(128, GRAD ? QAOA_SPLIT_GRAD_BLOCKS : 3) split_
         }
         float acc = 0.f;
 #pragma unroll
-        for (int i = 0; i < NR; ++i) acc += zz_sign(i) * fmaf(x[i].x, x[i].x, x[i].y * x[i].y);
+        for (int i = 0; i < NR; ++i) acc += (GRAD || !L.norm ? zz_sign(i) : 1.f) * fmaf(x[i].x, x[i].x, x[i].y * x[i].y);
         const float tv = acc * sig * mult;  // this tile's share of <Z_0 Z_1>
         add_gp(-0.5f * float(C->weight) * tv, L.energy, gj);
         if (L.terms) add_gp(tv, L.terms, C->rep * L.P + j);

@@ -278,7 +278,7 @@ int64_t tuned_grid(const qaoa_device_plan *d, int occupancy_grid) {
 // each wave streamed through the shape's pass list.
 cudaError_t run_big(const qaoa_device_plan *d, const qaoa_plan *plan, int64_t P, const double *params,
                     const float2 *lut, const float2 *mix, const float *kpow, double *energy, double *grad,
-                    double *terms, cudaStream_t s) {
+                    double *terms, bool norm, cudaStream_t s) {
     qaoa_device_plan *dm = const_cast<qaoa_device_plan *>(d);
     const int p = plan->p;
     float4 *cs = nullptr;
@@ -318,6 +318,7 @@ cudaError_t run_big(const qaoa_device_plan *d, const qaoa_plan *plan, int64_t P,
         B.grad = grad;
         B.terms = terms;
         B.status = d->status;
+        B.norm = norm ? 1 : 0;
         const std::vector<BigPass> &passes = g ? bs.grad : bs.fwd;
         for (int64_t i0 = 0; i0 < items && e == cudaSuccess; i0 += wave) {
             B.item0 = i0;
@@ -339,8 +340,10 @@ cudaError_t run_big(const qaoa_device_plan *d, const qaoa_plan *plan, int64_t P,
     return e;
 }
 
+// norm: the observable is the identity instead of Z_u Z_v (energy path only;
+// terms then receive sum |psi|^2 per representative and energy is scratch)
 int run(const qaoa_plan *plan, int64_t n_points, const double *params, double *energy, double *grad,
-        double *terms, cudaStream_t s) {
+        double *terms, cudaStream_t s, bool norm = false) {
     if (!plan || n_points < 1 || !params || !energy) {
         set_error("need a plan, n_points >= 1, params and energy");
         return QAOA_E_INVALID;
@@ -393,7 +396,7 @@ int run(const qaoa_plan *plan, int64_t n_points, const double *params, double *e
         cudaEventRecord(ev0, s);
     }
     // depth 1 (no per-cone terms asked for): the depth-1 kernel over flat block lists
-    const bool use_p1 = p == 1 && d->reg_p1.warps > 0 && terms == nullptr;
+    const bool use_p1 = p == 1 && d->reg_p1.warps > 0 && terms == nullptr && !norm;
     if (e == cudaSuccess && use_p1) {
         RegLaunch L;
         L.n_points = n_points;
@@ -432,7 +435,7 @@ int run(const qaoa_plan *plan, int64_t n_points, const double *params, double *e
         int64_t grid = std::min<int64_t>(tuned_grid(d, reg_p1_grid(grad != nullptr, smem)), (tasks + 3) / 4);
         e = launch_reg_p1(L, grad != nullptr, int(std::max<int64_t>(grid, 1)), s);
         dm->all_launches += 1;
-        if (e == cudaSuccess && !d->big.empty()) e = run_big(d, plan, n_points, params, lut, mix, kpow, energy, grad, terms, s);
+        if (e == cudaSuccess && !d->big.empty()) e = run_big(d, plan, n_points, params, lut, mix, kpow, energy, grad, terms, norm, s);
     } else if (e == cudaSuccess) {
         RegLaunch L;
         L.n_points = n_points;
@@ -464,6 +467,7 @@ int run(const qaoa_plan *plan, int64_t n_points, const double *params, double *e
         L.grad = grad;
         L.terms = terms;
         L.status = d->status;
+        L.norm = norm && !grad ? 1 : 0;
         if (grad) {
             const int rg = reg_bits_for(d, p);
             L.work = as_reg(d, d->reg_g[rg - 4]);
@@ -480,7 +484,7 @@ int run(const qaoa_plan *plan, int64_t n_points, const double *params, double *e
             }
         }
         if (L.work.warps > 0) dm->all_launches += 1;
-        if (e == cudaSuccess && !d->big.empty()) e = run_big(d, plan, n_points, params, lut, mix, kpow, energy, grad, terms, s);
+        if (e == cudaSuccess && !d->big.empty()) e = run_big(d, plan, n_points, params, lut, mix, kpow, energy, grad, terms, norm, s);
     }
     if (ev0) {
         cudaEventRecord(ev1, s);
@@ -739,6 +743,24 @@ extern "C" int qaoa_plan_info(const qaoa_plan *plan, qaoa_plan_info_t *info) {
 extern "C" int qaoa_energy(const qaoa_plan *plan, int64_t n_points, const double *params_dev, double *energy_dev,
                            double *terms_dev, qaoa_stream_t stream) {
     return run(plan, n_points, params_dev, energy_dev, nullptr, terms_dev, (cudaStream_t)stream);
+}
+
+extern "C" int qaoa_norms(const qaoa_plan *plan, int64_t n_points, const double *params_dev, double *norms_dev,
+                          qaoa_stream_t stream) {
+    if (!plan || n_points < 1 || !params_dev || !norms_dev) {
+        set_error("need a plan, n_points >= 1, params and norms");
+        return QAOA_E_INVALID;
+    }
+    const cudaStream_t s = (cudaStream_t)stream;
+    double *scratch = nullptr;  // the energy output of the identity observable, unused
+    cudaError_t e = cudaMallocAsync(&scratch, size_t(plan->n_graphs) * size_t(n_points) * sizeof(double), s);
+    if (e != cudaSuccess) {
+        set_error(std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? QAOA_E_OOM : QAOA_E_CUDA;
+    }
+    const int rc = run(plan, n_points, params_dev, scratch, nullptr, norms_dev, s, true);
+    cudaFreeAsync(scratch, s);
+    return rc;
 }
 
 extern "C" int qaoa_energy_grad(const qaoa_plan *plan, int64_t n_points, const double *params_dev,

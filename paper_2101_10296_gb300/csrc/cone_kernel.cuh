@@ -187,16 +187,18 @@ __device__ __forceinline__ void mix_lane(float2 (&x)[1 << R], int k, float tau) 
     }
 }
 
-// sum_i w_(i>>2) |x_i|^2 (-1)^(i_0 xor i_1)
+// sum_i w_(i>>2) |x_i|^2 (-1)^(i_0 xor i_1); with ns = +1 instead of -1 the
+// identity's sum_i w |x_i|^2 (the norm)
 template <int R>
-__device__ __forceinline__ float zz_partial(const float2 (&x)[1 << R], const float (&wk)[1 << (R - 2)]) {
+__device__ __forceinline__ float zz_partial(const float2 (&x)[1 << R], const float (&wk)[1 << (R - 2)],
+                                            float ns = -1.f) {
     float tot = 0.f;
 #pragma unroll
     for (int k = 0; k < (1 << (R - 2)); ++k) {
         const float2 a = x[4 * k], b = x[4 * k + 1], c = x[4 * k + 2], d = x[4 * k + 3];
         const float pos = fmaf(a.x, a.x, fmaf(a.y, a.y, fmaf(d.x, d.x, d.y * d.y)));
         const float neg = fmaf(b.x, b.x, fmaf(b.y, b.y, fmaf(c.x, c.x, c.y * c.y)));
-        tot = fmaf(wk[k], pos - neg, tot);
+        tot = fmaf(wk[k], fmaf(ns, neg, pos), tot);
     }
     return tot;
 }
@@ -374,7 +376,7 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? (R <= 4 ? kGradMinBlocks : k
                     fw ^= f;
                 }
             }
-            const float tl = zz_partial<R>(x, wk);
+            const float tl = GRAD ? zz_partial<R>(x, wk) : zz_partial<R>(x, wk, L.norm ? 1.f : -1.f);
             stash(0, jj, -0.5f * wgt * sig * tl);
             if (L.terms) {
                 float tv = sig * tl;

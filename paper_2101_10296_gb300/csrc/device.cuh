@@ -118,6 +118,7 @@ struct RegLaunch {
     double *grad;             // [G][P][2p] or null
     double *terms;            // [reps][P] or null
     int32_t *status;
+    int32_t norm = 0;         // 1: the observable is the identity (terms = sum |psi|^2, energy unused)
 };
 
 struct PrepArgs {

@@ -79,6 +79,7 @@ _SIGS = {
     "qaoa_plan_upload": (C.c_int, [_P]),
     "qaoa_cut_table": (C.c_int, [_P, C.c_int64, _P, _P]),
     "qaoa_energy": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P]),
+    "qaoa_norms": (C.c_int, [_P, C.c_int64, _P, _P, _P]),
     "qaoa_energy_grad": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P, _P]),
     "qaoa_energy_noalloc": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P]),
     "qaoa_device_status": (C.c_int, [_P, _I32P]),
@@ -314,6 +315,17 @@ class Plan:
         _check(lib().qaoa_energy(self._h, P, C.c_void_p(params.data_ptr()), C.c_void_p(e.data_ptr()),
                                  C.c_void_p(t.data_ptr()) if terms else None, _stream_handle(stream)))
         return (e, t) if terms else e
+
+    def norms(self, params, stream=None):
+        """sum_z |psi_z|^2 of every representative's cone state at every point,
+        [n_reps, P] (1 up to the FP32 state's rounding; a diagnostic)."""
+        import torch
+        params = self._params(params)
+        P = params.shape[1]
+        out = torch.empty(self.info()["n_reps"], P, dtype=torch.float64, device=params.device)
+        _check(lib().qaoa_norms(self._h, P, C.c_void_p(params.data_ptr()), C.c_void_p(out.data_ptr()),
+                                _stream_handle(stream)))
+        return out
 
     def energy_noalloc(self, params, out=None, terms=None, stream=None):
         """E[g, j] through qaoa_energy_noalloc, into caller-provided tensors.

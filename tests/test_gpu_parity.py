@@ -290,6 +290,35 @@ def test_depth1_kernel_edge_cases(q, P):
     assert plan.device_status() == 0
 
 
+@pytest.mark.parametrize("graph,p,kw", [
+    (I.petersen(), 2, {}),                                   # register cones, p = 2
+    (I.hypercube(8), 1, {}),                                 # a depth-1 plan (norms take the general kernel)
+    (I.hypercube(8), 1, {"full_cone": True}),                # a 16-qubit block, core-tile schedule
+    (I.hypercube(8), 1, {"full_cone": True, "big_general": True}),   # general schedule
+    (I.random_regular(24, 3, 1), 3, {}),                     # large-state cones of 10-14 inner qubits
+    (I.circulant(30, [1, 2]), 4, {}),                        # default plan on the general schedule
+    (I.erdos_renyi(14, 0.3, 2), 2, {"weights": (1, -1, 2)}),  # signed, two-bit weights
+])
+def test_state_norms_are_one(q, graph, p, kw):
+    """qaoa_norms: the forward sweep with the identity as the observable gives
+    sum_z |psi_z|^2 = 1 for every representative at every point (Sec. 2.2:
+    the evolution is unitary), on every schedule; the departure from 1 is
+    the FP32 state's rounding.  An energy call after it is unchanged."""
+    n, edges = graph
+    kw = dict(kw)
+    if "weights" in kw:
+        kw["weights"] = np.random.default_rng(3).choice(kw["weights"], len(edges))
+    theta = I.draw_params(p, 4, 9)
+    plan = q.Plan((n, edges), p, **kw)
+    e0 = plan.energy(_params(theta)).cpu().numpy()
+    nrm = plan.norms(_params(theta)).cpu().numpy()
+    assert nrm.shape == (plan.info()["n_reps"], 4)
+    assert np.max(np.abs(nrm - 1.0)) <= 1e-5, np.max(np.abs(nrm - 1.0))
+    e1 = plan.energy(_params(theta)).cpu().numpy()
+    assert np.array_equal(e0, e1) or np.allclose(e0, e1, rtol=1e-12, atol=0)
+    assert plan.device_status() == 0
+
+
 def test_depth1_kernel_routing(q):
     """The depth-1 kernel takes p = 1 plans whose register cones all have the
     inner part {u, v}; deeper plans and full cones keep the general kernels."""
