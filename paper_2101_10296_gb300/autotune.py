@@ -7,9 +7,9 @@ the groups before it):
 1. the number of parameter points a warp task of the register kernels
    evaluates (1 .. 32 while the phase tables fit) and the persistent grid's
    blocks per SM;
-2. with gradients and register-resident cones: the adjoint register kernel's
-   tile, 2^(bits + 5) amplitudes per warp with 4 or 5 register qubits per
-   thread;
+2. with gradients and register-resident cones on the general register
+   kernel (not depth-1 plans): the adjoint register kernel's tile,
+   2^(bits + 5) amplitudes per warp with 4 or 5 register qubits per thread;
 3. with large-state cones: the scratch per call, i.e. how many state blocks a
    wave holds (waves that fit the L2 keep their passes on chip), and the
    widest window of outer qubits a shared-memory chunk pass mixes (the chunk
@@ -59,7 +59,9 @@ def candidate_groups(plan, n_points, grad):
     row_bytes = info["p"] * (info["max_edges"] + 1) * 8
     jpts = [j for j in (1, 2, 4, 8, 16, 32) if j <= max(1, n_points) and j * row_bytes * 4 <= 48 * 1024]
     groups = [[{"points_per_task": j, "blocks_per_sm": b} for j in jpts for b in (0, 1, 2)]]
-    has_reg = info["n_reps"] > info["n_big"]
+    # the adjoint register tile matters only to the general register kernel
+    # (depth-1 plans run their register cones on the depth-1 kernel)
+    has_reg = info["n_reps"] > info["n_big"] and not info["depth1_kernel"]
     if grad and has_reg:
         groups.append([{"reg_bits_grad": r} for r in (4, 5)])
     if info["n_big"] > 0:

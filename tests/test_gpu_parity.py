@@ -847,6 +847,9 @@ def test_autotune_searches_tile_shapes_per_plan_shape(q, tmp_path):
     assert {c.get("reg_bits_grad") for c in c_small} >= {4, 5}
     assert not any("chunk_window" in c for c in c_small)
     assert {c.get("chunk_window") for c in c_large} >= {8, 10}
+    # a depth-1 plan has no adjoint register tile to choose
+    p1 = q.Plan(I.random_regular(200, 3, 1), 1)
+    assert not any("reg_bits_grad" in c for c in autotune.candidates(p1, 16, grad=True))
     cache = str(tmp_path / "tune.json")
     for plan, G, p, P in ((small, 2, 2, 16), (large, 1, 3, 4)):
         th = _params(np.stack([I.draw_params(p, P, 60 + g) for g in range(G)]))
