@@ -795,6 +795,32 @@ def test_cuda_graph_replay_matches_direct_calls(q):
     assert plan.device_status() == 0
 
 
+def test_cuda_graph_replay_of_a_depth1_plan(q, tmp_path):
+    """The headline's path: a depth-1 plan, autotuned, captured into a CUDA
+    graph and replayed with new parameters from the device and from pinned
+    host memory; energies and gradients equal those of direct calls (the same
+    kernels and tuning; only the order of the FP64 atomics may differ)."""
+    from paper_2101_10296_gb300 import autotune
+    graphs = [I.hypercube(8), I.torus(10, 10), I.random_regular(300, 3, 2), I.circulant(200, [1, 7, 23])]
+    G, P = len(graphs), 24
+    plan = q.Plan(graphs, 1)
+    assert plan.info()["depth1_kernel"] == 1
+    th_a = _params(np.stack([I.draw_params(1, P, 500 + g) for g in range(G)]))
+    th_b = np.stack([I.draw_params(1, P, 600 + g) for g in range(G)])
+    autotune.autotune(plan, th_a, grad=True, reps=1, cache_path=str(tmp_path / "tune.json"))
+    graph = plan.graph(th_a, grad=True)
+    host_b = torch.tensor(th_b).pin_memory()
+    for th in (th_a, host_b, th_a):
+        e, g = graph.run(th)
+        e, g = e.cpu().numpy(), g.cpu().numpy()
+        ref = th if th.is_cuda else _params(th_b)
+        e_ref, g_ref = plan.energy_grad(ref)
+        assert np.allclose(e, e_ref.cpu().numpy(), rtol=1e-12, atol=0)
+        assert np.allclose(g, g_ref.cpu().numpy(), rtol=1e-9, atol=1e-12)
+    graph.close()
+    assert plan.device_status() == 0
+
+
 def test_tuning_leaves_results_unchanged(q):
     plan, G = _mixed_plan(q)
     th = _params(np.stack([I.draw_params(3, 7, 30 + g) for g in range(G)]))
