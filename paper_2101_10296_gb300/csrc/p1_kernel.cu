@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? kP1GradMinBlocks : kP1Energy
             float e4[4] = {0.f, 0.f, 0.f, 0.f};
             float b4[4] = {0.f, 0.f, 0.f, 0.f};
             float g4[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 4
+#pragma unroll 16
             for (int b = 0; b < kP1Blocks; ++b) {
                 const uint2 rc = my_rec[b * 32 + lane];
                 const float wb = __uint_as_float(rc.y);
