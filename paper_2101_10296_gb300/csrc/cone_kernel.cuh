@@ -400,61 +400,84 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? (R <= 4 ? kGradMinBlocks : k
                     const int k = k_of(l);
                     const int kr = k < R ? k : R;
                     const float *kpl = kp + l * kRegKpow;
-                    // d/d beta_l = 2 sigma Im <r| sum_q X_q |s>, register qubits
-                    // on the untouched state first
-                    float d[NA / 4];
+                    float db = 0.f;
+                    if (PC > 0 && l == p - 1 && __all_sync(kFull, k == 2)) {
+                        // The last layer of a pruned cone mixes qubits 0 and 1 only, and
+                        // r = Z_0 Z_1 x here, so the two pair terms of each qubit coincide
+                        // (with p a compile-time constant; the run-time-p body stays small):
+                        // Im<r|X_0 + X_1|x> = 2 [Im(x0* x1) - Im(x2* x3) + Im(x0* x2) - Im(x1* x3)]
+                        // per group of four amplitudes (half the products; the 2 is in the stash).
 #pragma unroll
-                    for (int kk = 0; kk < NA / 4; ++kk) d[kk] = 0.f;
+                        for (int kk = 0; kk < NA / 4; ++kk) {
+                            const float2 a = x[4 * kk], b = x[4 * kk + 1], c = x[4 * kk + 2], e = x[4 * kk + 3];
+                            float d = 0.f;
+                            acc_imconj(d, a, b);
+                            acc_imconj(d, a, c);
+                            d = fmaf(-c.x, e.y, d);
+                            d = fmaf(c.y, e.x, d);
+                            d = fmaf(-b.x, e.y, d);
+                            d = fmaf(b.y, e.x, d);
+                            db = fmaf(wk[kk], d, db);
+                        }
+                        db *= 2.f;
+                        if (l > 0) mix_reg_fixed<R, 2>(x, -tau);
+                        mix_reg_fixed<R, 2>(r, -tau);
+                    } else {
+                        // d/d beta_l = 2 sigma Im <r| sum_q X_q |s>, register qubits
+                        // on the untouched state first
+                        float d[NA / 4];
 #pragma unroll
-                    for (int q = 0; q < R; ++q) {
-                        if (q < k) {
+                        for (int kk = 0; kk < NA / 4; ++kk) d[kk] = 0.f;
+#pragma unroll
+                        for (int q = 0; q < R; ++q) {
+                            if (q < k) {
+#pragma unroll
+                                for (int i = 0; i < NA; ++i) {
+                                    if (i & (1 << q)) continue;
+                                    const int i2 = i | (1 << q);
+                                    acc_imconj(d[i >> 2], r[i], x[i2]);
+                                    acc_imconj(d[i >> 2], r[i2], x[i]);
+                                }
+                            }
+                        }
+#pragma unroll
+                        for (int kk = 0; kk < NA / 4; ++kk) db = fmaf(wk[kk], d[kk], db);
+                        // lane qubits: each term is taken after the lane qubits before
+                        // it were undone, which scales it by (1 + tau^2) each; kappa^2
+                        // per undone qubit takes that back out
+#pragma unroll 1
+                        for (int Lb = 0; Lb < kLaneBits; ++Lb) {
+                            const bool mine = (R + Lb) < k;
+                            if (!__any_sync(kFull, mine)) break;
+                            const int m = 1 << Lb;
+                            float e4[NA / 4];
+#pragma unroll
+                            for (int kk = 0; kk < NA / 4; ++kk) e4[kk] = 0.f;
 #pragma unroll
                             for (int i = 0; i < NA; ++i) {
-                                if (i & (1 << q)) continue;
-                                const int i2 = i | (1 << q);
-                                acc_imconj(d[i >> 2], r[i], x[i2]);
-                                acc_imconj(d[i >> 2], r[i2], x[i]);
+                                float2 xo, ro;
+                                xo.x = __shfl_xor_sync(kFull, x[i].x, m);
+                                xo.y = __shfl_xor_sync(kFull, x[i].y, m);
+                                ro.x = __shfl_xor_sync(kFull, r[i].x, m);
+                                ro.y = __shfl_xor_sync(kFull, r[i].y, m);
+                                if (mine) {
+                                    acc_imconj(e4[i >> 2], r[i], xo);
+                                    x[i] = bfly(x[i], xo, -tau);
+                                    r[i] = bfly(r[i], ro, -tau);
+                                }
                             }
-                        }
-                    }
-                    float db = 0.f;
-#pragma unroll
-                    for (int kk = 0; kk < NA / 4; ++kk) db = fmaf(wk[kk], d[kk], db);
-                    // lane qubits: each term is taken after the lane qubits before
-                    // it were undone, which scales it by (1 + tau^2) each; kappa^2
-                    // per undone qubit takes that back out
-#pragma unroll 1
-                    for (int Lb = 0; Lb < kLaneBits; ++Lb) {
-                        const bool mine = (R + Lb) < k;
-                        if (!__any_sync(kFull, mine)) break;
-                        const int m = 1 << Lb;
-                        float e4[NA / 4];
-#pragma unroll
-                        for (int kk = 0; kk < NA / 4; ++kk) e4[kk] = 0.f;
-#pragma unroll
-                        for (int i = 0; i < NA; ++i) {
-                            float2 xo, ro;
-                            xo.x = __shfl_xor_sync(kFull, x[i].x, m);
-                            xo.y = __shfl_xor_sync(kFull, x[i].y, m);
-                            ro.x = __shfl_xor_sync(kFull, r[i].x, m);
-                            ro.y = __shfl_xor_sync(kFull, r[i].y, m);
                             if (mine) {
-                                acc_imconj(e4[i >> 2], r[i], xo);
-                                x[i] = bfly(x[i], xo, -tau);
-                                r[i] = bfly(r[i], ro, -tau);
+                                float e = 0.f;
+#pragma unroll
+                                for (int kk = 0; kk < NA / 4; ++kk) e = fmaf(wk[kk], e4[kk], e);
+                                db = fmaf(e, kpl[Lb], db);
                             }
                         }
-                        if (mine) {
-                            float e = 0.f;
-#pragma unroll
-                            for (int kk = 0; kk < NA / 4; ++kk) e = fmaf(wk[kk], e4[kk], e);
-                            db = fmaf(e, kpl[Lb], db);
-                        }
+                        // undo the register-qubit butterflies (psi only above layer 1: below
+                        // it psi is the layer-1 phase table itself, read back for d/d gamma_1)
+                        if (l > 0) mix_reg<R>(x, kr, -tau);
+                        mix_reg<R>(r, kr, -tau);
                     }
-                    // undo the register-qubit butterflies (psi only above layer 1: below
-                    // it psi is the layer-1 phase table itself, read back for d/d gamma_1)
-                    if (l > 0) mix_reg<R>(x, kr, -tau);
-                    mix_reg<R>(r, kr, -tau);
                     // the blocks' terms cancel across lanes: the grouped reduction
                     // adds the lanes' shares with compensation
                     stash(1 + p + l, jj, gw2 * sig * db);
