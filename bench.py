@@ -123,6 +123,9 @@ def algorithmic_flops(reps, p, grad, depth1=False):
         the butterfly on both states (8), on the co-state only in layer 1 (4);
         per layer the Im<lam|C|psi> term (5); undoing the phase on both states
         above layer 1 (12).
+    For register-resident cones (<= 9 inner qubits) at p <= 3 whose last layer
+    mixes qubits 0 and 1 only, that layer's pair terms are taken once (the
+    co-state is Z_u Z_v psi there): 2 per amplitude per qubit instead of 4.
     With depth1 (p = 1 plans on the depth-1 kernel, k_1 = 2 for every cone)
     the adjoint is A (4 + 8 + 3.75): the co-state's signs fold into the next
     FMAs (0); the two pair terms of a mixed qubit coincide once the co-state
@@ -139,6 +142,12 @@ def algorithmic_flops(reps, p, grad, depth1=False):
         flops = flops + A * (2 * ksum + 4 * ksum + 3.75)
     elif grad:
         flops = flops + A * (2 + 12 * (ksum - k[:, 0]) + 8 * k[:, 0] + 5 * p + 12 * (p - 1))
+        if p <= 3:
+            # the general register kernel (inner parts of <= 9 qubits) takes the last
+            # layer's pair terms once when it mixes qubits 0 and 1 only: 2 per
+            # amplitude per qubit instead of 4
+            last2 = (reps["n_inner"] <= 9) & (k[:, p - 1] == 2)
+            flops = flops - A * 4 * last2
     return float(flops.sum())
 
 

@@ -51,12 +51,13 @@ def test_flop_model_counts():
     a0, a1 = 81 * 2 ** 6, 3 * 2 ** 2
     assert fwd == a0 * (6 + 4 * 8 + 4) + a1 * (6 + 4 * 4 + 4)
     both = bench.algorithmic_flops(reps, 2, grad=True)
-    assert both == fwd + a0 * (2 + 12 * 2 + 8 * 6 + 10 + 12) + a1 * (2 + 12 * 2 + 8 * 2 + 10 + 12)
+    # both cones are register-resident with a last layer of qubits 0 and 1: pair terms once (-4)
+    assert both == fwd + a0 * (2 + 12 * 2 + 8 * 6 + 10 + 12 - 4) + a1 * (2 + 12 * 2 + 8 * 2 + 10 + 12 - 4)
     # depth 1: blocks of 4 amplitudes mixed on qubits u, v
     r1 = {"n_inner": np.array([2, 2]), "n_blocks": np.array([9, 169]), "mix_qubits": np.array([[2], [2]])}
     a = 4 * (9 + 169)
     assert bench.algorithmic_flops(r1, 1, grad=False) == a * 12
-    assert bench.algorithmic_flops(r1, 1, grad=True) == a * (12 + 2 + 16 + 5)
+    assert bench.algorithmic_flops(r1, 1, grad=True) == a * (12 + 2 + 16 + 5 - 4)
     assert bench.algorithmic_flops(r1, 1, grad=True, depth1=True) == a * (12 + 4 + 8 + 3.75)
 
 
