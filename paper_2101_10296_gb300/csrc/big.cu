@@ -298,22 +298,30 @@ __global__ void __launch_bounds__(128, 4) big_mix_kernel(const __grid_constant__
 // layer, which a small gradient (near a stationary point, a second
 // derivative times that shift) feels in full.  The lo parts (two more FMAs
 // per output) take the shift away; what remains is per-operation rounding.
-__global__ void big_prep_kernel(const double *params, int64_t GPp, int p, float4 *cs) {
+__global__ void big_prep_kernel(const double *params, int64_t GPp, int p, float4 *cs, float2 *fa) {
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < GPp; i += int64_t(gridDim.x) * blockDim.x) {
         const int64_t gj = i / p, l = i % p;
         double sn, c;
         sincos(params[gj * 2 * p + p + l], &sn, &c);
         const float ch = float(c), sh = float(sn);
         cs[i] = make_float4(ch, sh, float(c - double(ch)), float(sn - double(sh)));
+        if (fa && l == 0) {
+            // the first layer's factored coefficient: tan beta, or cot beta where
+            // |tan beta| > 1 (the same choice, and the same rounded hi part, as
+            // the register kernels' mixer table), with its FP32 rounding error
+            const double a = fabs(sn) > fabs(c) ? c / sn : sn / c;
+            const float ah = float(a);
+            fa[gj] = make_float2(ah, float(a - double(ah)));
+        }
     }
 }
 
 }  // namespace
 
-cudaError_t launch_big_prep(const double *params, int64_t GP, int p, float4 *cs, cudaStream_t s) {
+cudaError_t launch_big_prep(const double *params, int64_t GP, int p, float4 *cs, float2 *fa, cudaStream_t s) {
     const int64_t n = GP * p;
     int blocks = int(std::min<int64_t>((n + 255) / 256, 1024));
-    big_prep_kernel<<<blocks < 1 ? 1 : blocks, 256, 0, s>>>(params, n, p, cs);
+    big_prep_kernel<<<blocks < 1 ? 1 : blocks, 256, 0, s>>>(params, n, p, cs, fa);
     return cudaGetLastError();
 }
 

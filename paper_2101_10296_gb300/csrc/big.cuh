@@ -57,6 +57,8 @@ struct BigLaunch {
     int64_t item0, n_items;   // items (cone, point, shell block) of this wave
     const float2 *lut;        // [G][P][p][cmax1]
     const float4 *cs;         // [G][P][p] (cos beta, sin beta, and their FP32 rounding errors)
+    const float2 *fa;         // [G][P] the first layer's factored coefficient as FP32 hi + lo
+                              // (adjoint passes), or null: the hi part alone (see first_mix)
     const float2 *mix;        // [G][P][p] (tau, flip) and
     const float *kpow;        // [G][P][p][kKpow] kappa^(2k): the register kernels' mixer tables
     float2 *psi, *lam;        // scratch: n_items blocks of 2^n_in
@@ -76,7 +78,7 @@ struct BigLaunch {
 // cone, point by point, shell block by shell block.
 std::vector<BigPass> big_forward_passes(int n_in, int p, const int32_t *k);
 std::vector<BigPass> big_grad_passes(int n_in, int p, const int32_t *k);
-cudaError_t launch_big_prep(const double *params, int64_t GP, int p, float4 *cs, cudaStream_t s);
+cudaError_t launch_big_prep(const double *params, int64_t GP, int p, float4 *cs, float2 *fa, cudaStream_t s);
 cudaError_t launch_big_pass(const BigLaunch &a, bool grad, int grid, cudaStream_t s);
 int big_grid(bool grad);
 

@@ -52,17 +52,28 @@ namespace {
 // and every derivative term is taken either before any of the first mixer
 // is undone or after all of it, so (D'D = 1 / kappa^2 per qubit) nothing else
 // changes.
-template <bool B, bool INV>
-__device__ __forceinline__ float2 fmix(float2 me, float2 o, float a) {
-    if (!B) return INV ? make_float2(fmaf(-a, o.y, me.x), fmaf(a, o.x, me.y))
-                       : make_float2(fmaf(a, o.y, me.x), fmaf(-a, o.x, me.y));
-    return INV ? make_float2(fmaf(a, me.x, -o.y), fmaf(a, me.y, o.x))
-               : make_float2(fmaf(a, me.x, o.y), fmaf(a, me.y, -o.x));
+//
+// With LO the coefficient is a + alo (FP32 hi and lo parts of the FP64 value),
+// one FMA more per output: a single FP32 a is tan or cot of a slightly
+// different angle (|delta beta| ~ 1e-8), which moves the gradient by the
+// Hessian times that shift -- as large as the whole 1e-4 tolerance at points
+// where |grad E| ~ 1e-3 |E|.  The adjoint's passes use it; the energy's need
+// not (E moves by grad E . delta beta).
+template <bool B, bool INV, bool LO>
+__device__ __forceinline__ float2 fmix(float2 me, float2 o, float a, float alo) {
+    if (!B) {
+        const float ox = LO ? fmaf(INV ? -alo : alo, o.y, me.x) : me.x;
+        const float oy = LO ? fmaf(INV ? alo : -alo, o.x, me.y) : me.y;
+        return INV ? make_float2(fmaf(-a, o.y, ox), fmaf(a, o.x, oy)) : make_float2(fmaf(a, o.y, ox), fmaf(-a, o.x, oy));
+    }
+    const float px = LO ? fmaf(alo, me.x, INV ? -o.y : o.y) : (INV ? -o.y : o.y);
+    const float py = LO ? fmaf(alo, me.y, INV ? o.x : -o.x) : (INV ? o.x : -o.x);
+    return make_float2(fmaf(a, me.x, px), fmaf(a, me.y, py));
 }
 
 // D (or D') on register bits [r0, r1).
-template <int NR, bool B, bool INV>
-__device__ __forceinline__ void fmix_regs(float2 (&x)[NR], int r0, int r1, float a) {
+template <int NR, bool B, bool INV, bool LO>
+__device__ __forceinline__ void fmix_regs(float2 (&x)[NR], int r0, int r1, float a, float alo) {
 #pragma unroll
     for (int rb = 0; (1 << rb) < NR; ++rb) {
         if (rb >= r0 && rb < r1) {
@@ -71,16 +82,16 @@ __device__ __forceinline__ void fmix_regs(float2 (&x)[NR], int r0, int r1, float
                 if (i & (1 << rb)) continue;
                 const int i2 = i | (1 << rb);
                 const float2 u = x[i], v = x[i2];
-                x[i] = fmix<B, INV>(u, v, a);
-                x[i2] = fmix<B, INV>(v, u, a);
+                x[i] = fmix<B, INV, LO>(u, v, a, alo);
+                x[i2] = fmix<B, INV, LO>(v, u, a, alo);
             }
         }
     }
 }
 
 // D (or D') on lane bits [0, nb).
-template <int NR, bool B, bool INV>
-__device__ __forceinline__ void fmix_lanes(float2 (&x)[NR], int nb, float a) {
+template <int NR, bool B, bool INV, bool LO>
+__device__ __forceinline__ void fmix_lanes(float2 (&x)[NR], int nb, float a, float alo) {
     for (int lb = 0; lb < nb; ++lb) {
         const int m = 1 << lb;
 #pragma unroll
@@ -88,31 +99,16 @@ __device__ __forceinline__ void fmix_lanes(float2 (&x)[NR], int nb, float a) {
             float2 o;
             o.x = __shfl_xor_sync(kFull, x[i].x, m);
             o.y = __shfl_xor_sync(kFull, x[i].y, m);
-            x[i] = fmix<B, INV>(x[i], o, a);
+            x[i] = fmix<B, INV, LO>(x[i], o, a, alo);
         }
     }
 }
 
-template <int NR, bool INV>
-__device__ __forceinline__ void first_mix_regs(float2 (&x)[NR], int r0, int r1, float a, bool b) {
-    if (b)
-        fmix_regs<NR, true, INV>(x, r0, r1, a);
-    else
-        fmix_regs<NR, false, INV>(x, r0, r1, a);
-}
-
-template <int NR, bool INV>
-__device__ __forceinline__ void first_mix_lanes(float2 (&x)[NR], int nb, float a, bool b) {
-    if (b)
-        fmix_lanes<NR, true, INV>(x, nb, a);
-    else
-        fmix_lanes<NR, false, INV>(x, nb, a);
-}
-
-// The first layer's a, form (b: the a I - i X form) and kappa^(2 n_in) of one
-// (graph, point), from the register kernels' mixer tables.
+// The first layer's a (hi and lo), form (b: the a I - i X form) and
+// kappa^(2 n_in) of one (graph, point): a and the form from the register
+// kernels' mixer tables, the lo part from L.fa where the launch has it.
 struct FirstMix {
-    float a, k2n;
+    float a, alo, k2n;
     bool b;
 };
 __device__ __forceinline__ FirstMix first_mix(const BigLaunch &L, int64_t gj, int n_in) {
@@ -120,6 +116,7 @@ __device__ __forceinline__ FirstMix first_mix(const BigLaunch &L, int64_t gj, in
     FirstMix f;
     f.b = m.y != 0.f;
     f.a = f.b ? -m.x : m.x;  // flip form: tau = -cot beta
+    f.alo = L.fa ? __ldg(L.fa + gj).y : 0.f;
     f.k2n = __ldg(L.kpow + gj * L.p * kKpow + n_in);
     return f;
 }
@@ -130,8 +127,37 @@ __device__ __forceinline__ FirstMix layer_mix(const BigLaunch &L, int64_t gj, in
     FirstMix f;
     f.b = m.y != 0.f;
     f.a = f.b ? -m.x : m.x;
+    f.alo = 0.f;
     f.k2n = __ldg(L.kpow + (gj * L.p + l) * kKpow + k);
     return f;
+}
+
+template <int NR, bool INV>
+__device__ __forceinline__ void first_mix_regs(float2 (&x)[NR], int r0, int r1, const FirstMix &f) {
+    if (f.alo != 0.f) {
+        if (f.b)
+            fmix_regs<NR, true, INV, true>(x, r0, r1, f.a, f.alo);
+        else
+            fmix_regs<NR, false, INV, true>(x, r0, r1, f.a, f.alo);
+    } else if (f.b) {
+        fmix_regs<NR, true, INV, false>(x, r0, r1, f.a, 0.f);
+    } else {
+        fmix_regs<NR, false, INV, false>(x, r0, r1, f.a, 0.f);
+    }
+}
+
+template <int NR, bool INV>
+__device__ __forceinline__ void first_mix_lanes(float2 (&x)[NR], int nb, const FirstMix &f) {
+    if (f.alo != 0.f) {
+        if (f.b)
+            fmix_lanes<NR, true, INV, true>(x, nb, f.a, f.alo);
+        else
+            fmix_lanes<NR, false, INV, true>(x, nb, f.a, f.alo);
+    } else if (f.b) {
+        fmix_lanes<NR, true, INV, false>(x, nb, f.a, 0.f);
+    } else {
+        fmix_lanes<NR, false, INV, false>(x, nb, f.a, 0.f);
+    }
 }
 
 // exp(-i beta X) on register qubits [0, nbits) (nbits <= log2 NR).
@@ -319,8 +345,8 @@ __global__ void __launch_bounds__(128, GRAD ? QAOA_SPLIT_GRAD_BLOCKS : 3) split_
         // |psi|^2 = 2^-n kappa_1^(2 n_in) |x|^2 (the first mixer's factored form)
         float sig = __int_as_float((127 - C->n) << 23) * f1.k2n;
         // first mixer on the core qubits
-        first_mix_regs<NR, false>(x, 0, RB, f1.a, f1.b);
-        first_mix_lanes<NR, false>(x, 5, f1.a, f1.b);
+        first_mix_regs<NR, false>(x, 0, RB, f1);
+        first_mix_lanes<NR, false>(x, 5, f1);
         for (int l = 1; l < p; ++l) {
             const float2 *__restrict__ lt = lut + l * L.cmax1;
 #pragma unroll
@@ -332,8 +358,8 @@ __global__ void __launch_bounds__(128, GRAD ? QAOA_SPLIT_GRAD_BLOCKS : 3) split_
                 if (kl > RB) mix_lanes<NR>(x, kl - RB, c_s);
             } else {  // the energy: the factored form, two FMAs per output, kappa^(2 k_l) into sigma
                 const FirstMix fl = layer_mix(L, gj, l, kl);
-                first_mix_regs<NR, false>(x, 0, kl < RB ? kl : RB, fl.a, fl.b);
-                if (kl > RB) first_mix_lanes<NR, false>(x, kl - RB, fl.a, fl.b);
+                first_mix_regs<NR, false>(x, 0, kl < RB ? kl : RB, fl);
+                if (kl > RB) first_mix_lanes<NR, false>(x, kl - RB, fl);
                 sig *= fl.k2n;
             }
         }
@@ -384,8 +410,8 @@ __global__ void __launch_bounds__(128, GRAD ? QAOA_SPLIT_GRAD_BLOCKS : 3) split_
             // O = -1/2 Z_0 Z_1, and <psi|O X_q|psi> is real for every q other
             // than 0 and 1 (X_q and O commute), so only those two contribute.
             add_gp(xterms<NR>(x, r, p > 1), wgt2, L.grad, gj * 2 * p + p);
-            first_mix_regs<NR, true>(r, 0, RB, f1.a, f1.b);
-            first_mix_lanes<NR, true>(r, 5, f1.a, f1.b);
+            first_mix_regs<NR, true>(r, 0, RB, f1);
+            first_mix_lanes<NR, true>(r, 5, f1);
 #pragma unroll
             for (int i = 0; i < NR; ++i) sp[i << 5] = r[i];
         }
@@ -430,9 +456,9 @@ __global__ void __launch_bounds__(128, MODE == kOuterGen ? 4 : 3) split_outer_ke
         }
         if (MODE == kOuterMix) {
             if (L.sign > 0)
-                first_mix_regs<32, false>(x, r0, r1, f1.a, f1.b);
+                first_mix_regs<32, false>(x, r0, r1, f1);
             else
-                first_mix_regs<32, true>(x, r0, r1, f1.a, f1.b);
+                first_mix_regs<32, true>(x, r0, r1, f1);
         } else {
             const float2 *__restrict__ lut = L.lut + gj * p * L.cmax1;  // first layer's phase table
             float mult = 1.f;
@@ -458,9 +484,9 @@ __global__ void __launch_bounds__(128, MODE == kOuterGen ? 4 : 3) split_outer_ke
             if (MODE == kOuterGen) {
 #pragma unroll
                 for (int i = 0; i < 32; ++i) x[i] = __ldg(lut + __popcll(lo[i & 3] ^ hi[i >> 2]));
-                first_mix_regs<32, false>(x, r0, r1, f1.a, f1.b);
+                first_mix_regs<32, false>(x, r0, r1, f1);
             } else {  // kOuterFirst: x holds lambda
-                first_mix_regs<32, true>(x, r0, r1, f1.a, f1.b);
+                first_mix_regs<32, true>(x, r0, r1, f1);
                 // the outer qubits' mixer terms vanish at p = 1, where the first
                 // layer is the last (only qubits 0 and 1 contribute there)
                 const bool outer_terms = p > 1;
@@ -636,9 +662,9 @@ __device__ __forceinline__ void chunk_round(float2 *__restrict__ sm, int n_el, i
             for (int i = 0; i < NR; ++i) x[i] = sm[sidx(sb | (i << pos), rd_swz)];
         }
         if (inv)
-            first_mix_regs<NR, true>(x, 0, G, f.a, f.b);
+            first_mix_regs<NR, true>(x, 0, G, f);
         else
-            first_mix_regs<NR, false>(x, 0, G, f.a, f.b);
+            first_mix_regs<NR, false>(x, 0, G, f);
 #pragma unroll
         for (int i = 0; i < NR; ++i) sm[sidx(sb | (i << pos), wr_swz)] = x[i];
     }

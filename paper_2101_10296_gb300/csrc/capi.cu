@@ -282,9 +282,14 @@ cudaError_t run_big(const qaoa_device_plan *d, const qaoa_plan *plan, int64_t P,
     qaoa_device_plan *dm = const_cast<qaoa_device_plan *>(d);
     const int p = plan->p;
     float4 *cs = nullptr;
+    float2 *fa = nullptr;  // the adjoint's first-layer coefficient in hi + lo
     cudaError_t e = cudaMallocAsync(&cs, size_t(plan->n_graphs) * P * p * sizeof(float4), s);
     if (e != cudaSuccess) return e;
-    e = launch_big_prep(params, int64_t(plan->n_graphs) * P, p, cs, s);
+    if (grad && (e = cudaMallocAsync(&fa, size_t(plan->n_graphs) * P * sizeof(float2), s)) != cudaSuccess) {
+        cudaFreeAsync(cs, s);
+        return e;
+    }
+    e = launch_big_prep(params, int64_t(plan->n_graphs) * P, p, cs, fa, s);
     dm->all_launches += 1;
     const bool g = grad != nullptr;
     const int grid = big_grid(g);
@@ -309,6 +314,7 @@ cudaError_t run_big(const qaoa_device_plan *d, const qaoa_plan *plan, int64_t P,
         B.cmax1 = d->cmax1;
         B.lut = lut;
         B.cs = cs;
+        B.fa = fa;
         B.mix = mix;
         B.kpow = kpow;
         B.psi = scratch;
@@ -337,6 +343,7 @@ cudaError_t run_big(const qaoa_device_plan *d, const qaoa_plan *plan, int64_t P,
         cudaFreeAsync(scratch, s);
     }
     cudaFreeAsync(cs, s);
+    if (fa) cudaFreeAsync(fa, s);
     return e;
 }
 

@@ -181,7 +181,7 @@ extern "C" int qaoa_energy_noalloc(const qaoa_plan *plan, int64_t n_points, cons
     }
     // large-state cones: waves sized to the room left in the array
     if (e == cudaSuccess && !d->big.empty()) {
-        e = launch_big_prep(params_dev, int64_t(GP), p, cs, s);
+        e = launch_big_prep(params_dev, int64_t(GP), p, cs, nullptr, s);
         const int grid = big_grid(false);
         int64_t launches = 0;
         for (const BigShape &bs : d->big) {
@@ -200,6 +200,7 @@ extern "C" int qaoa_energy_noalloc(const qaoa_plan *plan, int64_t n_points, cons
             B.cmax1 = d->cmax1;
             B.lut = lut;
             B.cs = cs;
+            B.fa = nullptr;
             B.mix = mix;
             B.kpow = kpow;
             B.psi = reinterpret_cast<float2 *>(blocks);

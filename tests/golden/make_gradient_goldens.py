@@ -32,6 +32,7 @@ term and gradient of that cone at one point.
 
 Run once on a CPU (it takes about an hour; the 28-qubit cone needs ~30 GB):
     python tests/golden/make_gradient_goldens.py [near|full|all]
+``near`` computes only the cases not yet in near_stationary.json and keeps the rest.
 """
 from __future__ import annotations
 
@@ -73,6 +74,12 @@ def near_cases():
     out.append(("C30(1,2)", ("circulant", [30, [1, 2]]), 4, circulant_orbits(n, e), None))
     n, e = I.complete_bipartite(8, 8)
     out.append(("K8,8", ("complete_bipartite", [8, 8]), 3, np.zeros(len(e), dtype=np.int64), None))
+    # p = 3 default plans on the core-tile schedule: 15-qubit cones with 11 inner
+    # qubits, and 20-qubit cones with 14 (later layers mix at most nine qubits)
+    for nn, jumps in ((30, [1, 2]), (40, [1, 3])):
+        n, e = I.circulant(nn, jumps)
+        name = f"C{nn}({','.join(str(j) for j in jumps)})p3"
+        out.append((name, ("circulant", [nn, jumps]), 3, circulant_orbits(n, e), None))
     return out
 
 
@@ -123,12 +130,20 @@ def _near_job(args):
     return th, en, g
 
 
-def make_near():
+def make_near(only_missing=True):
+    """Computes the cases not yet in near_stationary.json (all of them with
+    only_missing=False) and writes the file with every case."""
+    path = os.path.join(HERE, "near_stationary.json")
     rows = []
+    if only_missing and os.path.exists(path):
+        rows = json.load(open(path))["rows"]
+    have = {r["case"] for r in rows}
     for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[var] = "1"
     pool = get_context("spawn").Pool(os.cpu_count() or 1)
     for k, (name, spec, p, oid, star) in enumerate(near_cases()):
+        if name in have:
+            continue
         t0 = time.time()
         graph = build(spec)
         m = len(graph[1])
@@ -150,7 +165,7 @@ def make_near():
                     "(|grad E| = rho |E|); written by tests/golden/make_gradient_goldens.py from oracle/ only",
            "rhos": list(RHOS), "orbits": "Q_d, K_{a,b}: one orbit; circulants: one orbit per jump (rotations)",
            "rows": rows}
-    with open(os.path.join(HERE, "near_stationary.json"), "w") as f:
+    with open(path, "w") as f:
         json.dump(doc, f, indent=1)
 
 

@@ -1097,14 +1097,16 @@ def _build(spec):
 _SCHEDULES = {"register": {}, "core-tile": {"full_cone": True}, "general": {"full_cone": True, "big_general": True}}
 
 
-@pytest.mark.parametrize("case", ["Q8", "Q9", "Q10", "C30(1,2)"])
+@pytest.mark.parametrize("case", ["Q8", "Q9", "Q10", "C30(1,2)", "C30(1,2)p3", "C40(1,3)p3"])
 def test_gradient_at_near_stationary_points(q, case):
     """Six points near a local maximum of E (|grad E| = 1e-3 |E|, where the
     derivative sums cancel to ~1e-3 of their terms), FP64 oracle values from
     tests/golden/near_stationary.json: energy and gradient of every schedule
     that takes the case, at the unchanged tolerances.  C_30(1,2) at p = 4 is a
     default (pruned) plan whose later layers mix more qubits than a core tile
-    holds, so its gradient runs on the general schedule.  (The golden file
+    holds, so its gradient runs on the general schedule; C_30(1,2) and C_40(1,3)
+    at p = 3 are default plans on the core-tile schedule (inner parts of 11
+    and 14 qubits, later layers of at most nine).  (The golden file
     also holds points at |grad E| = 2e-4 |E| and the case K_{8,8} at p = 3:
     there the FP32 state's own rounding, correlated over the many equal
     amplitudes of a highly symmetric cone, exceeds 1e-4 of the gradient.)"""
@@ -1115,6 +1117,8 @@ def test_gradient_at_near_stationary_points(q, case):
     theta = np.array([r["theta"] for r in rows])
     if case.startswith("Q"):
         schedules = _SCHEDULES
+    elif case.endswith("p3"):
+        schedules = {"core-tile": {}}
     else:
         schedules = {"default": {}}
     for name, kw in schedules.items():
@@ -1123,7 +1127,7 @@ def test_gradient_at_near_stationary_points(q, case):
         if name == "register":
             assert info["n_big"] == 0
         elif name == "core-tile":
-            assert info["n_big"] == 1 and info["n_big_general_grad"] == 0
+            assert info["n_big"] >= 1 and info["n_big_general_grad"] == 0
         else:
             assert info["n_big"] >= 1 and info["n_big_general_grad"] == info["n_big"]
         runs = {name: plan.energy_grad(_params(theta))}
