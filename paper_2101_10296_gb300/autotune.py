@@ -5,7 +5,7 @@ time (coordinate descent, each group timed with the best values found for
 the groups before it):
 
 1. the number of parameter points a warp task of the register kernels
-   evaluates (1 .. 32 while the phase tables fit) and the persistent grid's
+   evaluates (1, 2, 4, 8, 12, 16, 32 while the phase tables fit) and the persistent grid's
    blocks per SM;
 2. with gradients and register-resident cones on the general register
    kernel (not depth-1 plans): the adjoint register kernel's tile,
@@ -57,7 +57,7 @@ def candidate_groups(plan, n_points, grad):
     of lists of partial tunings (dicts over qaoa_tuning_t's fields)."""
     info = plan.info()
     row_bytes = info["p"] * (info["max_edges"] + 1) * 8
-    jpts = [j for j in (1, 2, 4, 8, 16, 32) if j <= max(1, n_points) and j * row_bytes * 4 <= 48 * 1024]
+    jpts = [j for j in (1, 2, 4, 8, 12, 16, 32) if j <= max(1, n_points) and j * row_bytes * 4 <= 48 * 1024]
     groups = [[{"points_per_task": j, "blocks_per_sm": b} for j in jpts for b in (0, 1, 2)]]
     # the adjoint register tile matters only to the general register kernel
     # (depth-1 plans run their register cones on the depth-1 kernel)

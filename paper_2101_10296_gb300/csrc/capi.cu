@@ -426,7 +426,7 @@ int run(const qaoa_plan *plan, int64_t n_points, const double *params, double *e
             const int64_t row = int64_t(d->cmax1 + 1) * int64_t(sizeof(float2));
             const int64_t fixed = int64_t(reg_p1_smem_bytes(0, d->cmax1, g)) / (kRegBlock / 32);
             const int blocks = g ? kP1GradMinBlocks : kP1EnergyMinBlocks;
-            const int64_t fit = (int64_t(227) * 1024 / (blocks * (kRegBlock / 32)) - fixed) / row;
+            const int64_t fit = (int64_t(smem_per_block(blocks)) / (kRegBlock / 32) - fixed) / row;
             const int64_t cap = (int64_t(kRegMaxSmem) / (kRegBlock / 32) - fixed) / row;
             int64_t jpt = d->points_per_task;
             if (jpt <= 0) {

@@ -146,6 +146,10 @@ cudaError_t launch_cut_table(const DevCone *cone, uint8_t *out, int32_t n, int32
 // occupancy-sized persistent grids for a given dynamic shared memory size
 int reg_energy_grid(bool wide, size_t smem);
 int sm_count();  // multiprocessors of the current device (cached)
+// Dynamic shared memory a block may use when `blocks` blocks share one
+// multiprocessor of the current device: the multiprocessor's shared memory
+// split evenly, less what the hardware reserves per block (cached).
+int smem_per_block(int blocks);
 int reg_grad_grid(bool wide, size_t smem, int p, int rg);
 cudaError_t reg_grad_prepare();
 // Raises the register kernels' dynamic shared memory limit to kRegMaxSmem
@@ -207,10 +211,13 @@ constexpr int kP1GradMinBlocks = 6;
 constexpr int kP1EnergyMinBlocks = 8;
 // Dynamic shared memory of a depth-1 block: per warp jpt phase tables, jpt
 // (tau, kappa^4) pairs, the records of its 32 slots and the reduction buffer.
+// Points per reduction group of the depth-1 kernel (see reg_flush): four for
+// the adjoint, whose three outputs would otherwise take 3 KB per warp
+__host__ __device__ constexpr int reg_p1_group(bool grad) { return grad ? 4 : 8; }
 inline size_t reg_p1_smem_bytes(int jpt, int cmax1, bool grad) {
     return size_t(kRegBlock / 32) *
            (size_t(jpt) * (cmax1 + 1) * sizeof(float2) + size_t(kP1Blocks) * 32 * sizeof(uint2) +
-            size_t(reg_outputs(1, grad)) * reg_group(1, grad) * 32 * sizeof(float));
+            size_t(reg_outputs(1, grad)) * reg_p1_group(grad) * 32 * sizeof(float));
 }
 int reg_p1_grid(bool grad, size_t smem);
 cudaError_t reg_p1_prepare();

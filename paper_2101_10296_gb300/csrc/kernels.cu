@@ -30,6 +30,7 @@
 // exp(-i gamma c), tan and the kappa powers are computed in FP64 and rounded
 // once; lane partial sums are reduced across the warp in FP32 and
 // accumulated across warps, cones and orbits in FP64 (atomicAdd).
+#include <algorithm>
 #include <map>
 #include <set>
 #include <mutex>
@@ -140,6 +141,22 @@ int sm_count() {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cache[dev] = sms;
     return sms;
+}
+
+int smem_per_block(int blocks) {
+    static std::mutex mu;
+    static std::map<std::pair<int, int>, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find({dev, blocks});
+    if (it != cache.end()) return it->second;
+    int per_sm = 0, reserved = 0;
+    cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    const int v = std::max(0, per_sm / std::max(blocks, 1) - reserved);
+    cache[{dev, blocks}] = v;
+    return v;
 }
 
 cudaError_t launch_prep(const PrepArgs &a, cudaStream_t s) {

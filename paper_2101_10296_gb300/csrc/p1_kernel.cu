@@ -65,13 +65,25 @@ __device__ __forceinline__ void mix01(float2 (&x)[4], float tau) {
     x[3] = bfly(b, a, tau);
 }
 
+// Count byte a of w as the FP32 value 2^23 + c (its bit pattern is
+// 0x4B0000cc): one byte permute, and differences of two such values are
+// exact FP32 subtractions
+__device__ __forceinline__ uint32_t count_bits(uint32_t w, int a) { return __byte_perm(w, 0x4B000000u, 0x7540u | a); }
+
+// float2 at a 32-bit shared-memory address
+__device__ __forceinline__ float2 lds2(uint32_t addr) {
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];\n" : "=f"(v.x), "=f"(v.y) : "r"(addr));
+    return v;
+}
+
 template <bool GRAD>
 __global__ void __launch_bounds__(kRegBlock, GRAD ? kP1GradMinBlocks : kP1EnergyMinBlocks)
     reg_p1_kernel(const RegLaunch L) {
     extern __shared__ float2 s_tab[];
     constexpr int kWarps = kRegBlock / 32;
     constexpr int NOUT = reg_outputs(1, GRAD);
-    constexpr int G = reg_group(1, GRAD);
+    constexpr int G = reg_p1_group(GRAD);
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const RegWork &W = L.work;
@@ -109,7 +121,9 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? kP1GradMinBlocks : kP1Energy
         cp_async_wait_all();
         __syncwarp();  // the staged data are complete and visible to the warp
         for (int jj = 0; jj < jn; ++jj) {
-            const float2 *lut = my_tab + jj * cm1;
+            // address of entry c is lut0 + 8 (2^23 + c) (mod 2^32): the counts
+            // are read as 2^23 + c, see count_bits
+            const uint32_t lut0 = static_cast<uint32_t>(__cvta_generic_to_shared(my_tab + jj * cm1)) - (0x4B000000u << 3);
             const float2 tk = my_mix[jj];
             const float tau = tk.x;
             float e4[4] = {0.f, 0.f, 0.f, 0.f};
@@ -119,12 +133,12 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? kP1GradMinBlocks : kP1Energy
             for (int b = 0; b < kP1Blocks; ++b) {
                 const uint2 rc = my_rec[b * 32 + lane];
                 const float wb = __uint_as_float(rc.y);
-                int c[4];
+                uint32_t c[4];
                 float2 s[4], x[4];
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {
-                    c[a] = int((rc.x >> (8 * a)) & 0xffu);
-                    s[a] = lut[c[a]];
+                    c[a] = count_bits(rc.x, a);
+                    s[a] = lds2(lut0 + (c[a] << 3));
                     x[a] = s[a];
                 }
                 mix01(x, tau);
@@ -146,7 +160,8 @@ __global__ void __launch_bounds__(kRegBlock, GRAD ? kP1GradMinBlocks : kP1Energy
                     mix01(r, -tau);
                     float dg = 0.f;
 #pragma unroll
-                    for (int a = 1; a < 4; ++a) dg = fmaf(float(c[a] - c[0]), imconj(r[a], s[a]), dg);
+                    for (int a = 1; a < 4; ++a)
+                        dg = fmaf(__uint_as_float(c[a]) - __uint_as_float(c[0]), imconj(r[a], s[a]), dg);
                     g4[b & 3] = fmaf(wb, dg, g4[b & 3]);
                 }
             }
