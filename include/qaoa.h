@@ -384,8 +384,10 @@ int qaoa_device_status(const qaoa_plan *plan, int32_t *status);
  *   reg_bits_grad    register qubits per thread of the adjoint register
  *                    kernel, 4 or 5: a tile of 2^(bits + 5) amplitudes per
  *                    warp, 5 holding twice the amplitudes per thread at half
- *                    the resident blocks (default 4; which wins depends on
- *                    the plan, see autotune.py)
+ *                    the resident blocks (default: 5 when the plan's
+ *                    register work fills the GPU for at least four waves of
+ *                    8 warps per SM at 32 points per task, else 4; the
+ *                    autotuner times both)
  *   chunk_window     largest window of outer qubits a shared-memory chunk
  *                    pass of the large-state path mixes, 6..10 (default 10):
  *                    the 2^13-amplitude chunk is a window of w outer qubits

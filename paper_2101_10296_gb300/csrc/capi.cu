@@ -259,12 +259,18 @@ int ensure_uploaded(const qaoa_plan *plan) {
     return check_device(plan);
 }
 
-// Register qubits per thread of the adjoint kernel: the tuned value, else 4.
-// Which width wins depends on the plan (measured: 5 is 6% faster on random
-// cubic graphs at p = 2, whose cones have six inner qubits, but 14-25%
-// slower on tori with eight and on the p = 1 mix), so the autotuner picks it.
-int reg_bits_for(const qaoa_device_plan *d, int) {
-    return d->reg_bits_grad == 5 ? 5 : 4;
+// Register qubits per thread of the adjoint kernel: the tuned value, else by
+// the amount of work.  Five register qubits halve the lane exchanges but need
+// 255 registers (2 blocks of 128 threads per SM), so they win on plans that
+// keep the SMs busy for several waves (measured at p = 2: 10% faster on four
+// random cubic graphs of 2000 vertices, 9% on two random 4-regular ones) and
+// lose on small ones (11-28% slower on the 8x8 and 100x100 tori, one to three
+// cones).  The untuned choice takes 5 when the 5-qubit work list, at up to 32
+// points per warp task, gives at least four waves of 8 warps per SM.
+int reg_bits_for(const qaoa_device_plan *d, int64_t n_points) {
+    if (d->reg_bits_grad == 4 || d->reg_bits_grad == 5) return d->reg_bits_grad;
+    const int64_t tasks = d->reg_g[1].warps * ((n_points + 31) / 32);
+    return tasks >= int64_t(sm_count()) * 8 * 4 ? 5 : 4;
 }
 
 // Persistent grid: the occupancy-sized grid, or blocks_per_sm per SM if tuned
@@ -454,7 +460,7 @@ int run(const qaoa_plan *plan, int64_t n_points, const double *params, double *e
         {
             // one point's phase tables, mixer data and kappa powers
             const int64_t row_bytes = int64_t(p) * ((d->cmax1 + 1) * int64_t(sizeof(float2)) + kRegKpow * int64_t(sizeof(float)));
-            const int rgi = reg_bits_for(d, p) - 4;
+            const int rgi = reg_bits_for(d, n_points) - 4;
             const int64_t warps = grad ? d->reg_g[rgi].warps : d->reg_e.warps;
             int64_t jpt = d->points_per_task;
             if (jpt <= 0) {
@@ -476,7 +482,7 @@ int run(const qaoa_plan *plan, int64_t n_points, const double *params, double *e
         L.status = d->status;
         L.norm = norm && !grad ? 1 : 0;
         if (grad) {
-            const int rg = reg_bits_for(d, p);
+            const int rg = reg_bits_for(d, n_points);
             L.work = as_reg(d, d->reg_g[rg - 4]);
             if (L.work.warps > 0) {
                 int64_t grid = std::min<int64_t>(tuned_grid(d, reg_grad_grid(wide, smem, p, rg)),
