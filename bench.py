@@ -902,8 +902,10 @@ PROFILE_CASES = {
     "reg-mix48": "the benchmark workload (48-graph mix, p=1, 256 points): energy+grad",
     "reg-mix48-small": "the 48-graph mix, p=1, 16 points: energy+grad",
     "reg-mix48-p32": "the 48-graph mix, p=1, 32 points: energy+grad",
-    "reg-adjoint-rr3-n2000": "1 random 3-regular graph n=2000 (seed 1), p=2, 8 points: energy+grad",
-    "reg-adjoint-rr3-n2000-p64": "1 random 3-regular graph n=2000 (seed 1), p=2, 64 points: energy+grad",
+    "reg-adjoint-rr3-n2000": "1 random 3-regular graph n=2000 (seed 1), p=2, 8 points: energy+grad "
+                             "(5 register qubits per thread)",
+    "reg-adjoint-rr3-n2000-p64": "1 random 3-regular graph n=2000 (seed 1), p=2, 64 points: energy+grad "
+                                 "(5 register qubits per thread)",
     "reg-rr3-x4": "4 x rr3 n=2000, p=2, 64 points: energy+grad",
     "split-adjoint-rr3-n24": "1 random 3-regular graph n=24 (seed 1), p=3, 8 points: energy+grad",
     "split-adjoint-torus6": "6x6 torus, p=3, 2 points: energy+grad",
@@ -916,6 +918,7 @@ def run_case(name):
     import torch
     from paper_2101_10296_gb300 import inputs as I
     from paper_2101_10296_gb300 import qaoa
+    tuning = {}
     if name in ("reg-mix48", "reg-mix48-small", "reg-mix48-p32"):
         graphs, theta = workload()
         if name != "reg-mix48":
@@ -925,6 +928,9 @@ def run_case(name):
         graphs, theta = side_workload()
         p, grad, kw = 2, True, {}
     else:
+        if name.startswith("reg-adjoint-rr3-n2000"):
+            # the width the untuned plan of the 4-graph side workload takes
+            tuning = {"reg_bits_grad": 5}
         spec = {"reg-adjoint-rr3-n2000": ([I.random_regular(2000, 3, 1)], 2, 8, True, {}),
                 "reg-adjoint-rr3-n2000-p64": ([I.random_regular(2000, 3, 1)], 2, 64, True, {}),
                 "split-adjoint-rr3-n24": ([I.random_regular(24, 3, 1)], 3, 8, True, {}),
@@ -935,6 +941,8 @@ def run_case(name):
         theta = np.stack([I.draw_params(p, P, s + 1) for s in range(len(graphs))])
     plan = qaoa.Plan(graphs, p, **kw)
     plan.upload()
+    if tuning:
+        plan.set_tuning(**tuning)
     th = torch.tensor(theta, device="cuda")
     for _ in range(2):
         out = plan.energy_grad(th) if grad else plan.energy(th)
