@@ -36,6 +36,7 @@ as the paper extrapolates its infeasible runs in Sec. 5).
 from __future__ import annotations
 
 import argparse
+import datetime
 import hashlib
 import json
 import os
@@ -236,14 +237,21 @@ def large_state_measurement(device, flush, product=True):
 # -------------------------------------------------------------------- clocks
 
 class ClockSampler:
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi samples of the SM clock and the throttle reasons, every
+    period_ms, with their timestamps.  mark_start()/mark_end() bracket the
+    timed region; the summary uses the samples from its start on (the caller
+    keeps the same load running after the region until a few have arrived:
+    a timed region of a few milliseconds is shorter than the sampling period)."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
-    def __init__(self, index, period_ms=100):
+    def __init__(self, index, period_ms=50):
         self.index = index
         self.period_ms = period_ms
         self.proc = None
+        self.t0 = self.t1 = None
         # the raw samples go to $QAOA_BENCH_CLOCKS_DIR (default: the temp directory);
         # the JSON line carries their summary
         out_dir = os.environ.get("QAOA_BENCH_CLOCKS_DIR", tempfile.gettempdir())
@@ -276,27 +284,49 @@ class ClockSampler:
                 self.proc.kill()
             self.fh.close()
 
+    def mark_start(self):
+        self.t0 = datetime.datetime.now()
+
+    def mark_end(self):
+        self.t1 = datetime.datetime.now()
+
+    def _rows(self):
+        """(time, sm MHz, max sm MHz, active reasons) of every complete sample."""
+        rows = []
+        if not self.proc:
+            return rows
+        try:
+            lines = open(self.path).read().splitlines()
+        except OSError:
+            return rows
+        for line in lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 10:
+                continue
+            try:
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f")
+                sm, smax = float(f[2]), float(f[3])
+            except ValueError:
+                continue
+            rows.append((ts, sm, smax, {nm for nm, v in zip(self.REASONS, f[6:10]) if v.lower() == "active"}))
+        return rows
+
+    def count_since_start(self):
+        return sum(1 for r in self._rows() if self.t0 is None or r[0] >= self.t0)
+
     def summary(self):
         if not self.proc:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
-            f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                smax.append(float(f[2]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, f[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        if not sm:
+        rows = [r for r in self._rows() if self.t0 is None or r[0] >= self.t0]
+        if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        reasons = set().union(*(r[3] for r in rows))
+        inside = sum(1 for r in rows if self.t1 is None or r[0] <= self.t1)
+        return {"sm_mhz": statistics.median(r[1] for r in rows), "sm_max_mhz": max(r[2] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows), "samples_in_timed_region": inside,
+                "period_ms": self.period_ms,
+                "window": "from the start of the timed region through an untimed replay of the same step "
+                          "after it (the region is shorter than the sampling period)"}
 
 
 # --------------------------------------------------------------- CPU oracle
@@ -508,6 +538,7 @@ def run_ours(args, rank, world, local_rank):
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local_rank) as clk:
+        clk.mark_start()
         wall0 = time.perf_counter()
         for k in range(args.steps):
             flush.fill_(k & 0xFF)
@@ -516,6 +547,14 @@ def run_ours(args, rank, world, local_rank):
             ends[k].record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
+        clk.mark_end()
+        # the same load, untimed, until the sampler has caught up with the region (at most 1 s;
+        # polling nvidia-smi faster than this slows the host's launches, not the device's steps)
+        hold0 = time.perf_counter()
+        while clk.proc and clk.count_since_start() < 5 and time.perf_counter() - hold0 < 1.0:
+            for _ in range(8):
+                step()
+            torch.cuda.synchronize()
     clocks = clk.summary()
     if dist:
         dist.barrier()

@@ -62,16 +62,26 @@ def test_flop_model_counts():
 
 
 def test_clock_log_parser(tmp_path):
+    """Samples are read with their timestamps; those before the timed region's
+    start are left out, and those up to its end are counted as inside it."""
+    import datetime
     import bench
     c = bench.ClockSampler(0)
     c.path = str(tmp_path / "c.csv")
     c.proc = object()
     with open(c.path, "w") as f:
-        f.write("0, 1900, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active\n")
-        f.write("0, 1950, 2070, 950.2, 0x4, Not Active, Not Active, Not Active, Active\n")
-        f.write("0, 2000, 2070, 990.0, 0x0, Not Active, Not Active, Not Active, Not Active\n")
+        f.write("2026/12/03 10:00:00.000, 0, 1200, 2070, 300.0, 0x0, Not Active, Active, Not Active, Not Active\n")
+        f.write("2026/12/03 10:00:00.100, 0, 1900, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active\n")
+        f.write("2026/12/03 10:00:00.120, 0, 1950, 2070, 950.2, 0x4, Not Active, Not Active, Not Active, Active\n")
+        f.write("2026/12/03 10:00:00.140, 0, 2000, 2070, 990.0, 0x0, Not Active, Not Active, Not Active, Not Active\n")
+        f.write("2026/12/03 10:00:00.160, 0, 20")  # a sample still being written
+    s = c.summary()  # no region marked: every complete sample
+    assert s["samples"] == 4 and s["sm_mhz"] == 1925 and s["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
+    c.t0 = datetime.datetime(2026, 12, 3, 10, 0, 0, 50000)
+    c.t1 = datetime.datetime(2026, 12, 3, 10, 0, 0, 125000)
     s = c.summary()
     assert s["sm_mhz"] == 1950 and s["sm_max_mhz"] == 2070 and s["reasons"] == ["sw_power_cap"]
+    assert s["samples"] == 3 and s["samples_in_timed_region"] == 2 and c.count_since_start() == 3
 
 
 def test_oracle_sample_reports_parallel_and_one_core_rates():
