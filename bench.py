@@ -465,7 +465,8 @@ def timed_steps(fn, steps, warmup, flush, stream):
     """W warm-up calls, then K calls each between CUDA events on ``stream``
     with the L2 flush written before the first event; returns ms per call."""
     import torch
-    for _ in range(warmup):
+    for k in range(warmup):  # the same as a timed call, flush included
+        flush.fill_(k & 0xFF)
         fn()
     torch.cuda.synchronize()
     out = []
@@ -528,7 +529,8 @@ def run_ours(args, rank, world, local_rank):
     def step():
         return graph.run()
 
-    for _ in range(args.warmup):
+    for k in range(args.warmup):  # the same as a timed step, flush included
+        flush.fill_(k & 0xFF)
         step()
     torch.cuda.synchronize()
 
