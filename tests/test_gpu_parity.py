@@ -261,19 +261,21 @@ def test_depth1_kernel_edge_cases(q, P):
     """Depth-1 lists at their edges, against the FP64 oracle summed over every
     edge: an edgeless graph inside a batch (no blocks, energy 0), a single
     edge (one cone of one block: the graph's warp is almost all padding), a
-    path, isolated vertices, and a weighted star whose cones carry 54 cut-word
-    bits (weights 9: counts beyond one 32-bit word, up to 54 per byte);
-    1 point, and 13 points (a ragged last task)."""
+    path, isolated vertices, a weighted star whose cones carry 54 cut-word
+    bits (weights 9: counts beyond one 32-bit word, up to 54 per byte), and
+    one at the cap of 64 bits (8 edges of weight 8: counts 0..64, a phase
+    table of 65 entries); 1 point, and 13 points (a ragged last task)."""
     graphs = [(5, np.zeros((0, 2), dtype=np.int64)), (2, np.array([[0, 1]])), I.path(6),
-              (9, np.array([[0, 1], [1, 2], [6, 7]])), I.star(6)]
-    weights = [np.ones(len(e), dtype=np.int64) for _, e in graphs[:-1]] + [np.full(6, 9, dtype=np.int64)]
+              (9, np.array([[0, 1], [1, 2], [6, 7]])), I.star(6), I.star(8)]
+    weights = ([np.ones(len(e), dtype=np.int64) for _, e in graphs[:-2]] +
+               [np.full(6, 9, dtype=np.int64), np.full(8, 8, dtype=np.int64)])
     # seeds whose points all have |grad E| > 0.02 |E| (seed 70 puts a point of the
     # weighted star at 9 gamma = pi mod 2 pi, a stationary point, where the FP32
     # floor of the near-stationary tests applies instead)
     theta = np.stack([I.draw_params(1, P, 80 + k) for k in range(len(graphs))])
     plan = q.Plan(graphs, 1, weights=weights)
     info = plan.info()
-    assert info["depth1_kernel"] == 1 and info["max_edges"] == 6
+    assert info["depth1_kernel"] == 1 and info["max_edges"] == 8
     e, g = plan.energy_grad(_params(theta))
     e_only = plan.energy(_params(theta)).cpu().numpy()
     e, g = e.cpu().numpy(), g.cpu().numpy()
@@ -818,6 +820,34 @@ def test_cuda_graph_replay_of_a_depth1_plan(q, tmp_path):
         assert np.allclose(e, e_ref.cpu().numpy(), rtol=1e-12, atol=0)
         assert np.allclose(g, g_ref.cpu().numpy(), rtol=1e-9, atol=1e-12)
     graph.close()
+    assert plan.device_status() == 0
+
+
+@pytest.mark.parametrize("graph,signs", [
+    (I.random_regular(40, 3, 3), None),       # six inner qubits: one lane qubit at R = 5
+    (I.random_regular(16, 4, 2), None),       # eight inner qubits: three lane qubits at R = 5
+    (I.random_regular(30, 3, 4), (1, -1)),    # signed edges
+])
+def test_adjoint_register_widths_match_oracle(q, graph, signs):
+    """Both widths of the p = 2 adjoint register kernel (4 and 5 register
+    qubits per thread; an untuned plan picks one by its amount of work)
+    against the FP64 oracle's adjoint summed over every edge, at the 1x
+    gradient tolerance."""
+    n, edges = graph
+    w = None if signs is None else np.random.default_rng(6).choice(signs, len(edges))
+    p, P = 2, 2
+    theta = I.draw_params(p, P, 21)
+    refs = [O.orbit_grad_adjoint(n, edges, theta[j], p, np.arange(len(edges)), weights=w) for j in range(P)]
+    plan = q.Plan((n, edges), p, weights=w)
+    assert plan.info()["n_big"] == 0 and plan.info()["depth1_kernel"] == 0
+    for rb in (4, 5):
+        plan.set_tuning(reg_bits_grad=rb)
+        e, g = plan.energy_grad(_params(theta[None]))
+        e, g = e.cpu().numpy()[0], g.cpu().numpy()[0]
+        for j, (eref, gref) in enumerate(refs):
+            assert abs(e[j] - eref) <= E_REL_TOL * max(abs(eref), 1.0), (rb, j)
+            _check_grad(g[j], gref, energy=eref)
+    plan.set_tuning()
     assert plan.device_status() == 0
 
 

@@ -93,6 +93,12 @@ def test_weighted_input_errors_and_caps(qlib):
     with pytest.raises(qlib.QAOAError) as ei:
         qlib.Plan((n, edges), 1, weights=np.full(len(edges), 30))
     assert ei.value.code == qlib.QAOA_E_CONE_TOO_LARGE and "weight" in str(ei.value)
+    # the boundary: a star's cone holds all its edges; 8 x 8 = 64 bits fit, 5 x 13 = 65 do not
+    plan = qlib.Plan(I.star(8), 1, weights=np.full(8, 8))
+    assert plan.info()["max_edges"] == 8 and plan.info()["n_reps"] == 1
+    with pytest.raises(qlib.QAOAError) as ei:
+        qlib.Plan(I.star(5), 1, weights=np.full(5, 13))
+    assert ei.value.code == qlib.QAOA_E_CONE_TOO_LARGE and "65 > cap 64" in str(ei.value)
 
 
 def test_orbit_id_is_smallest_edge_of_orbit(qlib):
