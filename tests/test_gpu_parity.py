@@ -823,19 +823,22 @@ def test_cuda_graph_replay_of_a_depth1_plan(q, tmp_path):
     assert plan.device_status() == 0
 
 
-@pytest.mark.parametrize("graph,signs", [
-    (I.random_regular(40, 3, 3), None),       # six inner qubits: one lane qubit at R = 5
-    (I.random_regular(16, 4, 2), None),       # eight inner qubits: three lane qubits at R = 5
-    (I.random_regular(30, 3, 4), (1, -1)),    # signed edges
+@pytest.mark.parametrize("graph,p,signs", [
+    (I.random_regular(40, 3, 3), 2, None),       # six inner qubits: one lane qubit at R = 5
+    (I.random_regular(16, 4, 2), 2, None),       # eight inner qubits: three lane qubits at R = 5
+    (I.random_regular(30, 3, 4), 2, (1, -1)),    # signed edges
+    (I.cycle(24), 3, None),                      # depth 3 (compile-time): six inner qubits
+    (I.cycle(20), 4, None),                      # depth 4 (run-time depth): eight inner qubits
 ])
-def test_adjoint_register_widths_match_oracle(q, graph, signs):
-    """Both widths of the p = 2 adjoint register kernel (4 and 5 register
-    qubits per thread; an untuned plan picks one by its amount of work)
-    against the FP64 oracle's adjoint summed over every edge, at the 1x
-    gradient tolerance."""
+def test_adjoint_register_widths_match_oracle(q, graph, p, signs):
+    """Both widths of the adjoint register kernel (4 and 5 register qubits
+    per thread; an untuned plan picks one by its amount of work) against the
+    FP64 oracle's adjoint summed over every edge, at the 1x gradient
+    tolerance, at p = 2, 3 and 4 (the depth as a compile-time constant and
+    read at run time)."""
     n, edges = graph
     w = None if signs is None else np.random.default_rng(6).choice(signs, len(edges))
-    p, P = 2, 2
+    P = 2
     theta = I.draw_params(p, P, 21)
     refs = [O.orbit_grad_adjoint(n, edges, theta[j], p, np.arange(len(edges)), weights=w) for j in range(P)]
     plan = q.Plan((n, edges), p, weights=w)
