@@ -431,6 +431,49 @@ def test_big_full_cone_matches_register_path(q, graph, p):
     assert full.device_status() == 0
 
 
+def test_cone_at_the_qubit_cap(q):
+    """The 8x8 torus at p = 3: one 32-qubit cone (the cap), 18 inner qubits,
+    1,656 merged shell blocks of 2^18 amplitudes.  An FP64 state of 2^32
+    amplitudes is beyond the oracle, so what holds at any size checks it:
+    unit norm (Sec. 2.2: the evolution is unitary), energies within
+    [0, |E|], periods 2 pi in each gamma (integer cut values) and pi/2 in
+    each beta (e^{-i(beta + pi/2) X} = -i X e^{-i beta X}, and the global
+    flip leaves every Z_u Z_v unchanged; the kernel takes that X into its
+    flip words), the adjoint gradient against central differences of the
+    energy (FP32 energies: h = 1e-3, 2e-3 norm-wise), and the general
+    large-state schedule (other kernels) against the default core-tile one."""
+    n, edges = I.torus(8, 8)
+    p = 3
+    plan = q.Plan((n, edges), p)
+    info = plan.info()
+    assert info["n_reps"] == 1 and info["max_qubits"] == 32 and info["max_inner"] == 18 and info["n_big"] == 1
+    theta = I.draw_params(p, 2, 31)
+    nrm = plan.norms(_params(theta[None])).cpu().numpy()
+    assert np.max(np.abs(nrm - 1.0)) <= 1e-5, np.max(np.abs(nrm - 1.0))
+    e, g = plan.energy_grad(_params(theta[None]))
+    e, g = e.cpu().numpy()[0], g.cpu().numpy()[0]
+    assert np.all(e > 0) and np.all(e < len(edges))
+    shifted = theta.copy()
+    shifted[:, :p] += 2 * math.pi
+    shifted[:, p:] += math.pi / 2
+    e2 = plan.energy(_params(shifted[None])).cpu().numpy()[0]
+    assert np.allclose(e2, e, rtol=1e-5, atol=0), (e2, e)
+    h = 1e-3
+    fd_pts = []
+    for k in range(2 * p):
+        for sgn in (1, -1):
+            t = theta[0].copy()
+            t[k] += sgn * h
+            fd_pts.append(t)
+    ef = plan.energy(_params(np.array(fd_pts)[None])).cpu().numpy()[0]
+    fd = (ef[0::2] - ef[1::2]) / (2 * h)
+    assert np.linalg.norm(g[0] - fd) <= 2e-3 * np.linalg.norm(g[0]), (g[0], fd)
+    gen = q.Plan((n, edges), p, big_general=True)
+    eg = gen.energy(_params(theta[None])).cpu().numpy()[0]
+    assert np.allclose(eg, e, rtol=E_REL_TOL, atol=0), (eg, e)
+    assert plan.device_status() == 0 and gen.device_status() == 0
+
+
 @pytest.mark.parametrize("graph,p,general", [(I.petersen(), 3, None), (I.circulant(30, [1, 2]), 3, None),
                                              (I.circulant(40, [1, 3]), 3, None), (I.random_regular(16, 3, 3), 3, None),
                                              (I.circulant(30, [1, 2]), 4, True), (I.complete_bipartite(8, 8), 3, True)])
