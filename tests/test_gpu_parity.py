@@ -293,6 +293,42 @@ def test_depth1_kernel_edge_cases(q, P):
 
 
 @pytest.mark.parametrize("graph,p,kw", [
+    (I.random_regular(30, 3, 1), 1, {}),                     # depth-1 kernel
+    (I.petersen(), 2, {}),                                   # general register kernel
+    (I.hypercube(8), 1, {"full_cone": True}),                # a 16-qubit block, core-tile schedule
+    (I.hypercube(8), 1, {"full_cone": True, "big_general": True}),   # general schedule
+    (I.random_regular(24, 3, 1), 3, {}),                     # core-tile adjoint of 10-14 inner qubits
+    (I.circulant(30, [1, 2]), 4, {}),                        # default plan on the general schedule
+])
+def test_degenerate_angles(q, graph, p, kw):
+    """Where the method degenerates (Sec. 2.2), on every schedule: with every
+    gamma_l = 0 the phases vanish and |+> is an eigenstate of every mixer;
+    with every beta_l = 0, or every beta_l = pi/2 (e^{-i pi/2 X} = -i X: the
+    kernels take it as a flip with tau = 0), the state stays |+> up to
+    diagonal phases.  Either way E = |E|/2 exactly, and E is flat in the
+    parameters that do nothing: d/d beta at gamma = 0, d/d gamma at beta = 0
+    or pi/2 (all of them at theta = 0)."""
+    n, edges = graph
+    rnd = I.draw_params(p, 1, 33)[0]
+    pts = np.zeros((4, 2 * p))
+    pts[1, p:] = rnd[p:]                        # gamma = 0, beta random
+    pts[2, :p] = rnd[:p]                        # beta = 0, gamma random
+    pts[3, :p] = rnd[:p]                        # beta = pi/2, gamma random
+    pts[3, p:] = math.pi / 2
+    plan = q.Plan((n, edges), p, **kw)
+    e, g = plan.energy_grad(_params(pts[None]))
+    e, g = e.cpu().numpy()[0], g.cpu().numpy()[0]
+    half = 0.5 * len(edges)
+    assert np.allclose(e, half, rtol=E_REL_TOL, atol=0), e
+    flat = 1e-5 * half
+    assert np.max(np.abs(g[0])) <= flat, g[0]
+    assert np.max(np.abs(g[1, p:])) <= flat, g[1]
+    assert np.max(np.abs(g[2, :p])) <= flat and np.max(np.abs(g[3, :p])) <= flat, g[2:]
+    assert np.allclose(plan.energy(_params(pts[None])).cpu().numpy()[0], half, rtol=E_REL_TOL, atol=0)
+    assert plan.device_status() == 0
+
+
+@pytest.mark.parametrize("graph,p,kw", [
     (I.petersen(), 2, {}),                                   # register cones, p = 2
     (I.hypercube(8), 1, {}),                                 # a depth-1 plan (norms take the general kernel)
     (I.hypercube(8), 1, {"full_cone": True}),                # a 16-qubit block, core-tile schedule
