@@ -641,11 +641,17 @@ def run_ours(args, rank, world, local_rank):
     s_graph.close()
     sp_graph.close()
     s_evals = len(sg) * stheta.shape[1]
+    s_reps = splan.reps()
+    s_reps["n_blocks"] = splan.shell_blocks()
+    s_flops = algorithmic_flops(s_reps, 2, grad=True) * stheta.shape[1]
     side = {"workload": "rr3-n2000x4-p2-P64: 4 random 3-regular graphs n=2000 (seeds 1-4), p=2, 64 points each, "
                         "energy+grad",
             "energy_grad_evals_per_s": world * s_evals / (s_ms / 1e3),
             "plain_all_edge_evals_per_s": world * s_evals / (sp_ms / 1e3),
-            "n_reps": int(splan.info()["n_reps"]), "tuning": s_tuning}
+            "n_reps": int(splan.info()["n_reps"]), "tuning": s_tuning,
+            # the general adjoint register kernel's algorithmic FP32 work over the whole step
+            # (prep_kernel + that kernel), against the same FP32 peak as the roofline
+            "fp32_tflops_alg": s_flops / (s_ms / 1e3) / 1e12}
     # the training driver: Adam on -E from 64 starts per graph, timed after a warm-up step
     from paper_2101_10296_gb300 import train as qtrain
     tr_steps = 50
@@ -669,6 +675,7 @@ def run_ours(args, rank, world, local_rank):
     kern_avg_ms = kern_ms / max(kern_launches, 1)
     achieved = flops / (kern_avg_ms / 1e3) / 1e12
     peak, mhz = fp32_peak_tflops(sm_count)
+    side["fp32_frac_of_peak"] = side["fp32_tflops_alg"] / peak
     traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["kernels_sha1"] == kernels_sha1() else None
     amp_updates = float((np.ldexp(1.0, reps["n_qubits"].astype(np.int64)) * p).sum()) * P
     evolved = float((reps["n_blocks"] * np.ldexp(1.0, reps["n_inner"].astype(np.int64)) * p).sum()) * P
