@@ -375,7 +375,10 @@ int qaoa_device_status(const qaoa_plan *plan, int32_t *status);
  *   points_per_task  parameter points one warp task of the register kernels
  *                    evaluates for the same cone slots (default: up to 32,
  *                    while their phase tables fit 8 KB of shared memory;
- *                    larger values are cut to what fits 12 KB per warp)
+ *                    larger values are cut to what fits 12 KB per warp; the
+ *                    depth-1 kernel's default is what leaves room for its
+ *                    resident blocks: the multiprocessor's shared memory
+ *                    split among them, less the per-block reservation)
  *   blocks_per_sm    resident blocks per SM of the persistent grid (default:
  *                    the occupancy limit)
  *   big_scratch_bytes scratch per call for large-state cones, which sets how
