@@ -295,6 +295,12 @@ def test_cone_caps(qlib):
     with pytest.raises(qlib.QAOAError) as ei:
         qlib.Plan((n, edges), 1)
     assert ei.value.code == qlib.QAOA_E_CONE_TOO_LARGE
+    # the qubit cap, QAOA_MAX_CONE_QUBITS = 32: a p = 1 cone of a star holds the whole star
+    assert qlib.Plan(I.star(31), 1).info()["max_qubits"] == 32
+    assert qlib.Plan(I.torus(8, 8), 3).info()["max_qubits"] == 32
+    with pytest.raises(qlib.QAOAError) as ei:
+        qlib.Plan(I.star(32), 1)
+    assert ei.value.code == qlib.QAOA_E_CONE_TOO_LARGE and "33 qubits" in str(ei.value)
 
 
 def test_bad_call_arguments(qlib):
