@@ -550,8 +550,7 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
         clk.mark_end()
-        # the same load, untimed, until the sampler has caught up with the region (at most 1 s;
-        # polling nvidia-smi faster than this slows the host's launches, not the device's steps)
+        # the same load, untimed, until the sampler has caught up with the region (at most 1 s)
         hold0 = time.perf_counter()
         while clk.proc and clk.count_since_start() < 5 and time.perf_counter() - hold0 < 1.0:
             for _ in range(8):
