@@ -854,6 +854,32 @@ def _mixed_plan(q):
     return q.Plan(graphs, 3), len(graphs)
 
 
+def test_one_plan_on_two_streams_at_once(q):
+    """A plan is immutable after upload and may serve several streams at once,
+    each call with its own stream-ordered scratch: calls issued on two streams
+    without a synchronisation between them (register and large-state cones,
+    and a depth-1 plan) give what the same calls give one at a time."""
+    mixed, G = _mixed_plan(q)
+    assert mixed.info()["n_big"] > 0
+    depth1 = q.Plan([I.hypercube(8), I.random_regular(60, 3, 2)], 1)
+    assert depth1.info()["depth1_kernel"] == 1
+    for plan, p, G_ in ((mixed, 3, G), (depth1, 1, 2)):
+        ths = [_params(np.stack([I.draw_params(p, 5, 60 + 10 * k + g) for g in range(G_)])) for k in range(4)]
+        ref = [plan.energy_grad(th) for th in ths]
+        torch.cuda.synchronize()
+        ref = [(e.cpu().numpy(), g.cpu().numpy()) for e, g in ref]
+        streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+        outs = []
+        for k, th in enumerate(ths):  # alternate streams, no synchronisation between the calls
+            with torch.cuda.stream(streams[k % 2]):
+                outs.append(plan.energy_grad(th))
+        torch.cuda.synchronize()
+        for (e, g), (e0, g0) in zip(outs, ref):
+            assert np.allclose(e.cpu().numpy(), e0, rtol=1e-12, atol=0)
+            assert np.allclose(g.cpu().numpy(), g0, rtol=1e-9, atol=1e-12)
+        assert plan.device_status() == 0
+
+
 def test_cuda_graph_replay_matches_direct_calls(q):
     plan, G = _mixed_plan(q)
     assert plan.info()["n_big"] > 0
