@@ -299,6 +299,11 @@ class Plan:
         import torch
         if not (isinstance(params, torch.Tensor) and params.is_cuda and params.dtype == torch.float64):
             raise TypeError("params must be a CUDA float64 tensor")
+        # device pointers must be on the current device (the library checks that the
+        # plan is there too); outputs are allocated next to params
+        if params.device.index != torch.cuda.current_device():
+            raise ValueError(f"params are on {params.device}, the current device is "
+                             f"cuda:{torch.cuda.current_device()}")
         if params.dim() == 2:
             params = params.unsqueeze(0)
         if params.dim() != 3 or params.shape[0] != self.n_graphs or params.shape[2] != 2 * self.p:
