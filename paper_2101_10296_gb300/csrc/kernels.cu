@@ -45,17 +45,23 @@ __global__ void prep_kernel(const PrepArgs a) {
     const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     const int64_t GP = int64_t(a.G) * a.P;
-    const int64_t nlut = GP * a.p * a.cmax1;
     const int p2 = 2 * a.p;
-    for (int64_t i = tid; i < nlut; i += stride) {
-        const int64_t c = i % a.cmax1;
-        const int64_t r = i / a.cmax1;
+    // one row per (graph, point, layer): exp(-i gamma c) for c = 0 .. cmax1-1 by the
+    // recurrence z_(c+1) = z_c exp(-i gamma) in FP64 (one sincos per row; after at most
+    // 64 steps its rounding error, ~1e-14, is far below the FP32 table's own)
+    for (int64_t r = tid; r < GP * a.p; r += stride) {
         const int64_t l = r % a.p;
         const int64_t gj = r / a.p;
-        const double gam = a.params[gj * p2 + l];
         double sn, cs;
-        sincos(gam * double(c), &sn, &cs);
-        a.lut[i] = make_float2(float(cs), float(-sn));
+        sincos(a.params[gj * p2 + l], &sn, &cs);
+        float2 *row = a.lut + r * a.cmax1;
+        double zr = 1.0, zi = 0.0;
+        for (int c = 0; c < a.cmax1; ++c) {
+            row[c] = make_float2(float(zr), float(zi));
+            const double nr = fma(zr, cs, zi * sn);  // (zr + i zi)(cos gamma - i sin gamma)
+            zi = fma(zi, cs, -(zr * sn));
+            zr = nr;
+        }
     }
     for (int64_t i = tid; i < GP * a.p; i += stride) {
         const int64_t gj = i / a.p, l = i % a.p;
@@ -160,7 +166,9 @@ int smem_per_block(int blocks) {
 }
 
 cudaError_t launch_prep(const PrepArgs &a, cudaStream_t s) {
-    int64_t work = int64_t(a.G) * a.P * a.p * (a.cmax1 > kKpow ? a.cmax1 : kKpow);
+    // threads for the widest loop: table rows, gradient zeroing or term zeroing
+    int64_t work = int64_t(a.G) * a.P * 2 * a.p;
+    if (a.terms) work = std::max<int64_t>(work, a.n_reps * a.P);
     int64_t blocks = (work + 255) / 256;
     if (blocks < 1) blocks = 1;
     if (blocks > 4096) blocks = 4096;
